@@ -1,0 +1,243 @@
+"""Pins of the oracle's projections, BiCGStab, GMRES, GMRES-DR, two-grid driver and adjoint.
+
+Each test checks the oracle against something other than itself:
+  - projection invariants stated with the Section 2.2 projections (Galerkin: V^T r = 0;
+    MinRes: (AV)^T r = 0 and ||r|| cannot grow), and exact eigenvectors removing their
+    components;
+  - brute force: dense LU solutions on <= 15^2 / 7^3 grids;
+  - textbook special cases: A = lambda I converges in one BiCGStab half step; GMRES(n)
+    on an n x n system is exact; one GMRES-DR cycle is GMRES(m);
+  - the defining Petrov-Galerkin property of harmonic Ritz pairs (A y - theta y is
+    orthogonal to A V_m), computed with the actual vectors;
+  - harmonic Ritz values converge to the closed-form eigenvalues of the operator;
+  - the Section 4.1 cycle tolerance: cycles meeting the first criterion reach rtol
+    exactly at icyc = ncyc; the second criterion bounds progress to icyc/ncyc of the way;
+  - adjoint gradient against central finite differences of direct solves.
+Parity unpinned: iteration counts (they depend on rounding and on MATLAB internals).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import tg_inputs as gi
+from oracle import adjoint, krylov, twogrid
+from oracle.gmresdr import gmresdr, harmonic_ritz, select_k, eigen_residuals, arnoldi_extend
+from oracle.operators import CD2D, CD3D, U1_4D, VARK2D, Operator, cd2d_eigenvalues
+
+
+def _dense_solve(op, b):
+    return np.linalg.solve(op.sparse().toarray(), b)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_minres_projection_invariants():
+    op = Operator(CD2D, 15, (2.0,))
+    Y = gi.random_dense((op.n, 6), 1)
+    defl = krylov.make_deflation(op.apply, Y, "minres")
+    b = gi.rhs(op.n, 0)
+    x = gi.random_dense(op.n, 2)
+    r = b - op.apply(x)
+    x2, r2 = krylov.minres_project(defl, x, r)
+    scale = np.linalg.norm(defl.AY) * np.linalg.norm(r)
+    assert np.max(np.abs(defl.AY.T @ r2)) < 1e-13 * scale
+    assert np.linalg.norm(r2) <= np.linalg.norm(r)
+    assert _rel(r2, b - op.apply(x2)) < 1e-12
+
+
+def test_galerkin_projection_invariants():
+    op = Operator(CD2D, 15, (2.0,))
+    Y = gi.random_dense((op.n, 6), 3)
+    defl = krylov.make_deflation(op.apply, Y, "galerkin")
+    b = gi.rhs(op.n, 1)
+    x = np.zeros(op.n)
+    x2, r2 = krylov.galerkin_project(defl, x, b.copy())
+    assert np.max(np.abs(Y.T @ r2)) < 1e-12 * np.linalg.norm(Y) * np.linalg.norm(b)
+    assert _rel(r2, b - op.apply(x2)) < 1e-12
+
+
+def test_projection_with_exact_eigenvectors():
+    op = Operator(CD2D, 11, (1.0,))
+    lam, W = np.linalg.eig(op.sparse().toarray())
+    idx = np.argsort(lam.real)[:5]
+    Y = W[:, idx].real
+    b = gi.rhs(op.n, 4)
+    defl = krylov.make_deflation(op.apply, Y, "minres")
+    _, r2 = krylov.minres_project(defl, np.zeros(op.n), b.copy())
+    # span(AY) = span(Y) for exact eigenvectors, so the new residual is orthogonal to Y
+    assert np.max(np.abs(Y.T @ r2)) < 1e-12 * np.linalg.norm(b)
+
+
+def test_bicgstab_scalar_matrix_one_half_step():
+    lam = 3.7
+    b = gi.rhs(50, 5)
+    res = krylov.bicgstab_cycle(lambda u: lam * u, np.zeros(50), b, 1e-12 * np.linalg.norm(b))
+    assert res.converged and res.mvps == 1
+    assert _rel(res.x, b / lam) < 1e-15
+
+
+@pytest.mark.parametrize("kind,N,beta", [(CD2D, 15, (1.0,)), (CD3D, 7, (2.0, 1.0, 0.5))])
+def test_bicgstab_brute_force(kind, N, beta):
+    op = Operator(kind, N, beta)
+    b = gi.rhs(op.n, 6)
+    xs = _dense_solve(op, b)
+    for ncyc, cap in ((1, None), (0, 20), (10, None)):
+        res = krylov.bicgstab_proj(op.apply, b, np.zeros(op.n), None, rtol=1e-11,
+                                   ncyc=ncyc, restart_mvps=cap, max_mvps=20000)
+        assert res.converged
+        assert _rel(res.x, xs) < 1e-8
+        assert res.relres <= 1e-11
+
+
+def test_bicgstab_cycle_recurrences():
+    op = Operator(CD2D, 15, (1.0,))
+    b = gi.rhs(op.n, 7)
+    # half step only: s = r - alpha v is orthogonal to the shadow vector r_hat = r0
+    res = krylov.bicgstab_cycle(op.apply, np.zeros(op.n), b, 0.0, max_mvps=1)
+    assert abs(b @ res.r) < 1e-12 * np.linalg.norm(b) * np.linalg.norm(res.r)
+    assert _rel(res.r, b - op.apply(res.x)) < 1e-12
+    # full steps: the recursively updated residual stays equal to b - A x
+    res = krylov.bicgstab_cycle(op.apply, np.zeros(op.n), b, 0.0, max_mvps=12)
+    assert res.mvps == 12
+    assert _rel(res.r, b - op.apply(res.x)) < 1e-10
+
+
+def test_gmres_full_space_is_exact():
+    op = Operator(CD2D, 5, (3.0,))
+    b = gi.rhs(op.n, 8)
+    res = krylov.gmres_cycle(op.apply, np.zeros(op.n), b, op.n, 0.0)
+    assert _rel(res.x, _dense_solve(op, b)) < 1e-10
+    assert all(res.history[i + 1] <= res.history[i] * (1 + 1e-12) for i in range(len(res.history) - 1))
+
+
+def test_gmres_proj_brute_force():
+    op = Operator(CD2D, 15, (1.0,))
+    b = gi.rhs(op.n, 9)
+    lam, W = np.linalg.eig(op.sparse().toarray())
+    Y = W[:, np.argsort(lam.real)[:8]].real
+    defl = krylov.make_deflation(op.apply, Y, "minres")
+    res = krylov.gmres_proj(op.apply, b, np.zeros(op.n), defl, m=10, rtol=1e-11)
+    assert res.converged and _rel(res.x, _dense_solve(op, b)) < 1e-8
+    plain = krylov.gmres_proj(op.apply, b, np.zeros(op.n), None, m=10, rtol=1e-11)
+    assert res.mvps < plain.mvps
+
+
+def test_cycle_tolerance_schedule():
+    rtol, ncyc, nr0 = 1e-8, 7, 3.0
+    nr = nr0
+    for icyc in range(1, ncyc + 1):
+        rt = krylov.cycle_tolerance(rtol, nr0, nr, icyc, ncyc)
+        # the second criterion: at least icyc/ncyc of the way in orders of magnitude
+        assert rt * nr <= nr0 * rtol ** (icyc / ncyc) * (1 + 1e-12)
+        nr = rt * nr
+    assert abs(nr - rtol * nr0) < 1e-12 * rtol * nr0
+    # a residual that jumped up during the projection: the second criterion is the binding one
+    rt = krylov.cycle_tolerance(rtol, 1.0, 1e-2, 6, 20)
+    assert abs(rt * 1e-2 - rtol ** (6 / 20)) < 1e-12
+
+
+def test_harmonic_ritz_petrov_galerkin():
+    op = Operator(CD2D, 15, (2.0,))
+    m = 12
+    V = np.zeros((op.n, m + 1))
+    H = np.zeros((m + 1, m))
+    b = gi.rhs(op.n, 10)
+    V[:, 0] = b / np.linalg.norm(b)
+    V, H = arnoldi_extend(op.apply, V, H, 0, m)
+    theta, G = harmonic_ritz(H)
+    AV = np.stack([op.apply(V[:, j]) for j in range(m)], axis=1)
+    for i in range(m):
+        y = V[:, :m] @ G[:, i]
+        resid = AV @ G[:, i] - theta[i] * y
+        assert np.linalg.norm(AV.T @ resid) < 1e-8 * np.linalg.norm(AV) * np.linalg.norm(y) * abs(theta[i])
+    idx = select_k(theta, 4, True)
+    er = eigen_residuals(H, theta, G, idx)
+    for e, i in zip(er, idx):
+        g = G[:, i] / np.linalg.norm(G[:, i])
+        y = V[:, :m] @ g
+        assert abs(e - np.linalg.norm(AV @ g - theta[i] * y)) < 1e-9 * abs(theta[i])
+
+
+def test_gmresdr_single_cycle_is_gmres():
+    op = Operator(CD2D, 15, (1.0,))
+    b = gi.rhs(op.n, 11)
+    gd = gmresdr(op.apply, b, 20, 5, max_cycles=1, rtol=0.0)
+    ref = krylov.gmres_cycle(op.apply, np.zeros(op.n), b, 20, 0.0)
+    assert _rel(gd.x, ref.x) < 1e-10
+
+
+def test_gmresdr_ritz_values_converge_to_closed_form():
+    N = 31
+    op = Operator(CD2D, N, (1.0,))
+    b = gi.rhs(op.n, 12)
+    gd = gmresdr(op.apply, b, 30, 10, nev=6, rtolev=1e-9, rtol=1e-10, max_cycles=400)
+    assert gd.converged
+    exact = cd2d_eigenvalues(N, 1.0)[:6]
+    th = np.sort(gd.theta.real)[:6]
+    assert np.max(np.abs(th - exact) / exact) < 1e-8
+    assert _rel(gd.x, _dense_solve(op, b)) < 1e-7
+    # the returned basis is orthonormal and spans the converged eigenvectors
+    Q = gd.Yc
+    assert np.max(np.abs(Q.T @ Q - np.eye(Q.shape[1]))) < 1e-12
+    lam, W = np.linalg.eig(op.sparse().toarray())
+    w1 = W[:, np.argsort(lam.real)[0]].real
+    assert np.linalg.norm(w1 - Q @ (Q.T @ w1)) < 1e-6
+
+
+def test_gmresdr_complex_hermitian():
+    L = 4
+    op = Operator(U1_4D, L, links=gi.u1_links(L, 1), mass=0.05)
+    b = gi.rhs(op.n, 13).astype(np.complex128)
+    gd = gmresdr(op.apply, b, 30, 8, nev=4, rtolev=1e-8, rtol=1e-10, max_cycles=300,
+                 dtype=np.complex128)
+    assert gd.converged
+    lam = np.linalg.eigvalsh(op.sparse().toarray())
+    assert np.max(np.abs(np.sort(gd.theta.real)[:4] - lam[:4]) / lam[:4]) < 1e-7
+    assert _rel(gd.x, np.linalg.solve(op.sparse().toarray(), b)) < 1e-7
+
+
+@pytest.mark.parametrize("method", ["bicgstab", "gmres"])
+@pytest.mark.parametrize("kind,N,beta", [(CD2D, 15, (1.0,)), (CD3D, 7, (2.0, 1.0, 0.5))])
+def test_two_grid_brute_force(method, kind, N, beta):
+    op = Operator(kind, N, beta)
+    b = gi.rhs(op.n, 14)
+    res = twogrid.two_grid_solve(op, b, m=12, k=4, rtolev=1e-6, method=method, rtol=1e-11,
+                                 ncyc=10, restart_mvps=None, m3=8)
+    assert res.solve.converged
+    assert _rel(res.x, _dense_solve(op, b)) < 1e-8
+
+
+def test_two_grid_lattice_brute_force():
+    L = 8
+    links = gi.u1_links(L, 2)
+    op = Operator(U1_4D, L, links=links, mass=0.5)
+    b = (gi.rhs(op.n, 15) + 0j)
+    res = twogrid.two_grid_solve(op, b, m=20, k=8, rtolev=1e-4, rtol=1e-10, ncyc=10,
+                                 restart_mvps=None)
+    assert res.solve.converged
+    xs = twogrid.exact_solution(op, b)
+    assert _rel(res.x, xs) < 1e-7
+
+
+def test_exact_solution_matches_dense():
+    op = Operator(VARK2D, 9, (1.0,), gi.kappa_grf(9, 5))
+    b = gi.rhs(op.n, 16)
+    assert _rel(twogrid.exact_solution(op, b), _dense_solve(op, b)) < 1e-12
+
+
+def test_adjoint_gradient_vs_finite_differences():
+    N = 15
+    kap = gi.kappa_grf(N, 3)
+    op = Operator(VARK2D, N, (1.0,), kap)
+    b = gi.rhs(op.n, 17)
+    xstar = gi.random_dense(op.n, 18) * 1e-3
+    _, grad, _, _ = adjoint.loss_and_gradient(op, b, xstar)
+    nodes = gi.kappa_fd_nodes(N, 12, 0)
+    fd = adjoint.finite_difference(op, b, xstar, nodes)
+    assert np.max(np.abs(grad[nodes] - fd) / np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())) < 1e-5
+    # a boundary node touching one interior face
+    p = np.array([0 * (N + 2) + 5])
+    fdb = adjoint.finite_difference(op, b, xstar, p)
+    assert abs(grad[p][0] - fdb[0]) <= 1e-5 * max(abs(fdb[0]), 1e-3 * np.abs(fd).max())

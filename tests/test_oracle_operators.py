@@ -1,0 +1,182 @@
+"""Pins of the oracle's operators and grid transfer to facts the paper and mathematics fix.
+
+- closed-form eigenvalues of the centred convection-diffusion operator (diagonally
+  similar to a symmetric one when |beta h / 2| < 1), checked against LAPACK eig of the
+  independently assembled sparse matrix;
+- the free-field lattice spectrum (Fourier), Hermiticity and gauge covariance;
+- A^T = A(kappa, -beta) at matrix level;
+- bilinear/trilinear prolongation reproduces linear functions; its point formulas agree
+  with an entry-by-entry sparse P; P^H P = I for the lattice block transport, and the
+  Galerkin coarse operator of the free field has the closed form (m + 4) I - 1/2 hops.
+"""
+import numpy as np
+import pytest
+
+import tg_inputs as gi
+from oracle import transfer
+from oracle.operators import (CD2D, CD3D, U1_4D, VARK2D, Operator, cd2d_eigenvalues,
+                              cd3d_eigenvalues, coarse_operator, free_lattice_eigenvalues,
+                              lattice_shift_index)
+
+
+@pytest.mark.parametrize("N,beta", [(9, 3.0), (15, 1.0), (7, -5.0)])
+def test_cd2d_closed_form_spectrum(N, beta):
+    op = Operator(CD2D, N, (beta,))
+    lam = np.sort(np.linalg.eigvals(op.sparse().toarray()).real)
+    ref = cd2d_eigenvalues(N, beta)
+    assert np.max(np.abs(lam - ref)) / ref.max() < 1e-13
+
+
+def test_cd3d_closed_form_spectrum():
+    op = Operator(CD3D, 5, (2.0, 1.0, 0.5))
+    lam = np.sort(np.linalg.eigvals(op.sparse().toarray()).real)
+    ref = cd3d_eigenvalues(5, (2.0, 1.0, 0.5))
+    assert np.max(np.abs(lam - ref)) / ref.max() < 1e-13
+
+
+def test_cfg_sizes_smallest_eigenvalue():
+    # 127^2, beta = 1: the continuum operator -Lap + beta d/dx is similar to
+    # -Lap + beta^2/4, whose smallest eigenvalue on the unit square is 2 pi^2 + beta^2/4
+    lmin = cd2d_eigenvalues(127, 1.0)[0]
+    assert abs(lmin - 19.988) < 1e-3
+    assert abs(lmin - (2 * np.pi ** 2 + 0.25)) / lmin < 1e-4
+
+
+@pytest.mark.parametrize("kind,N,beta", [(CD2D, 11, (2.0,)), (CD3D, 5, (2.0, 1.0, 0.5))])
+def test_matrix_free_equals_assembled(kind, N, beta):
+    op = Operator(kind, N, beta)
+    u = gi.random_dense(op.n, 1)
+    y = op.apply(u)
+    assert np.max(np.abs(y - op.sparse() @ u)) <= 1e-14 * np.max(np.abs(y))
+
+
+def test_vark2d_assembled_and_special_case():
+    N = 9
+    kap = gi.kappa_grf(N, 0)
+    op = Operator(VARK2D, N, (1.0,), kap)
+    u = gi.random_dense(op.n, 2)
+    y = op.apply(u)
+    assert np.max(np.abs(y - op.sparse() @ u)) <= 1e-14 * np.max(np.abs(y))
+    # kappa == 1 reduces to the constant-coefficient operator
+    one = Operator(VARK2D, N, (1.0,), np.ones((N + 2) ** 2))
+    assert np.max(np.abs(one.apply(u) - Operator(CD2D, N, (1.0,)).apply(u))) <= 1e-12 * np.max(np.abs(y))
+
+
+@pytest.mark.parametrize("kind", [CD2D, CD3D, VARK2D])
+def test_transpose_is_beta_negated(kind):
+    N = 7
+    beta = (1.5,) if kind != CD3D else (2.0, 1.0, 0.5)
+    kap = gi.kappa_grf(N, 1) if kind == VARK2D else None
+    op = Operator(kind, N, beta, kap)
+    diff = (op.sparse().T - op.transposed().sparse()).toarray()
+    assert np.max(np.abs(diff)) == 0.0
+
+
+def test_lattice_free_field_spectrum():
+    L, m = 4, 0.3
+    op = Operator(U1_4D, L, links=np.ones((4, L ** 4), dtype=np.complex128), mass=m)
+    lam = np.linalg.eigvalsh(op.sparse().toarray())
+    assert np.max(np.abs(np.sort(lam) - free_lattice_eigenvalues(L, m))) < 1e-12
+
+
+def test_lattice_hermitian_and_gauge_covariant():
+    L = 4
+    links = gi.u1_links(L, 3)
+    op = Operator(U1_4D, L, links=links, mass=0.2)
+    A = op.sparse().toarray()
+    assert np.max(np.abs(A - A.conj().T)) == 0.0
+    psi = gi.random_dense(L ** 4, 4) + 1j * gi.random_dense(L ** 4, 5)
+    assert np.max(np.abs(op.apply(psi) - A @ psi)) < 1e-13
+    g = np.exp(1j * gi.random_dense(L ** 4, 6))
+    links2 = np.stack([g * links[mu] * np.conj(g[lattice_shift_index(L, mu, +1)]) for mu in range(4)])
+    op2 = Operator(U1_4D, L, links=links2, mass=0.2)
+    assert np.max(np.abs(op2.apply(g * psi) - g * op.apply(psi))) < 1e-12
+
+
+def _linear(xs, ys, zs=None):
+    f = 0.3 + 1.7 * xs - 0.9 * ys
+    return f if zs is None else f + 0.4 * zs
+
+
+def test_prolong2d_reproduces_linear_and_matches_sparse():
+    Nc = 7
+    N = 2 * Nc + 1
+    hc, h = 1.0 / (Nc + 1), 1.0 / (N + 1)
+    J, I = np.meshgrid(np.arange(1, Nc + 1), np.arange(1, Nc + 1), indexing="ij")
+    uc = _linear(I * hc, J * hc).reshape(-1)
+    uf = transfer.prolong2d(uc, Nc).reshape(N, N)
+    j, i = np.meshgrid(np.arange(1, N + 1), np.arange(1, N + 1), indexing="ij")
+    exact = _linear(i * h, j * h)
+    inner = (i >= 2) & (i <= N - 1) & (j >= 2) & (j <= N - 1)   # stencil clear of the boundary
+    assert np.max(np.abs(uf - exact)[inner]) < 1e-14
+    w = gi.random_dense(Nc * Nc, 3)
+    assert np.max(np.abs(transfer.prolong2d(w, Nc) - transfer.prolongation_matrix(Nc, 2) @ w)) < 1e-15
+
+
+def test_prolong3d_reproduces_linear_and_matches_sparse():
+    Nc = 4
+    N = 2 * Nc + 1
+    hc, h = 1.0 / (Nc + 1), 1.0 / (N + 1)
+    K, J, I = np.meshgrid(*(np.arange(1, Nc + 1),) * 3, indexing="ij")
+    uc = _linear(I * hc, J * hc, K * hc).reshape(-1)
+    uf = transfer.prolong3d(uc, Nc).reshape(N, N, N)
+    k, j, i = np.meshgrid(*(np.arange(1, N + 1),) * 3, indexing="ij")
+    exact = _linear(i * h, j * h, k * h)
+    inner = (i >= 2) & (i <= N - 1) & (j >= 2) & (j <= N - 1) & (k >= 2) & (k <= N - 1)
+    assert np.max(np.abs(uf - exact)[inner]) < 1e-14
+    w = gi.random_dense(Nc ** 3, 3)
+    assert np.max(np.abs(transfer.prolong3d(w, Nc) - transfer.prolongation_matrix(Nc, 3) @ w)) < 1e-15
+
+
+def test_full_weighting_of_constant():
+    N = 15
+    uf = np.ones(N * N)
+    uc = transfer.restrict(uf, N, 2).reshape(7, 7)
+    assert np.allclose(uc[1:-1, 1:-1], 1.0, atol=1e-15)
+    uc3 = transfer.restrict(np.ones(9 ** 3), 9, 3).reshape(4, 4, 4)
+    assert np.allclose(uc3[1:-1, 1:-1, 1:-1], 1.0, atol=1e-15)
+
+
+def test_coarse_rediscretisation():
+    op = Operator(VARK2D, 9, (1.0,), gi.kappa_grf(9, 2))
+    opc = coarse_operator(op)
+    assert opc.N == 4
+    K = op.kappa.reshape(11, 11)
+    assert np.array_equal(opc.kappa.reshape(6, 6), K[::2, ::2])
+
+
+def test_lattice_block_transport():
+    L = 8
+    links = gi.u1_links(L, 0)
+    op = Operator(U1_4D, L, links=links, mass=0.1)
+    Ac, P, diag, fwd, bwd = transfer.lattice_coarse_stencil(op)
+    assert np.max(np.abs((P.conj().T @ P).toarray() - np.eye(P.shape[1]))) < 1e-15
+    D = Ac - Ac.conj().T
+    assert abs(D).max() < 1e-14
+    psi = gi.random_dense(4 ** 4, 1) + 1j * gi.random_dense(4 ** 4, 2)
+    assert np.max(np.abs(transfer.apply_lattice_coarse(diag, fwd, bwd, 4, psi) - Ac @ psi)) < 1e-13
+    assert Ac.nnz <= 9 * 4 ** 4
+
+
+def test_lattice_coarse_free_field_closed_form():
+    L, m = 8, 0.25
+    op = Operator(U1_4D, L, links=np.ones((4, L ** 4), dtype=np.complex128), mass=m)
+    _, _, diag, fwd, bwd = transfer.lattice_coarse_stencil(op)
+    assert np.allclose(diag, m + 4.0, atol=1e-14)
+    assert np.allclose(fwd, -0.5, atol=1e-14) and np.allclose(bwd, -0.5, atol=1e-14)
+
+
+def test_lattice_coarse_gauge_covariant():
+    L = 8
+    links = gi.u1_links(L, 4)
+    g = np.exp(1j * gi.random_dense(L ** 4, 7))
+    links2 = np.stack([g * links[mu] * np.conj(g[lattice_shift_index(L, mu, +1)]) for mu in range(4)])
+    Ac1 = transfer.lattice_coarse_stencil(Operator(U1_4D, L, links=links, mass=0.1))[0]
+    Ac2 = transfer.lattice_coarse_stencil(Operator(U1_4D, L, links=links2, mass=0.1))[0]
+    Lc = L // 2
+    X = np.arange(Lc ** 4)
+    Xc = [(X // Lc ** a) % Lc for a in range(4)]
+    gc = g[2 * Xc[0] + L * (2 * Xc[1] + L * (2 * Xc[2] + L * 2 * Xc[3]))]
+    import scipy.sparse as sp
+    G = sp.diags(gc)
+    assert abs(Ac2 - G @ Ac1 @ G.conj()).max() < 1e-13
