@@ -1,0 +1,1282 @@
+// Host side of the tg library: handles, workspaces, the solver drivers and the C ABI
+// declared in include/tg.h.  Every numerical step runs in the kernels of
+// tg_kernels.cuh, tg_small.cu and tg_setup.cu; the host only launches them, reads a few
+// scalars per cycle and takes the restart decisions of the algorithms.
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tg_kernels.cuh"
+#include "tg_setup.cuh"
+#include "tg_small.cuh"
+
+namespace tg {
+
+// ============================================================================= errors
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int cuda_status(cudaError_t e, const char *where) {
+    set_error("%s: %s", where, cudaGetErrorString(e));
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? TG_OOM : TG_CUDA_ERROR;
+}
+
+#define TG_ARG(cond, ...)                 \
+    do {                                  \
+        if (!(cond)) {                    \
+            ::tg::set_error(__VA_ARGS__); \
+            return TG_BAD_ARG;            \
+        }                                 \
+    } while (0)
+
+int num_sms() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    return v;
+}
+
+int grid_for(int64_t n, int per_sm) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)num_sms() * per_sm;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+static int tiles_grid(int64_t n, int per_sm) {
+    int64_t b = (n + 31) / 32;
+    int64_t cap = (int64_t)num_sms() * per_sm;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+// ============================================================================= buffers
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int ensure(size_t b) {
+        if (bytes >= b && p) return TG_OK;
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return cuda_status(e, "cudaMalloc");
+        }
+        bytes = b;
+        return TG_OK;
+    }
+    template <class U> U *as() const { return reinterpret_cast<U *>(p); }
+};
+
+struct PinBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    PinBuf() = default;
+    PinBuf(const PinBuf &) = delete;
+    PinBuf &operator=(const PinBuf &) = delete;
+    ~PinBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    int ensure(size_t b) {
+        if (bytes >= b && p) return TG_OK;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cudaError_t e = cudaMallocHost(&p, b);
+        if (e != cudaSuccess) return cuda_status(e, "cudaMallocHost");
+        bytes = b;
+        return TG_OK;
+    }
+};
+
+enum Slot {
+    S_PART, S_TICKET, S_SMALL, S_RH, S_P, S_V, S_S, S_T, S_R32, S_E32, S_R64,
+    S_GV, S_GV2, S_GH, S_GH2, S_GC, S_GX, S_GD, S_GRES, S_GZ, S_GP, S_GCN, S_GTHETA, S_GWR, S_GWI,
+    S_GORD, S_GERES, S_GWORK, S_GY, S_GG, S_GINFO, S_GTMP, S_GB, S_GH1, S_GHV,
+    S_FV, S_FH, S_FCS, S_FSN, S_FG, S_FY, S_FSTATE, S_BC,
+    S_COUNT
+};
+
+}  // namespace tg
+
+using namespace tg;
+
+struct Level {
+    DevOp A, AT;
+    DevOp32 A32, AT32;
+};
+
+struct tg_op {
+    int kind = 0;
+    int dim = 2;
+    int N = 0, Nc = 0;
+    int n = 0, nc = 0;
+    bool cplx_ = false;
+    double beta[3] = {0, 0, 0};
+    double mass = 0;
+    Level fine, coarse;
+    DBuf kappa, kappa_c, coef, coef32, coefT, coefT32, ccoef, ccoef32, ccoefT, ccoefT32;
+    DBuf links, pw, cst;
+    DBuf ws[S_COUNT];
+    PinBuf pin;
+};
+
+struct tg_defl {
+    int kk = 0;
+    int n = 0;
+    int proj = TG_PROJ_MINRES;
+    int precision = TG_F64;
+    bool cplx_ = false;
+    bool transposed = false;
+    DBuf Y, AY, Q, AV, R, M, info;
+    DBuf W32, B1_32, B2_32;
+};
+
+namespace tg {
+
+static int elem_size(const tg_op *op) { return op->cplx_ ? 16 : 8; }
+
+template <class U> static U *wsp(tg_op *op, Slot s) { return op->ws[s].as<U>(); }
+static int wsx(tg_op *op, Slot s, size_t bytes) { return op->ws[s].ensure(bytes); }
+
+// reduction scratch: partials (sized generously), a ticket, a small result area
+static int red_ready(tg_op *op, size_t part_bytes) {
+    TG_CHECK(wsx(op, S_PART, part_bytes < (1 << 20) ? (1 << 20) : part_bytes));
+    if (!op->ws[S_TICKET].p) {
+        TG_CHECK(wsx(op, S_TICKET, 64));
+        TG_CHECK_CUDA(cudaMemset(op->ws[S_TICKET].p, 0, 64));
+    }
+    TG_CHECK(wsx(op, S_SMALL, 1 << 16));
+    TG_CHECK(op->pin.ensure(1 << 16));
+    return TG_OK;
+}
+
+static int readback(tg_op *op, const void *dev, size_t bytes, cudaStream_t s) {
+    TG_CHECK_CUDA(cudaMemcpyAsync(op->pin.p, dev, bytes, cudaMemcpyDeviceToHost, s));
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+static double dnorm2(double v) { return v; }
+static double dnorm2(cplx v) { return v.re; }
+
+// ||a||^2 and (optionally) <a, b>, read back to the host.
+template <class T>
+static int dot_host(tg_op *op, const T *a, const T *b, int n, double *aa, typename ST<T>::D *ab, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    TG_CHECK(red_ready(op, 0));
+    int g = grid_for(n, 4);
+    D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 1024);
+    k_dot<T><<<g, kThreads, 0, s>>>(a, b, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out);
+    TG_LAUNCH_CHECK();
+    TG_CHECK(readback(op, out, 2 * sizeof(D), s));
+    const D *h = reinterpret_cast<const D *>(op->pin.p);
+    *aa = dnorm2(h[0]);
+    if (ab) *ab = h[1];
+    return TG_OK;
+}
+
+static const DevOp &pick(const tg_op *op, int level, int transpose) {
+    const Level &L = level == TG_COARSE ? op->coarse : op->fine;
+    return transpose ? L.AT : L.A;
+}
+static const DevOp32 &pick32(const tg_op *op, int level, int transpose) {
+    const Level &L = level == TG_COARSE ? op->coarse : op->fine;
+    return transpose ? L.AT32 : L.A32;
+}
+
+template <class T>
+static int launch_apply(const DevOp &A, const DevOp32 &A32, const T *x, T *y, cudaStream_t s) {
+    k_apply<T><<<grid_for(A.n, 8), kThreads, 0, s>>>(A, A32, x, y);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+// ----------------------------------------------------------------------------- tall-skinny helpers
+template <class T>
+static int set_smem(const void *fn, size_t bytes) {
+    if (bytes > 48 * 1024) TG_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return TG_OK;
+}
+
+// Out (n x q) = In (n x p) S (p x q)
+template <class T>
+static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Out, size_t ldo, int n, cudaStream_t s) {
+    size_t smem = (size_t)32 * p * sizeof(T);
+    TG_CHECK(set_smem<T>((const void *)k_tsm<T>, smem));
+    k_tsm<T><<<tiles_grid(n, 4), kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+// h = V^H w (ncol entries, device D array)
+template <class T>
+static int gemv_t(tg_op *op, const T *V, size_t ldv, int ncol, const T *w, int n, typename ST<T>::D *h, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    int gb = tiles_grid(n, 2);
+    TG_CHECK(red_ready(op, (size_t)gb * ncol * sizeof(D)));
+    k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, wsp<D>(op, S_PART));
+    TG_LAUNCH_CHECK();
+    k_sum_part<D><<<1, 256, 0, s>>>(wsp<D>(op, S_PART), gb, ncol, h, 0);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+// G = A^H B (k x k, device D array, column-major)
+template <class T, int EPT>
+static int gram_ept(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int sym, typename ST<T>::D *G,
+                    cudaStream_t s) {
+    using D = typename ST<T>::D;
+    int gb = tiles_grid(n, 1);
+    TG_CHECK(red_ready(op, (size_t)gb * k * k * sizeof(D)));
+    size_t smem = (size_t)2 * 32 * k * sizeof(T);
+    TG_CHECK(set_smem<T>((const void *)k_gram_part<T, EPT>, smem));
+    k_gram_part<T, EPT><<<gb, kThreads, smem, s>>>(A, B, ld, k, n, sym, wsp<D>(op, S_PART));
+    TG_LAUNCH_CHECK();
+    k_sum_part<D><<<(k * k + 255) / 256, 256, 0, s>>>(wsp<D>(op, S_PART), gb, k * k, G, 0);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+template <class T>
+static int gram(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int sym, typename ST<T>::D *G,
+                cudaStream_t s) {
+    if (k * k <= 4 * kThreads) return gram_ept<T, 4>(op, A, B, ld, k, n, sym, G, s);
+    if (k * k <= 16 * kThreads) return gram_ept<T, 16>(op, A, B, ld, k, n, sym, G, s);
+    return gram_ept<T, 64>(op, A, B, ld, k, n, sym, G, s);
+}
+
+// CholQR2: A (n x k) = Q R.  Writes Q (n x k), R and Rinv (k x k, device D).
+template <class T>
+static int cholqr2(tg_op *op, const T *A, int k, int n, T *Q, T *R, T *Rinv, int *info_dev, cudaStream_t s) {
+    DBuf G, R1, R1i, R2, R2i;
+    size_t kb = (size_t)k * k * sizeof(T);
+    TG_CHECK(G.ensure(kb));
+    TG_CHECK(R1.ensure(kb));
+    TG_CHECK(R1i.ensure(kb));
+    TG_CHECK(R2.ensure(kb));
+    TG_CHECK(R2i.ensure(kb));
+    TG_CHECK(gram<T>(op, A, A, n, k, n, 1, G.as<T>(), s));
+    launch_chol_inv<T>(G.as<T>(), k, R1.as<T>(), R1i.as<T>(), info_dev, s);
+    TG_LAUNCH_CHECK();
+    TG_CHECK(tsm<T>(A, n, k, R1i.as<T>(), k, k, Q, n, n, s));
+    TG_CHECK(gram<T>(op, Q, Q, n, k, n, 1, G.as<T>(), s));
+    launch_chol_inv<T>(G.as<T>(), k, R2.as<T>(), R2i.as<T>(), info_dev + 1, s);
+    TG_LAUNCH_CHECK();
+    TG_CHECK(tsm<T>(Q, n, k, R2i.as<T>(), k, k, Q, n, n, s));   // in place: each tile is staged first
+    TG_CHECK(tsm<T>(R2.as<T>(), k, k, R1.as<T>(), k, k, R, k, k, s));     // R = R2 R1
+    TG_CHECK(tsm<T>(R1i.as<T>(), k, k, R2i.as<T>(), k, k, Rinv, k, k, s));  // R^-1 = R1^-1 R2^-1
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));   // the local buffers are freed on return
+    return TG_OK;
+}
+
+}  // namespace tg
+
+// ============================================================================= operator set-up
+extern "C" const char *tg_status_string(int status) {
+    switch (status) {
+        case TG_OK: return "ok";
+        case TG_NOT_CONVERGED: return "not converged";
+        case TG_BREAKDOWN: return "breakdown";
+        case TG_NAN: return "NaN or Inf encountered";
+        case TG_BAD_ARG: return "bad argument";
+        case TG_OOM: return "out of device memory";
+        case TG_CUDA_ERROR: return "CUDA error";
+        case TG_SYNC_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *tg_last_error(void) { return g_err.c_str(); }
+
+static void const_coefs(DevOp &A, DevOp &AT, DevOp32 &A32, DevOp32 &AT32, int kind, int N, const double *beta) {
+    const double h = 1.0 / (N + 1);
+    const double d = -1.0 / (h * h);
+    const int dim = kind == TG_CD3D ? 3 : 2;
+    A.c0 = 2.0 * dim / (h * h);
+    double bx = beta[0], by = dim == 3 ? beta[1] : 0.0, bz = dim == 3 ? beta[2] : 0.0;
+    A.cxm = d - bx / (2 * h);
+    A.cxp = d + bx / (2 * h);
+    A.cym = d - by / (2 * h);
+    A.cyp = d + by / (2 * h);
+    A.czm = d - bz / (2 * h);
+    A.czp = d + bz / (2 * h);
+    AT.c0 = A.c0;
+    AT.cxm = A.cxp; AT.cxp = A.cxm;
+    AT.cym = A.cyp; AT.cyp = A.cym;
+    AT.czm = A.czp; AT.czp = A.czm;
+    auto f = [](const DevOp &o, DevOp32 &o32) {
+        o32.c0 = (float)o.c0; o32.cxm = (float)o.cxm; o32.cxp = (float)o.cxp; o32.cym = (float)o.cym;
+        o32.cyp = (float)o.cyp; o32.czm = (float)o.czm; o32.czp = (float)o.czp;
+    };
+    f(A, A32);
+    f(AT, AT32);
+}
+
+extern "C" int tg_setup_operator(tg_op **op_out, int kind, const int64_t *dims, int ndim, const double *beta,
+                                 const double *mass, const void *coeffs, int coarse_factor, void *stream) {
+    TG_ARG(op_out != nullptr, "op_out is NULL");
+    *op_out = nullptr;
+    TG_ARG(dims != nullptr && ndim >= 1, "dims must give the grid size");
+    TG_ARG(coarse_factor == 2, "coarse_factor must be 2 (got %d)", coarse_factor);
+    TG_ARG(kind == TG_CD2D || kind == TG_CD3D || kind == TG_U1_4D || kind == TG_VARK2D, "unknown operator kind %d", kind);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = dims[0];
+    tg_op *op = new tg_op();
+    op->kind = kind;
+    op->N = (int)N;
+    int rc = TG_OK;
+    auto fail = [&](int code) {
+        delete op;
+        return code;
+    };
+    if (kind == TG_U1_4D) {
+        if (!(N >= 4 && N % 2 == 0 && N <= 64)) { set_error("lattice size L must be even, 4..64 (got %lld)", (long long)N); return fail(TG_BAD_ARG); }
+        if (!mass || !coeffs) { set_error("the lattice needs mass and links"); return fail(TG_BAD_ARG); }
+        op->cplx_ = true;
+        op->dim = 4;
+        op->Nc = (int)N / 2;
+        op->n = (int)(N * N * N * N);
+        op->nc = op->Nc * op->Nc * op->Nc * op->Nc;
+        op->mass = *mass;
+        const int V = op->n, Vc = op->nc, L = (int)N;
+        if ((rc = op->links.ensure((size_t)4 * V * 16)) || (rc = op->pw.ensure((size_t)V * 16)) ||
+            (rc = op->cst.ensure((size_t)9 * Vc * 16)))
+            return fail(rc);
+        if (cudaMemcpyAsync(op->links.p, coeffs, (size_t)4 * V * 16, cudaMemcpyDefault, s) != cudaSuccess) {
+            set_error("copy of the links failed");
+            return fail(TG_CUDA_ERROR);
+        }
+        launch_lattice_weights(grid_for(V, 8), s, op->links.as<cplx>(), L, op->pw.as<cplx>());
+        launch_lattice_coarse(grid_for(Vc, 8), s, op->links.as<cplx>(), op->pw.as<cplx>(), L,
+                                                               op->mass + 8.0, op->cst.as<cplx>());
+        DevOp A{};
+        A.kind = DK_U1; A.N = L; A.n = V; A.links = op->links.as<cplx>(); A.mdiag = op->mass + 8.0;
+        op->fine.A = op->fine.AT = A;
+        DevOp C{};
+        C.kind = DK_U1C; C.N = op->Nc; C.n = Vc; C.cst = op->cst.as<cplx>();
+        op->coarse.A = op->coarse.AT = C;
+    } else {
+        const int dim = kind == TG_CD3D ? 3 : 2;
+        if (!(N >= 3 && N % 2 == 1)) { set_error("grid size N must be odd and >= 3 (got %lld)", (long long)N); return fail(TG_BAD_ARG); }
+        const double nn = dim == 3 ? (double)N * N * N : (double)N * N;
+        if (nn >= 2147483647.0) { set_error("grid too large"); return fail(TG_BAD_ARG); }
+        if (!beta) { set_error("beta is NULL"); return fail(TG_BAD_ARG); }
+        op->dim = dim;
+        op->Nc = (int)(N - 1) / 2;
+        op->n = (int)nn;
+        op->nc = dim == 3 ? op->Nc * op->Nc * op->Nc : op->Nc * op->Nc;
+        for (int a = 0; a < dim && a < 3; ++a) op->beta[a] = beta[a];
+        if (kind == TG_VARK2D) {
+            if (!coeffs) { set_error("TG_VARK2D needs kappa"); return fail(TG_BAD_ARG); }
+            const int NP = (int)N + 2, NPc = op->Nc + 2;
+            const int n = op->n, nc = op->nc;
+            if ((rc = op->kappa.ensure((size_t)NP * NP * 8)) || (rc = op->kappa_c.ensure((size_t)NPc * NPc * 8)) ||
+                (rc = op->coef.ensure((size_t)5 * n * 8)) || (rc = op->coef32.ensure((size_t)5 * n * 4)) ||
+                (rc = op->coefT.ensure((size_t)5 * n * 8)) || (rc = op->coefT32.ensure((size_t)5 * n * 4)) ||
+                (rc = op->ccoef.ensure((size_t)5 * nc * 8)) || (rc = op->ccoef32.ensure((size_t)5 * nc * 4)) ||
+                (rc = op->ccoefT.ensure((size_t)5 * nc * 8)) || (rc = op->ccoefT32.ensure((size_t)5 * nc * 4)))
+                return fail(rc);
+            if (cudaMemcpyAsync(op->kappa.p, coeffs, (size_t)NP * NP * 8, cudaMemcpyDefault, s) != cudaSuccess) {
+                set_error("copy of kappa failed");
+                return fail(TG_CUDA_ERROR);
+            }
+            launch_inject_kappa(grid_for(NPc * NPc, 8), s, op->kappa.as<double>(), (int)N, op->kappa_c.as<double>());
+            launch_vark_coefs(grid_for(n, 8), s, op->kappa.as<double>(), (int)N, beta[0], 1, op->coef.as<double>(), op->coef32.as<float>());
+            launch_vark_coefs(grid_for(n, 8), s, op->kappa.as<double>(), (int)N, beta[0], -1, op->coefT.as<double>(), op->coefT32.as<float>());
+            launch_vark_coefs(grid_for(nc, 8), s, op->kappa_c.as<double>(), op->Nc, beta[0], 1, op->ccoef.as<double>(), op->ccoef32.as<float>());
+            launch_vark_coefs(grid_for(nc, 8), s, op->kappa_c.as<double>(), op->Nc, beta[0], -1, op->ccoefT.as<double>(), op->ccoefT32.as<float>());
+            DevOp A{};
+            A.kind = DK_VAR2D; A.N = (int)N; A.n = n;
+            DevOp AT = A, C = A, CT = A;
+            A.vc = op->coef.as<double>(); A.vc32 = op->coef32.as<float>();
+            AT.vc = op->coefT.as<double>(); AT.vc32 = op->coefT32.as<float>();
+            C.N = op->Nc; C.n = nc; C.vc = op->ccoef.as<double>(); C.vc32 = op->ccoef32.as<float>();
+            CT.N = op->Nc; CT.n = nc; CT.vc = op->ccoefT.as<double>(); CT.vc32 = op->ccoefT32.as<float>();
+            op->fine.A = A; op->fine.AT = AT; op->coarse.A = C; op->coarse.AT = CT;
+        } else {
+            DevOp A{}, AT{}, C{}, CT{};
+            A.kind = AT.kind = C.kind = CT.kind = (kind == TG_CD3D) ? DK_CD3D : DK_CD2D;
+            A.N = AT.N = (int)N;
+            A.n = AT.n = op->n;
+            C.N = CT.N = op->Nc;
+            C.n = CT.n = op->nc;
+            const_coefs(A, AT, op->fine.A32, op->fine.AT32, kind, (int)N, op->beta);
+            const_coefs(C, CT, op->coarse.A32, op->coarse.AT32, kind, op->Nc, op->beta);
+            op->fine.A = A; op->fine.AT = AT; op->coarse.A = C; op->coarse.AT = CT;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(cuda_status(e, "tg_setup_operator"));
+    *op_out = op;
+    return TG_OK;
+}
+
+extern "C" int tg_destroy_op(tg_op *op) {
+    delete op;
+    return TG_OK;
+}
+
+extern "C" int64_t tg_op_size(const tg_op *op, int level) {
+    if (!op) return -1;
+    return level == TG_COARSE ? op->nc : op->n;
+}
+
+extern "C" int tg_apply(const tg_op *op, int level, int transpose, int precision, const void *x, void *y, void *stream) {
+    TG_ARG(op && x && y, "NULL argument");
+    TG_ARG(level == TG_FINE || level == TG_COARSE, "bad level");
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevOp &A = pick(op, level, transpose);
+    const DevOp32 &A32 = pick32(op, level, transpose);
+    if (op->cplx_) {
+        TG_ARG(precision == TG_F64, "the lattice operator is complex128 only");
+        return launch_apply<cplx>(A, A32, (const cplx *)x, (cplx *)y, s);
+    }
+    if (precision == TG_F32_IR) return launch_apply<float>(A, A32, (const float *)x, (float *)y, s);
+    return launch_apply<double>(A, A32, (const double *)x, (double *)y, s);
+}
+
+// ============================================================================= transfer
+static int prolong_impl(const tg_op *op, const void *coarse, void *fine, int ncols, cudaStream_t s) {
+    for (int c = 0; c < ncols; ++c) {
+        if (op->cplx_) {
+            const cplx *uc = (const cplx *)coarse + (size_t)c * op->nc;
+            cplx *uf = (cplx *)fine + (size_t)c * op->n;
+            launch_prolong_lattice(grid_for(op->n, 8), s, uc, op->pw.as<cplx>(), op->N, uf);
+        } else {
+            const double *uc = (const double *)coarse + (size_t)c * op->nc;
+            double *uf = (double *)fine + (size_t)c * op->n;
+            if (op->dim == 3) launch_prolong3d(grid_for(op->n, 8), s, uc, op->Nc, uf);
+            else launch_prolong2d(grid_for(op->n, 8), s, uc, op->Nc, uf);
+        }
+        TG_LAUNCH_CHECK();
+    }
+    return TG_OK;
+}
+
+static int restrict_impl(const tg_op *op, const void *fine, void *coarse, int ncols, cudaStream_t s) {
+    for (int c = 0; c < ncols; ++c) {
+        if (op->cplx_) {
+            const cplx *uf = (const cplx *)fine + (size_t)c * op->n;
+            cplx *uc = (cplx *)coarse + (size_t)c * op->nc;
+            launch_restrict_lattice(grid_for(op->nc, 8), s, uf, op->pw.as<cplx>(), op->N, uc);
+        } else {
+            const double *uf = (const double *)fine + (size_t)c * op->n;
+            double *uc = (double *)coarse + (size_t)c * op->nc;
+            if (op->dim == 3) launch_restrict3d(grid_for(op->nc, 8), s, uf, op->N, uc);
+            else launch_restrict2d(grid_for(op->nc, 8), s, uf, op->N, uc);
+        }
+        TG_LAUNCH_CHECK();
+    }
+    return TG_OK;
+}
+
+extern "C" int tg_prolong(const tg_op *op, const void *coarse, void *fine, int ncols, void *stream) {
+    TG_ARG(op && coarse && fine && ncols >= 0, "bad argument");
+    return prolong_impl(op, coarse, fine, ncols, (cudaStream_t)stream);
+}
+
+extern "C" int tg_restrict(const tg_op *op, const void *fine, void *coarse, int ncols, void *stream) {
+    TG_ARG(op && coarse && fine && ncols >= 0, "bad argument");
+    return restrict_impl(op, fine, coarse, ncols, (cudaStream_t)stream);
+}
+
+// ============================================================================= deflation
+namespace tg {
+
+template <class T>
+static int build_defl(tg_op *op, int transpose, tg_defl *d, cudaStream_t s) {
+    const int n = op->n, kk = d->kk;
+    const DevOp &A = pick(op, TG_FINE, transpose);
+    const DevOp32 &A32 = pick32(op, TG_FINE, transpose);
+    size_t nb = (size_t)n * kk * sizeof(T);
+    size_t kb = (size_t)kk * kk * sizeof(T);
+    TG_CHECK(d->AY.ensure(nb));
+    TG_CHECK(d->Q.ensure(nb));
+    TG_CHECK(d->R.ensure(kb));
+    TG_CHECK(d->M.ensure(kb));
+    TG_CHECK(d->info.ensure(64));
+    TG_CHECK_CUDA(cudaMemsetAsync(d->info.p, 0, 64, s));
+    const T *Y = d->Y.as<T>();
+    T *AY = d->AY.as<T>();
+    for (int c = 0; c < kk; ++c) TG_CHECK(launch_apply<T>(A, A32, Y + (size_t)c * n, AY + (size_t)c * n, s));
+    int *info = d->info.as<int>();
+    if (d->proj == TG_PROJ_MINRES) {
+        TG_CHECK(cholqr2<T>(op, AY, kk, n, d->Q.as<T>(), d->R.as<T>(), d->M.as<T>(), info, s));
+    } else {
+        // V = orth(Y) (in Q), A V = A Y Ry^{-1} (in AV), H = V^H A V (in R), M = H^{-1}
+        DBuf Ry, Ryi, W;
+        TG_CHECK(Ry.ensure(kb));
+        TG_CHECK(Ryi.ensure(kb));
+        TG_CHECK(W.ensure(2 * kb));
+        TG_CHECK(d->AV.ensure(nb));
+        TG_CHECK(cholqr2<T>(op, Y, kk, n, d->Q.as<T>(), Ry.as<T>(), Ryi.as<T>(), info, s));
+        TG_CHECK(tsm<T>(AY, n, kk, Ryi.as<T>(), kk, kk, d->AV.as<T>(), n, n, s));
+        TG_CHECK(gram<T>(op, d->Q.as<T>(), d->AV.as<T>(), n, kk, n, 0, d->R.as<T>(), s));
+        launch_inverse<T>(d->R.as<T>(), kk, d->M.as<T>(), W.as<T>(), info + 2, s);
+        TG_LAUNCH_CHECK();
+        TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    int hinfo[3] = {0, 0, 0};
+    TG_CHECK_CUDA(cudaMemcpy(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost));
+    if (hinfo[0] || hinfo[1] || hinfo[2]) {
+        set_error("deflation basis is numerically rank deficient (Cholesky/pivot failure %d %d %d)", hinfo[0], hinfo[1], hinfo[2]);
+        return TG_BREAKDOWN;
+    }
+    if (d->precision == TG_F32_IR && !d->cplx_) {
+        // float copies: W (Q or V), B1 (Y or V), B2 (Q or A V)
+        TG_CHECK(d->W32.ensure((size_t)n * kk * 4));
+        TG_CHECK(d->B1_32.ensure((size_t)n * kk * 4));
+        TG_CHECK(d->B2_32.ensure((size_t)n * kk * 4));
+        const double *B1 = d->proj == TG_PROJ_MINRES ? (const double *)d->Y.p : (const double *)d->Q.p;
+        const double *B2 = d->proj == TG_PROJ_MINRES ? (const double *)d->Q.p : (const double *)d->AV.p;
+        launch_d2f(grid_for((int64_t)n * kk, 8), s, (const double *)d->Q.p, d->W32.as<float>(), (size_t)n * kk);
+        launch_d2f(grid_for((int64_t)n * kk, 8), s, B1, d->B1_32.as<float>(), (size_t)n * kk);
+        launch_d2f(grid_for((int64_t)n * kk, 8), s, B2, d->B2_32.as<float>(), (size_t)n * kk);
+        TG_LAUNCH_CHECK();
+    }
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+// One projection: c = W^H r; d = M c; x += B1 d; r -= B2 e (e = c for MinRes, d for Galerkin).
+template <class T>
+static int project_impl(tg_op *op, const tg_defl *df, const T *W, const T *B1, const T *B2, T *x, T *r, int n,
+                        cudaStream_t s) {
+    using D = typename ST<T>::D;
+    const int kk = df->kk;
+    TG_CHECK(red_ready(op, 0));
+    D *cvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192);
+    D *dvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192 + 4096);
+    TG_CHECK(gemv_t<T>(op, W, n, kk, r, n, cvec, s));
+    launch_small_gemv<D>(df->M.as<D>(), kk, cvec, dvec, s);
+    TG_LAUNCH_CHECK();
+    const D *e = df->proj == TG_PROJ_MINRES ? cvec : dvec;
+    k_proj_update<T><<<grid_for(n, 8), kThreads, 0, s>>>(B1, B2, n, kk, dvec, e, x, r, n);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+template <class T>
+static int project64(tg_op *op, const tg_defl *df, T *x, T *r, cudaStream_t s) {
+    const T *W = df->Q.as<T>();
+    const T *B1 = df->proj == TG_PROJ_MINRES ? df->Y.as<T>() : df->Q.as<T>();
+    const T *B2 = df->proj == TG_PROJ_MINRES ? df->Q.as<T>() : df->AV.as<T>();
+    return project_impl<T>(op, df, W, B1, B2, x, r, op->n, s);
+}
+
+}  // namespace tg
+
+static int defl_create(tg_op *op, int transpose, int kk, int proj, int precision, tg_defl **out) {
+    tg_defl *d = new tg_defl();
+    d->kk = kk;
+    d->n = op->n;
+    d->proj = proj;
+    d->precision = precision;
+    d->cplx_ = op->cplx_;
+    d->transposed = transpose != 0;
+    int rc = d->Y.ensure((size_t)op->n * kk * elem_size(op));
+    if (rc) {
+        delete d;
+        return rc;
+    }
+    *out = d;
+    return TG_OK;
+}
+
+extern "C" int tg_defl_from_basis(tg_op *op, int transpose, const void *Y, int k, int proj, int precision,
+                                  tg_defl **defl_out, void *stream) {
+    TG_ARG(op && Y && defl_out, "NULL argument");
+    TG_ARG(k >= 1 && k <= 128, "k must be in 1..128 (got %d)", k);
+    TG_ARG(proj == TG_PROJ_MINRES || proj == TG_PROJ_GALERKIN, "bad projection kind");
+    TG_ARG(precision == TG_F64 || precision == TG_F32_IR, "bad precision");
+    TG_ARG(!(op->cplx_ && precision == TG_F32_IR), "the lattice path is complex128 only");
+    cudaStream_t s = (cudaStream_t)stream;
+    *defl_out = nullptr;
+    tg_defl *d;
+    TG_CHECK(defl_create(op, transpose, k, proj, precision, &d));
+    int rc = cudaMemcpyAsync(d->Y.p, Y, (size_t)op->n * k * elem_size(op), cudaMemcpyDefault, s) == cudaSuccess
+                 ? TG_OK : TG_CUDA_ERROR;
+    if (!rc) rc = op->cplx_ ? build_defl<cplx>(op, transpose, d, s) : build_defl<double>(op, transpose, d, s);
+    if (rc) {
+        delete d;
+        return rc;
+    }
+    *defl_out = d;
+    return TG_OK;
+}
+
+extern "C" int tg_destroy_defl(tg_defl *d) {
+    delete d;
+    return TG_OK;
+}
+
+extern "C" int tg_defl_copy(const tg_defl *d, int what, void *dst, int *kk_out, void *stream) {
+    TG_ARG(d, "NULL deflation handle");
+    if (kk_out) *kk_out = d->kk;
+    if (!dst) return TG_OK;
+    const size_t es = d->cplx_ ? 16 : 8;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+        case 0: src = d->Y.p; bytes = (size_t)d->n * d->kk * es; break;
+        case 1: src = d->Q.p; bytes = (size_t)d->n * d->kk * es; break;
+        case 2: src = d->AY.p; bytes = (size_t)d->n * d->kk * es; break;
+        case 3: src = d->R.p; bytes = (size_t)d->kk * d->kk * es; break;
+        default: set_error("what must be 0..3"); return TG_BAD_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    TG_CHECK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+extern "C" int tg_project(const tg_op *op_c, const tg_defl *d, void *x, void *r, void *stream) {
+    TG_ARG(op_c && d && x && r, "NULL argument");
+    tg_op *op = const_cast<tg_op *>(op_c);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->cplx_) return project64<cplx>(op, d, (cplx *)x, (cplx *)r, s);
+    return project64<double>(op, d, (double *)x, (double *)r, s);
+}
+
+// ============================================================================= BiCGStab cycles
+namespace tg {
+
+template <class T> struct BiVecs {
+    T *rh, *p, *v, *s, *t;
+};
+
+template <class T>
+static int bicg_vecs(tg_op *op, int n, BiVecs<T> *w) {
+    size_t b = (size_t)n * sizeof(T);
+    TG_CHECK(wsx(op, S_RH, b));
+    TG_CHECK(wsx(op, S_P, b));
+    TG_CHECK(wsx(op, S_V, b));
+    TG_CHECK(wsx(op, S_S, b));
+    TG_CHECK(wsx(op, S_T, b));
+    w->rh = wsp<T>(op, S_RH);
+    w->p = wsp<T>(op, S_P);
+    w->v = wsp<T>(op, S_V);
+    w->s = wsp<T>(op, S_S);
+    w->t = wsp<T>(op, S_T);
+    return TG_OK;
+}
+
+struct CycleOut {
+    int mvps = 0;
+    int iters = 0;
+    int status = 0;
+    double rr = 0;
+};
+
+// One BiCGStab cycle on A e = r, updating x and r in place (device-resident scalars).
+template <class T>
+static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r, int n, double target2, int cap,
+                      CycleOut *out, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    BiVecs<T> w;
+    TG_CHECK(bicg_vecs<T>(op, n, &w));
+    const int g = grid_for(n, 8);
+    TG_CHECK(red_ready(op, (size_t)g * 4 * sizeof(D)));
+    D *part = wsp<D>(op, S_PART);
+    unsigned *tk = wsp<unsigned>(op, S_TICKET);
+    BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL));
+    k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st);
+    TG_LAUNCH_CHECK();
+    int chunk = 4;
+    int launched = 0;
+    BiState<D> h{};
+    while (true) {
+        for (int c = 0; c < chunk; ++c) {
+            k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st);
+            k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st);
+            k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st);
+            k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st);
+        }
+        TG_LAUNCH_CHECK();
+        launched += chunk;
+        TG_CHECK(readback(op, st, sizeof(BiState<D>), s));
+        memcpy(&h, op->pin.p, sizeof(h));
+        if (h.status != 0) break;
+        if (launched > cap + 8) {   // the cap test ends a cycle after `cap` products; this cannot trigger
+            set_error("BiCGStab cycle exceeded its product cap");
+            return TG_SYNC_TIMEOUT;
+        }
+        chunk = chunk < 32 ? chunk * 2 : 32;
+    }
+    out->mvps = h.mvps;
+    out->iters = h.iters;
+    out->status = h.status;
+    out->rr = h.rr;
+    return TG_OK;
+}
+
+static double cycle_tol(double rtol, double nr0, double nr, int icyc, int ncyc) {
+    double a = pow(rtol * nr0 / nr, 1.0 / (ncyc - icyc + 1));
+    double b = (nr0 / nr) * pow(rtol, (double)icyc / ncyc);
+    return a < b ? a : b;
+}
+
+struct SolveCfg {
+    double rtol;
+    int ncyc;
+    int restart_mvps;
+    int m3;
+    int64_t max_mvps;
+};
+
+static void hist_push(tg_stats *st, double relres, double rt, int64_t mvps) {
+    if (!st) return;
+    if (st->history && st->history_len < st->history_cap) {
+        double *h = st->history + 3 * (size_t)st->history_len;
+        h[0] = relres;
+        h[1] = rt;
+        h[2] = (double)mvps;
+    }
+    st->history_len += 1;
+}
+
+// r = b - A x (float64 / complex128); returns ||r||, ||b||.
+template <class T>
+static int true_residual(tg_op *op, const DevOp &A, const T *b, const T *x, T *r, double *nr, double *nb, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    const int n = A.n;
+    const int g = grid_for(n, 8);
+    TG_CHECK(red_ready(op, (size_t)g * 2 * sizeof(D)));
+    D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 2048);
+    k_residual<T><<<g, kThreads, 0, s>>>(A, b, x, r, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out);
+    TG_LAUNCH_CHECK();
+    TG_CHECK(readback(op, out, 2 * sizeof(D), s));
+    const D *h = reinterpret_cast<const D *>(op->pin.p);
+    *nr = sqrt(dnorm2(h[0]));
+    *nb = sqrt(dnorm2(h[1]));
+    return TG_OK;
+}
+
+// BiCGStab(ncyc)-Proj(k) in float64 / complex128 (Section 4.1, step 3).
+template <class T>
+static int solve_bicg64(tg_op *op, int transpose, const tg_defl *df, const T *b, T *x, const SolveCfg &cfg,
+                        tg_stats *st, cudaStream_t s) {
+    const DevOp &A = pick(op, TG_FINE, transpose);
+    const DevOp32 &A32 = pick32(op, TG_FINE, transpose);
+    const int n = op->n;
+    TG_CHECK(wsx(op, S_R64, (size_t)n * sizeof(T)));
+    T *r = wsp<T>(op, S_R64);
+    double nr, nb;
+    TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
+    int64_t mvps = 0;
+    int cyc = 0;
+    int status = TG_NOT_CONVERGED;
+    if (!std::isfinite(nr)) status = TG_NAN;
+    else if (nb == 0.0 || nr <= cfg.rtol * nb) status = TG_OK;
+    while (status == TG_NOT_CONVERGED) {
+        ++cyc;
+        if (cfg.ncyc && cyc > cfg.ncyc) break;
+        if (df && df->kk > 0) {                                    // step a
+            TG_CHECK(project64<T>(op, df, x, r, s));
+            double rr;
+            TG_CHECK(dot_host<T>(op, r, nullptr, n, &rr, nullptr, s));
+            nr = sqrt(rr);
+        }
+        double rt = cfg.ncyc ? cycle_tol(cfg.rtol, nb, nr, cyc, cfg.ncyc) : cfg.rtol * nb / nr;   // step b
+        hist_push(st, nr / nb, rt, mvps);
+        int64_t cap64 = cfg.max_mvps - mvps;
+        if (cfg.restart_mvps > 0 && cap64 > cfg.restart_mvps) cap64 = cfg.restart_mvps;
+        if (cap64 > INT_MAX / 2) cap64 = INT_MAX / 2;
+        CycleOut co;
+        TG_CHECK(bicg_cycle<T>(op, A, A32, x, r, n, (rt * nr) * (rt * nr), (int)cap64, &co, s));   // step c
+        mvps += co.mvps;
+        if (co.status == 4) { status = TG_NAN; break; }
+        TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
+        if (!std::isfinite(nr)) { status = TG_NAN; break; }
+        if (nr <= cfg.rtol * nb) { status = TG_OK; break; }        // step d
+        if (mvps >= cfg.max_mvps) break;
+        if (co.mvps == 0) { status = TG_BREAKDOWN; break; }   // no progress possible
+    }
+    if (st) {
+        st->mvps = mvps;
+        st->cycles = cyc;
+        st->relres = nb > 0 ? nr / nb : 0.0;
+        st->status = status;
+        st->vops = mvps * 7;
+    }
+    return status;
+}
+
+// float32 inner cycles with float64 refinement (real operators only).
+static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const double *b, double *x, const SolveCfg &cfg,
+                         tg_stats *st, cudaStream_t s) {
+    const DevOp &A = pick(op, TG_FINE, transpose);
+    const DevOp32 &A32 = pick32(op, TG_FINE, transpose);
+    const int n = op->n;
+    TG_CHECK(wsx(op, S_R64, (size_t)n * 8));
+    TG_CHECK(wsx(op, S_R32, (size_t)n * 4));
+    TG_CHECK(wsx(op, S_E32, (size_t)n * 4));
+    double *r = wsp<double>(op, S_R64);
+    float *r32 = wsp<float>(op, S_R32), *e32 = wsp<float>(op, S_E32);
+    double nr, nb;
+    TG_CHECK(true_residual<double>(op, A, b, x, r, &nr, &nb, s));
+    int64_t mvps = 0;
+    int cyc = 0;
+    int status = TG_NOT_CONVERGED;
+    if (!std::isfinite(nr)) status = TG_NAN;
+    else if (nb == 0.0 || nr <= cfg.rtol * nb) status = TG_OK;
+    const int g = grid_for(n, 8);
+    while (status == TG_NOT_CONVERGED) {
+        ++cyc;
+        if (cfg.ncyc && cyc > cfg.ncyc) break;
+        // correction equation A e = r, scaled so that ||r32|| = 1
+        launch_d2f_scaled(g, s, r, r32, n, 1.0 / nr);
+        TG_CHECK_CUDA(cudaMemsetAsync(e32, 0, (size_t)n * 4, s));
+        double scale = nr;
+        double nrel = 1.0;
+        if (df && df->kk > 0) {
+            TG_CHECK(project_impl<float>(op, df, df->W32.as<float>(), df->B1_32.as<float>(), df->B2_32.as<float>(), e32,
+                                         r32, n, s));
+            double rr;
+            TG_CHECK(dot_host<float>(op, r32, nullptr, n, &rr, nullptr, s));
+            nrel = sqrt(rr);
+        }
+        const double nrp = nrel * scale;    // residual norm after the projection
+        double rt = cfg.ncyc ? cycle_tol(cfg.rtol, nb, nrp, cyc, cfg.ncyc) : cfg.rtol * nb / nrp;
+        if (rt < 1e-6) rt = 1e-6;   // a float32 cycle cannot resolve more; refinement continues
+        hist_push(st, nrp / nb, rt, mvps);
+        int64_t cap64 = cfg.max_mvps - mvps;
+        if (cfg.restart_mvps > 0 && cap64 > cfg.restart_mvps) cap64 = cfg.restart_mvps;
+        if (cap64 > INT_MAX / 2) cap64 = INT_MAX / 2;
+        CycleOut co;
+        TG_CHECK(bicg_cycle<float>(op, A, A32, e32, r32, n, (rt * nrel) * (rt * nrel), (int)cap64, &co, s));
+        mvps += co.mvps;
+        launch_add_f2d_scaled(g, s, x, e32, n, scale);
+        TG_LAUNCH_CHECK();
+        TG_CHECK(true_residual<double>(op, A, b, x, r, &nr, &nb, s));
+        if (!std::isfinite(nr)) { status = TG_NAN; break; }
+        if (nr <= cfg.rtol * nb) { status = TG_OK; break; }
+        if (mvps >= cfg.max_mvps) break;
+        if (co.mvps == 0) { status = TG_BREAKDOWN; break; }
+    }
+    if (st) {
+        st->mvps = mvps;
+        st->cycles = cyc;
+        st->relres = nb > 0 ? nr / nb : 0.0;
+        st->status = status;
+        st->vops = mvps * 7;
+    }
+    return status;
+}
+
+// ----------------------------------------------------------------------------- Arnoldi (CGS2)
+// Extends V (ld ldv, columns 0..j orthonormal) by column j+1 = A v_j orthogonalised; writes
+// Hbar column j (ld ldh).  Two classical Gram-Schmidt passes as tall-skinny products.
+template <class T>
+static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int n, int j, T *H, int ldh,
+                        cudaStream_t s) {
+    using D = typename ST<T>::D;
+    T *w = V + (size_t)(j + 1) * ldv;
+    TG_CHECK(launch_apply<T>(A, A32, V + (size_t)j * ldv, w, s));
+    TG_CHECK(red_ready(op, 0));
+    D *h1 = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384);
+    D *h2 = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384 + 4096);
+    D *nrm = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
+    const int g = grid_for(n, 8);
+    TG_CHECK(gemv_t<T>(op, V, ldv, j + 1, w, n, h1, s));
+    k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h1, -1.0, w, n);
+    TG_LAUNCH_CHECK();
+    TG_CHECK(gemv_t<T>(op, V, ldv, j + 1, w, n, h2, s));
+    k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h2, -1.0, w, n);
+    TG_LAUNCH_CHECK();
+    int gd = grid_for(n, 4);
+    k_dot<T><<<gd, kThreads, 0, s>>>(w, nullptr, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm);
+    TG_LAUNCH_CHECK();
+    k_arnoldi_finish<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, reinterpret_cast<double *>(nrm) + 4);
+    TG_LAUNCH_CHECK();
+    k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, reinterpret_cast<double *>(nrm) + 4);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+// GMRES(m)-Proj(k) (Section 2.2) in float64 / complex128.
+template <class T>
+static int solve_gmres64(tg_op *op, int transpose, const tg_defl *df, const T *b, T *x, const SolveCfg &cfg,
+                         tg_stats *st, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    const DevOp &A = pick(op, TG_FINE, transpose);
+    const DevOp32 &A32 = pick32(op, TG_FINE, transpose);
+    const int n = op->n, m = cfg.m3;
+    const int ldh = m + 1;
+    TG_CHECK(wsx(op, S_R64, (size_t)n * sizeof(T)));
+    TG_CHECK(wsx(op, S_FV, (size_t)n * (m + 1) * sizeof(T)));
+    TG_CHECK(wsx(op, S_FH, (size_t)(m + 1) * m * sizeof(T)));
+    TG_CHECK(wsx(op, S_FCS, (size_t)(m + 1) * sizeof(D)));
+    TG_CHECK(wsx(op, S_FSN, (size_t)(m + 1) * sizeof(D)));
+    TG_CHECK(wsx(op, S_FG, (size_t)(m + 1) * sizeof(D)));
+    TG_CHECK(wsx(op, S_FY, (size_t)(m + 1) * sizeof(D)));
+    TG_CHECK(wsx(op, S_FSTATE, sizeof(GivensState)));
+    T *r = wsp<T>(op, S_R64);
+    T *V = wsp<T>(op, S_FV);
+    D *H = wsp<D>(op, S_FH);
+    GivensState *gs = wsp<GivensState>(op, S_FSTATE);
+    double nr, nb;
+    TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
+    int64_t mvps = 0;
+    int cyc = 0;
+    int status = TG_NOT_CONVERGED;
+    if (!std::isfinite(nr)) status = TG_NAN;
+    else if (nb == 0.0 || nr <= cfg.rtol * nb) status = TG_OK;
+    while (status == TG_NOT_CONVERGED && mvps < cfg.max_mvps) {
+        ++cyc;
+        if (df && df->kk > 0) {
+            TG_CHECK(project64<T>(op, df, x, r, s));
+            double rr;
+            TG_CHECK(dot_host<T>(op, r, nullptr, n, &rr, nullptr, s));
+            nr = sqrt(rr);
+        }
+        hist_push(st, nr / nb, 0.0, mvps);
+        // v_0 = r / ||r||; g = ||r|| e_1
+        TG_CHECK_CUDA(cudaMemcpyAsync(V, r, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        GivensState h0{};
+        h0.target = cfg.rtol * nb;
+        h0.resid = nr;
+        double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
+        double hinv = 1.0 / nr;
+        TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(gs, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemsetAsync(wsp<D>(op, S_FG), 0, (size_t)(m + 1) * sizeof(D), s));
+        D g0{};
+        memcpy(&g0, &nr, sizeof(double));
+        TG_CHECK_CUDA(cudaMemcpyAsync(wsp<D>(op, S_FG), &g0, sizeof(D), cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemsetAsync(H, 0, (size_t)(m + 1) * m * sizeof(D), s));
+        k_scale_by<T><<<grid_for(n, 8), kThreads, 0, s>>>(V, n, inv);
+        TG_LAUNCH_CHECK();
+        int steps = 0;
+        const int mm = (int)((cfg.max_mvps - mvps) < m ? (cfg.max_mvps - mvps) : m);
+        for (int j = 0; j < mm; ++j) {
+            TG_CHECK(arnoldi_step<T>(op, A, A32, V, n, n, j, reinterpret_cast<T *>(H), ldh, s));
+            launch_givens_step<D>(H, ldh, j, wsp<D>(op, S_FCS), wsp<D>(op, S_FSN), wsp<D>(op, S_FG), gs, s);
+            TG_LAUNCH_CHECK();
+            TG_CHECK(readback(op, gs, sizeof(GivensState), s));
+            GivensState hg;
+            memcpy(&hg, op->pin.p, sizeof(hg));
+            steps = hg.steps;
+            if (hg.done) break;
+        }
+        mvps += steps;
+        launch_givens_solve<D>(H, ldh, wsp<D>(op, S_FG), wsp<D>(op, S_FY), gs, s);
+        k_gemv_n<T><<<grid_for(n, 8), kThreads, 0, s>>>(V, n, steps, wsp<D>(op, S_FY), 1.0, x, n);
+        TG_LAUNCH_CHECK();
+        TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
+        if (!std::isfinite(nr)) { status = TG_NAN; break; }
+        if (nr <= cfg.rtol * nb) { status = TG_OK; break; }
+    }
+    if (st) {
+        st->mvps = mvps;
+        st->cycles = cyc;
+        st->relres = nb > 0 ? nr / nb : 0.0;
+        st->status = status;
+    }
+    return status;
+}
+
+}  // namespace tg
+
+extern "C" int tg_solve_proj(tg_op *op, const tg_defl *defl, int method, int precision, const void *b, void *x,
+                             int nrhs, double rtol, int ncyc, int restart_mvps, int m3, int64_t max_mvps,
+                             tg_stats *stats, void *stream) {
+    TG_ARG(op && b && x, "NULL argument");
+    TG_ARG(nrhs >= 1, "nrhs must be >= 1");
+    TG_ARG(method == TG_BICGSTAB || method == TG_GMRES, "bad method");
+    TG_ARG(precision == TG_F64 || precision == TG_F32_IR, "bad precision");
+    TG_ARG(!(op->cplx_ && precision == TG_F32_IR), "the lattice path is complex128 only");
+    TG_ARG(!(method == TG_GMRES && precision == TG_F32_IR), "GMRES-Proj runs in float64");
+    TG_ARG(rtol > 0 && rtol < 1, "rtol must be in (0, 1)");
+    TG_ARG(ncyc >= 0 && restart_mvps >= 0, "ncyc and restart_mvps must be >= 0");
+    TG_ARG(ncyc > 0 || restart_mvps > 0 || method == TG_GMRES, "fixed-length restarting needs restart_mvps > 0");
+    TG_ARG(method != TG_GMRES || (m3 >= 1 && m3 <= 128), "m3 must be in 1..128");
+    TG_ARG(max_mvps > 0, "max_mvps must be > 0");
+    TG_ARG(!defl || (defl->n == op->n && !defl->transposed), "deflation handle does not match this operator");
+    TG_ARG(!defl || precision == TG_F64 || defl->precision == TG_F32_IR,
+           "the deflation handle was built without float32 copies (precision TG_F64)");
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveCfg cfg{rtol, ncyc, restart_mvps, m3, max_mvps};
+    int worst = TG_OK;
+    const size_t es = elem_size(op);
+    for (int c = 0; c < nrhs; ++c) {
+        tg_stats *st = stats ? stats + c : nullptr;
+        if (st) {
+            st->history_len = 0;
+            st->coarse_mvps = 0;
+        }
+        const char *bc = (const char *)b + (size_t)c * op->n * es;
+        char *xc = (char *)x + (size_t)c * op->n * es;
+        int rc;
+        if (method == TG_GMRES) {
+            rc = op->cplx_ ? solve_gmres64<cplx>(op, 0, defl, (const cplx *)bc, (cplx *)xc, cfg, st, s)
+                           : solve_gmres64<double>(op, 0, defl, (const double *)bc, (double *)xc, cfg, st, s);
+        } else if (precision == TG_F32_IR) {
+            rc = solve_bicg_ir(op, 0, defl, (const double *)bc, (double *)xc, cfg, st, s);
+        } else {
+            rc = op->cplx_ ? solve_bicg64<cplx>(op, 0, defl, (const cplx *)bc, (cplx *)xc, cfg, st, s)
+                           : solve_bicg64<double>(op, 0, defl, (const double *)bc, (double *)xc, cfg, st, s);
+        }
+        if (rc != TG_OK && worst == TG_OK) worst = rc;
+        if (rc == TG_CUDA_ERROR || rc == TG_OOM || rc == TG_BAD_ARG) return rc;
+    }
+    return worst;
+}
+
+// ============================================================================= GMRES-DR
+namespace tg {
+
+template <class T>
+static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int k, int nev, double rtolev,
+                        double rtol, int max_cycles, void *xc_out, tg_defl **defl_out, int proj, int precision,
+                        tg_stats *stats, cudaStream_t s) {
+    using D = T;
+    const DevOp &A = pick(op, TG_COARSE, transpose);
+    const DevOp32 &A32 = pick32(op, TG_COARSE, transpose);
+    const int nc = op->nc;
+    const int ldh = m + 1;
+    const size_t es = sizeof(T);
+    TG_CHECK(wsx(op, S_GV, (size_t)nc * (m + 1) * es));
+    TG_CHECK(wsx(op, S_GV2, (size_t)nc * (m + 1) * es));
+    TG_CHECK(wsx(op, S_GH, (size_t)ldh * m * es));
+    TG_CHECK(wsx(op, S_GH2, (size_t)ldh * m * es));
+    TG_CHECK(wsx(op, S_GC, (size_t)(m + 1) * es));
+    TG_CHECK(wsx(op, S_GX, (size_t)nc * es));
+    TG_CHECK(wsx(op, S_GD, (size_t)(m + 1) * es));
+    TG_CHECK(wsx(op, S_GRES, (size_t)(m + 1) * es));
+    TG_CHECK(wsx(op, S_GZ, (size_t)(m + 1) * es));
+    TG_CHECK(wsx(op, S_GP, (size_t)(m + 1) * (m + 2) * es));
+    TG_CHECK(wsx(op, S_GCN, (size_t)(m + 2) * es));
+    TG_CHECK(wsx(op, S_GTHETA, (size_t)2 * m * 8));
+    TG_CHECK(wsx(op, S_GWR, (size_t)m * 8));
+    TG_CHECK(wsx(op, S_GWI, (size_t)m * 8));
+    TG_CHECK(wsx(op, S_GORD, (size_t)m * 4));
+    TG_CHECK(wsx(op, S_GERES, (size_t)m * 8));
+    TG_CHECK(wsx(op, S_GWORK, ((size_t)(m + 1) * m + 2 * (size_t)m * m + 3 * (size_t)m + 4) * es));
+    TG_CHECK(wsx(op, S_GY, (size_t)m * m * 16));
+    TG_CHECK(wsx(op, S_GG, (size_t)m * m * 16));
+    TG_CHECK(wsx(op, S_GINFO, sizeof(GdrInfo)));
+    TG_CHECK(wsx(op, S_GB, (size_t)nc * es));
+    TG_CHECK(wsx(op, S_GTMP, (size_t)(m + 2) * es));
+    T *V = wsp<T>(op, S_GV), *V2 = wsp<T>(op, S_GV2);
+    T *H = wsp<T>(op, S_GH), *H2 = wsp<T>(op, S_GH2);
+    T *c = wsp<T>(op, S_GC), *xc = wsp<T>(op, S_GX), *bc = wsp<T>(op, S_GB);
+    // b_c = restrict(b); v_0 = b_c / ||b_c||; x_c = 0
+    TG_CHECK(restrict_impl(op, b_fine, bc, 1, s));
+    double nbc2;
+    TG_CHECK(dot_host<T>(op, bc, nullptr, nc, &nbc2, nullptr, s));
+    const double nbc = sqrt(nbc2);
+    TG_ARG(nbc > 0 && std::isfinite(nbc), "restricted right-hand side is zero or not finite");
+    TG_CHECK_CUDA(cudaMemcpyAsync(V, bc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
+    double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
+    double hinv = 1.0 / nbc;
+    TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
+    k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, inv);
+    TG_CHECK_CUDA(cudaMemsetAsync(xc, 0, (size_t)nc * es, s));
+    TG_CHECK_CUDA(cudaMemsetAsync(H, 0, (size_t)ldh * m * es, s));
+    TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * es, s));
+    T c0{};
+    memcpy(&c0, &nbc, sizeof(double));
+    TG_CHECK_CUDA(cudaMemcpyAsync(c, &c0, sizeof(T), cudaMemcpyHostToDevice, s));
+    int j0 = 0;
+    int cycles = 0;
+    int64_t cmvps = 0;
+    GdrInfo info{};
+    int kk = k;
+    bool converged = false;
+    while (true) {
+        ++cycles;
+        for (int j = j0; j < m; ++j) TG_CHECK(arnoldi_step<T>(op, A, A32, V, nc, nc, j, H, ldh, s));
+        cmvps += m - j0;
+        TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * es, s));
+        GdrArgs<T> a;
+        a.H = H; a.ldh = ldh; a.c = c; a.m = m; a.k = k; a.nev = nev; a.rtolev = rtolev;
+        a.d = wsp<T>(op, S_GD); a.res = wsp<T>(op, S_GRES); a.z = wsp<T>(op, S_GZ);
+        a.theta = wsp<double>(op, S_GTHETA); a.wr = wsp<double>(op, S_GWR); a.wi = wsp<double>(op, S_GWI);
+        a.order = wsp<int>(op, S_GORD); a.eres = wsp<double>(op, S_GERES); a.P = wsp<T>(op, S_GP);
+        a.Hnew = H2; a.cnew = wsp<T>(op, S_GCN); a.work = wsp<T>(op, S_GWORK);
+        a.ywork = wsp<cplx>(op, S_GY); a.gwork = wsp<cplx>(op, S_GG); a.info = wsp<GdrInfo>(op, S_GINFO);
+        launch_gmresdr_restart<T>(a, s);
+        TG_LAUNCH_CHECK();
+        // x_c += V_m d
+        k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, m, a.d, 1.0, xc, nc);
+        TG_LAUNCH_CHECK();
+        TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
+        memcpy(&info, op->pin.p, sizeof(info));
+        kk = info.kk;
+        if (info.status != 0) {
+            set_error("harmonic Ritz QR iteration did not converge");
+            return TG_NOT_CONVERGED;
+        }
+        if (!std::isfinite(info.rnorm)) return TG_NAN;
+        converged = info.rnorm <= rtol * nbc && info.nconv >= (nev < kk ? nev : kk);
+        if (converged || cycles >= max_cycles) break;
+        // restart: V_{k+1} = V_{m+1} P_{k+1}; Hbar = Hnew; c = cnew
+        TG_CHECK(tsm<T>(V, nc, m + 1, a.P, m + 1, kk + 1, V2, nc, nc, s));
+        std::swap(V, V2);
+        std::swap(H, H2);
+        TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * es, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(c, a.cnew, (size_t)(kk + 1) * es, cudaMemcpyDeviceToDevice, s));
+        // re-orthogonalise v_{k+1} against V_k and normalise
+        {
+            using DD = typename ST<T>::D;
+            T *w = V + (size_t)kk * nc;
+            DD *h1 = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384);
+            DD *nrm = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
+            TG_CHECK(gemv_t<T>(op, V, nc, kk, w, nc, h1, s));
+            k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, kk, h1, -1.0, w, nc);
+            k_dot<T><<<grid_for(nc, 4), kThreads, 0, s>>>(w, nullptr, nc, wsp<DD>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm);
+            launch_inv_sqrt(s, reinterpret_cast<const double *>(nrm), reinterpret_cast<double *>(nrm) + 4);
+            k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(w, nc, reinterpret_cast<double *>(nrm) + 4);
+            TG_LAUNCH_CHECK();
+        }
+        j0 = kk;
+    }
+    // the V_m P_k basis of the final cycle, prolonged; x_c out
+    if (stats) {
+        stats->coarse_mvps = cmvps;
+        stats->cycles = cycles;
+        stats->coarse_relres = info.rnorm / nbc;
+        stats->kk = kk;
+        stats->eig_converged = info.nconv;
+        stats->status = converged ? TG_OK : TG_NOT_CONVERGED;
+    }
+    if (xc_out) TG_CHECK_CUDA(cudaMemcpyAsync(xc_out, xc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
+    if (defl_out) {
+        DBuf Yc;
+        TG_CHECK(Yc.ensure((size_t)nc * kk * es));
+        TG_CHECK(tsm<T>(V, nc, m, wsp<T>(op, S_GP), m + 1, kk, Yc.as<T>(), nc, nc, s));
+        tg_defl *d;
+        TG_CHECK(defl_create(op, transpose, kk, proj, precision, &d));
+        int rc = prolong_impl(op, Yc.p, d->Y.p, kk, s);
+        if (!rc) rc = build_defl<T>(op, transpose, d, s);
+        if (rc) {
+            delete d;
+            return rc;
+        }
+        *defl_out = d;
+    }
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    return converged ? TG_OK : TG_NOT_CONVERGED;
+}
+
+}  // namespace tg
+
+extern "C" int tg_coarse_gmresdr(tg_op *op, int transpose, const void *b_fine, int m, int k, int nev, double rtolev,
+                                 double rtol, int max_cycles, void *xc_out, tg_defl **defl_out, int proj,
+                                 int precision, tg_stats *stats, void *stream) {
+    TG_ARG(op && b_fine, "NULL argument");
+    TG_ARG(m >= 2 && m <= kMaxM && k >= 1 && k < m - 1, "need 1 <= k < m - 1 and m <= %d (m=%d, k=%d)", kMaxM, m, k);
+    TG_ARG(m < op->nc, "m must be smaller than the coarse problem size");
+    TG_ARG(nev >= 0 && nev <= k, "nev must be in 0..k");
+    TG_ARG(max_cycles >= 1, "max_cycles must be >= 1");
+    TG_ARG(proj == TG_PROJ_MINRES || proj == TG_PROJ_GALERKIN, "bad projection kind");
+    TG_ARG(precision == TG_F64 || precision == TG_F32_IR, "bad precision");
+    TG_ARG(!(op->cplx_ && precision == TG_F32_IR), "the lattice path is complex128 only");
+    if (defl_out) *defl_out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->cplx_)
+        return gmresdr_impl<cplx>(op, transpose, b_fine, m, k, nev, rtolev, rtol, max_cycles, xc_out, defl_out, proj,
+                                  precision, stats, s);
+    return gmresdr_impl<double>(op, transpose, b_fine, m, k, nev, rtolev, rtol, max_cycles, xc_out, defl_out, proj,
+                                precision, stats, s);
+}
+
+// ============================================================================= adjoint
+extern "C" int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *dkappa, void *stream) {
+    TG_ARG(op && x && lambda && dkappa, "NULL argument");
+    TG_ARG(op->kind == TG_VARK2D, "the kappa gradient needs a TG_VARK2D operator");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int NP = op->N + 2;
+    launch_kappa_grad(grid_for(NP * NP, 8), s, (const double *)x, (const double *)lambda, op->N,
+                                                          (double *)dkappa);
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+extern "C" int tg_adjoint_solve(tg_op *op, const tg_defl *defl_left, const void *g, void *lambda, const void *x,
+                                void *dkappa, double rtol, int ncyc, int restart_mvps, int precision, tg_stats *stats,
+                                void *stream) {
+    TG_ARG(op && g && lambda, "NULL argument");
+    TG_ARG(!op->cplx_, "the adjoint form is for the real operators");
+    TG_ARG(!defl_left || (defl_left->transposed && defl_left->n == op->n), "defl_left must be built with transpose = 1");
+    TG_ARG(ncyc > 0 || restart_mvps > 0, "fixed-length restarting needs restart_mvps > 0");
+    TG_ARG(precision == TG_F64 || precision == TG_F32_IR, "bad precision");
+    TG_ARG(!defl_left || precision == TG_F64 || defl_left->precision == TG_F32_IR, "defl_left lacks float32 copies");
+    TG_ARG(!dkappa || x, "the gradient needs x");
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveCfg cfg{rtol, ncyc, restart_mvps, 0, (int64_t)1 << 40};
+    int rc = precision == TG_F32_IR
+                 ? solve_bicg_ir(op, 1, defl_left, (const double *)g, (double *)lambda, cfg, stats, s)
+                 : solve_bicg64<double>(op, 1, defl_left, (const double *)g, (double *)lambda, cfg, stats, s);
+    if (rc != TG_OK) return rc;
+    if (dkappa && op->kind == TG_VARK2D) TG_CHECK(tg_kappa_gradient(op, x, lambda, dkappa, stream));
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+// ============================================================================= test hook
+extern "C" int tg_harmonic_ritz(const void *Hbar, int m, int k, int complex_, void *theta_out, void *basis_out,
+                                void *eres_out, int *kk_out, void *stream) {
+    TG_ARG(Hbar && theta_out && basis_out && kk_out, "NULL argument");
+    TG_ARG(m >= 2 && m <= kMaxM && k >= 1 && k < m, "need 1 <= k < m <= %d", kMaxM);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = complex_ ? 16 : 8;
+    DBuf c, d, res, z, P, Hn, cn, th, wr, wi, ord, er, work, yw, gw, inf;
+    int rc;
+    if ((rc = c.ensure((m + 1) * es)) || (rc = d.ensure((m + 1) * es)) || (rc = res.ensure((m + 1) * es)) ||
+        (rc = z.ensure((m + 1) * es)) || (rc = P.ensure((size_t)(m + 1) * (m + 2) * es)) ||
+        (rc = Hn.ensure((size_t)(m + 1) * m * es)) || (rc = cn.ensure((m + 2) * es)) || (rc = th.ensure(2 * m * 8)) ||
+        (rc = wr.ensure(m * 8)) || (rc = wi.ensure(m * 8)) || (rc = ord.ensure(m * 4)) || (rc = er.ensure(m * 8)) ||
+        (rc = work.ensure(((size_t)(m + 1) * m + 2 * (size_t)m * m + 3 * m + 4) * es)) ||
+        (rc = yw.ensure((size_t)m * m * 16)) || (rc = gw.ensure((size_t)m * m * 16)) || (rc = inf.ensure(sizeof(GdrInfo))))
+        return rc;
+    TG_CHECK_CUDA(cudaMemsetAsync(c.p, 0, (m + 1) * es, s));
+    double one = 1.0;
+    TG_CHECK_CUDA(cudaMemcpyAsync(c.p, &one, 8, cudaMemcpyHostToDevice, s));
+    auto launch = [&](auto tag) -> int {
+        using T = decltype(tag);
+        GdrArgs<T> a;
+        a.H = (const T *)Hbar; a.ldh = m + 1; a.c = c.as<T>(); a.m = m; a.k = k; a.nev = k; a.rtolev = 0.0;
+        a.d = d.as<T>(); a.res = res.as<T>(); a.z = z.as<T>(); a.theta = th.as<double>(); a.wr = wr.as<double>();
+        a.wi = wi.as<double>(); a.order = ord.as<int>(); a.eres = er.as<double>(); a.P = P.as<T>(); a.Hnew = Hn.as<T>();
+        a.cnew = cn.as<T>(); a.work = work.as<T>(); a.ywork = yw.as<cplx>(); a.gwork = gw.as<cplx>();
+        a.info = inf.as<GdrInfo>();
+        launch_gmresdr_restart<T>(a, s);
+        TG_LAUNCH_CHECK();
+        return TG_OK;
+    };
+    TG_CHECK(complex_ ? launch(cplx{}) : launch(double{}));
+    GdrInfo info;
+    TG_CHECK_CUDA(cudaMemcpyAsync(&info, inf.p, sizeof(info), cudaMemcpyDeviceToHost, s));
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    *kk_out = info.kk;
+    TG_CHECK_CUDA(cudaMemcpyAsync(theta_out, th.p, 2 * m * 8, cudaMemcpyDefault, s));
+    TG_CHECK_CUDA(cudaMemcpy2DAsync(basis_out, m * es, P.p, (m + 1) * es, m * es, info.kk, cudaMemcpyDefault, s));
+    if (eres_out) TG_CHECK_CUDA(cudaMemcpyAsync(eres_out, er.p, info.kk * 8, cudaMemcpyDefault, s));
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    return info.status ? TG_NOT_CONVERGED : TG_OK;
+}

@@ -1,0 +1,332 @@
+// Shared device types and helpers of the tg library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include "tg.h"
+
+namespace tg {
+
+// ----------------------------------------------------------------------------- status
+void set_error(const char *fmt, ...);
+int cuda_status(cudaError_t e, const char *where);
+
+#define TG_CHECK_CUDA(expr)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) return ::tg::cuda_status(_e, #expr);                \
+    } while (0)
+#define TG_CHECK(expr)                                                             \
+    do {                                                                           \
+        int _s = (expr);                                                           \
+        if (_s != TG_OK) return _s;                                                \
+    } while (0)
+#define TG_LAUNCH_CHECK() TG_CHECK_CUDA(cudaGetLastError())
+
+// ----------------------------------------------------------------------------- complex
+struct __align__(16) cplx {
+    double re, im;
+};
+__host__ __device__ __forceinline__ cplx mkc(double a, double b) { return cplx{a, b}; }
+__host__ __device__ __forceinline__ cplx operator+(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cplx operator-(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cplx operator-(cplx a) { return {-a.re, -a.im}; }
+__host__ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cplx operator*(double s, cplx a) { return {s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cplx operator*(cplx a, double s) { return {s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cplx conj(cplx a) { return {a.re, -a.im}; }
+__host__ __device__ __forceinline__ double abs2(cplx a) { return a.re * a.re + a.im * a.im; }
+__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+    // Smith's algorithm
+    if (fabs(b.re) >= fabs(b.im)) {
+        double r = b.im / b.re, d = b.re + b.im * r;
+        return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+    }
+    double r = b.re / b.im, d = b.im + b.re * r;
+    return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+__host__ __device__ __forceinline__ double cabs_(cplx a) { return hypot(a.re, a.im); }
+
+// ----------------------------------------------------------------------------- scalar traits
+// Vector element type T; D = type of an inner product (double for real T, cplx for
+// complex T).  conj_mul(a, b) = conj(a) * b.
+template <class T> struct ST;
+template <> struct ST<double> {
+    using D = double;
+    __host__ __device__ static __forceinline__ double zero() { return 0.0; }
+    __host__ __device__ static __forceinline__ double conj_mul(double a, double b) { return a * b; }
+    __host__ __device__ static __forceinline__ double fma_cm(double a, double b, double acc) { return fma(a, b, acc); }
+    __host__ __device__ static __forceinline__ double scale(double s, double a) { return s * a; }
+    __host__ __device__ static __forceinline__ double from(double d) { return d; }
+};
+template <> struct ST<float> {
+    using D = double;
+    __host__ __device__ static __forceinline__ float zero() { return 0.0f; }
+    __host__ __device__ static __forceinline__ float conj_mul(float a, float b) { return a * b; }
+    __host__ __device__ static __forceinline__ float fma_cm(float a, float b, float acc) { return fmaf(a, b, acc); }
+    __host__ __device__ static __forceinline__ float scale(float s, float a) { return s * a; }
+    __host__ __device__ static __forceinline__ float from(double d) { return (float)d; }
+};
+template <> struct ST<cplx> {
+    using D = cplx;
+    __host__ __device__ static __forceinline__ cplx zero() { return {0.0, 0.0}; }
+    __host__ __device__ static __forceinline__ cplx conj_mul(cplx a, cplx b) {
+        return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+    }
+    __host__ __device__ static __forceinline__ cplx fma_cm(cplx a, cplx b, cplx acc) {
+        return {fma(a.re, b.re, fma(a.im, b.im, acc.re)), fma(a.re, b.im, fma(-a.im, b.re, acc.im))};
+    }
+    __host__ __device__ static __forceinline__ cplx from(cplx d) { return d; }
+};
+
+// Dot accumulators: per-thread partial in P, block/grid totals in D.
+template <class T> struct Acc { using P = T; };
+__device__ __forceinline__ double to_d(double a) { return a; }
+__device__ __forceinline__ double to_d(float a) { return (double)a; }
+__device__ __forceinline__ cplx to_d(cplx a) { return a; }
+
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_down(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ cplx shfl_down(cplx v, int o) {
+    return {__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o)};
+}
+__device__ __forceinline__ double dadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float dadd(float a, float b) { return a + b; }
+__device__ __forceinline__ cplx dadd(cplx a, cplx b) { return a + b; }
+
+template <class P> __device__ __forceinline__ P warp_sum(P v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = dadd(v, shfl_down(v, o));
+    return v;
+}
+
+// ----------------------------------------------------------------------------- operators
+enum DevKind { DK_CD2D = 0, DK_CD3D = 1, DK_U1 = 2, DK_VAR2D = 3, DK_U1C = 4 };
+
+// Device-side description of one operator level (passed by value to kernels).
+struct DevOp {
+    int kind;
+    int N;          // points per axis (grids) or L (lattice)
+    int n;          // unknowns (sites); the host rejects n >= 2^31
+    // constant-coefficient stencil (cd2d / cd3d), already including 1/h^2 and beta/(2h)
+    double c0, cxm, cxp, cym, cyp, czm, czp;
+    // variable coefficient: coefficient arrays [5][n]: diag, west, east, south, north
+    // (stored as the coefficient of u_nb in (A u)_ij, so y = sum coef * u)
+    const double *vc;
+    const float *vc32;
+    // lattice
+    const cplx *links;     // [4][V]
+    double mdiag;          // m + 8
+    // coarse lattice: [9][Vc]: diag, fwd mu=0..3, bwd mu=0..3
+    const cplx *cst;
+};
+
+// float copies of the constant coefficients
+struct DevOp32 {
+    float c0, cxm, cxp, cym, cyp, czm, czp;
+};
+
+__host__ __device__ __forceinline__ int lat_shift(int x, int L, int mu, int sign) {
+    int stride = 1;
+    for (int a = 0; a < mu; ++a) stride *= L;
+    int c = (x / stride) % L;
+    int cn = c + sign;
+    if (cn < 0) cn += L;
+    if (cn >= L) cn -= L;
+    return x + (cn - c) * stride;
+}
+
+// (A u)(idx) for real grids, u read through the functor `ld(j)`.
+template <class T, class LD>
+__device__ __forceinline__ T apply_real(const DevOp &op, const DevOp32 &o32, int idx, LD ld);
+
+template <class LD>
+__device__ __forceinline__ double apply_real_d(const DevOp &op, int idx, LD ld) {
+    const int N = op.N;
+    if (op.kind == DK_CD2D) {
+        int i = idx % N, j = idx / N;
+        double y = op.c0 * ld(idx);
+        if (i > 0) y = fma(op.cxm, ld(idx - 1), y);
+        if (i < N - 1) y = fma(op.cxp, ld(idx + 1), y);
+        if (j > 0) y = fma(op.cym, ld(idx - N), y);
+        if (j < N - 1) y = fma(op.cyp, ld(idx + N), y);
+        return y;
+    } else if (op.kind == DK_CD3D) {
+        int NN = N * N;
+        int i = idx % N, j = (idx / N) % N, k = idx / NN;
+        double y = op.c0 * ld(idx);
+        if (i > 0) y = fma(op.cxm, ld(idx - 1), y);
+        if (i < N - 1) y = fma(op.cxp, ld(idx + 1), y);
+        if (j > 0) y = fma(op.cym, ld(idx - N), y);
+        if (j < N - 1) y = fma(op.cyp, ld(idx + N), y);
+        if (k > 0) y = fma(op.czm, ld(idx - NN), y);
+        if (k < N - 1) y = fma(op.czp, ld(idx + NN), y);
+        return y;
+    } else {  // DK_VAR2D
+        int i = idx % N, j = idx / N;
+        const int n = op.n;
+        const double *c = op.vc;
+        double y = c[idx] * ld(idx);
+        if (i > 0) y = fma(c[n + idx], ld(idx - 1), y);
+        if (i < N - 1) y = fma(c[2 * n + idx], ld(idx + 1), y);
+        if (j > 0) y = fma(c[3 * n + idx], ld(idx - N), y);
+        if (j < N - 1) y = fma(c[4 * n + idx], ld(idx + N), y);
+        return y;
+    }
+}
+
+template <class LD>
+__device__ __forceinline__ float apply_real_f(const DevOp &op, const DevOp32 &o, int idx, LD ld) {
+    const int N = op.N;
+    if (op.kind == DK_CD2D) {
+        int i = idx % N, j = idx / N;
+        float y = o.c0 * ld(idx);
+        if (i > 0) y = fmaf(o.cxm, ld(idx - 1), y);
+        if (i < N - 1) y = fmaf(o.cxp, ld(idx + 1), y);
+        if (j > 0) y = fmaf(o.cym, ld(idx - N), y);
+        if (j < N - 1) y = fmaf(o.cyp, ld(idx + N), y);
+        return y;
+    } else if (op.kind == DK_CD3D) {
+        int NN = N * N;
+        int i = idx % N, j = (idx / N) % N, k = idx / NN;
+        float y = o.c0 * ld(idx);
+        if (i > 0) y = fmaf(o.cxm, ld(idx - 1), y);
+        if (i < N - 1) y = fmaf(o.cxp, ld(idx + 1), y);
+        if (j > 0) y = fmaf(o.cym, ld(idx - N), y);
+        if (j < N - 1) y = fmaf(o.cyp, ld(idx + N), y);
+        if (k > 0) y = fmaf(o.czm, ld(idx - NN), y);
+        if (k < N - 1) y = fmaf(o.czp, ld(idx + NN), y);
+        return y;
+    } else {
+        int i = idx % N, j = idx / N;
+        const int n = op.n;
+        const float *c = op.vc32;
+        float y = c[idx] * ld(idx);
+        if (i > 0) y = fmaf(c[n + idx], ld(idx - 1), y);
+        if (i < N - 1) y = fmaf(c[2 * n + idx], ld(idx + 1), y);
+        if (j > 0) y = fmaf(c[3 * n + idx], ld(idx - N), y);
+        if (j < N - 1) y = fmaf(c[4 * n + idx], ld(idx + N), y);
+        return y;
+    }
+}
+
+template <class LD>
+__device__ __forceinline__ cplx apply_cplx(const DevOp &op, int x, LD ld) {
+    const int L = op.N;
+    if (op.kind == DK_U1) {
+        const int V = op.n;
+        cplx y = op.mdiag * ld(x);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            int xp = lat_shift(x, L, mu, +1), xm = lat_shift(x, L, mu, -1);
+            cplx uf = op.links[mu * V + x];
+            cplx ub = op.links[mu * V + xm];
+            y = y - uf * ld(xp);
+            y = y - conj(ub) * ld(xm);
+        }
+        return y;
+    } else {  // DK_U1C: general 9-point coarse stencil
+        const int V = op.n;
+        cplx y = op.cst[x] * ld(x);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            int xp = lat_shift(x, L, mu, +1), xm = lat_shift(x, L, mu, -1);
+            y = y + op.cst[(1 + mu) * V + x] * ld(xp);
+            y = y + op.cst[(5 + mu) * V + x] * ld(xm);
+        }
+        return y;
+    }
+}
+
+// Generic entry used by templated kernels.
+template <class T> struct Apply;
+template <> struct Apply<double> {
+    template <class LD>
+    __device__ static __forceinline__ double at(const DevOp &op, const DevOp32 &, int idx, LD ld) {
+        return apply_real_d(op, idx, ld);
+    }
+};
+template <> struct Apply<float> {
+    template <class LD>
+    __device__ static __forceinline__ float at(const DevOp &op, const DevOp32 &o, int idx, LD ld) {
+        return apply_real_f(op, o, idx, ld);
+    }
+};
+template <> struct Apply<cplx> {
+    template <class LD>
+    __device__ static __forceinline__ cplx at(const DevOp &op, const DevOp32 &, int idx, LD ld) {
+        return apply_cplx(op, idx, ld);
+    }
+};
+
+// ----------------------------------------------------------------------------- launch shape
+constexpr int kThreads = 256;
+int num_sms();
+// Blocks for a grid-stride pass over n elements: a multiple of the SM count, at most
+// `per_sm` resident blocks per SM, and no more blocks than there is work for.
+int grid_for(int64_t n, int per_sm = 8);
+
+// ----------------------------------------------------------------------------- reductions
+// Deterministic two-level reduction: every block writes its partial sums (in a fixed
+// order over its grid-stride elements) to `part[block * nd + d]`; the last block to
+// finish (atomic ticket) adds the partials in block order and runs the finaliser.
+struct RedSlot {
+    void *part;          // nblocks * nd * sizeof(D)
+    unsigned *ticket;    // one counter, zero between uses
+};
+
+template <class P, class D, int ND>
+__device__ __forceinline__ void block_reduce_store(P (&v)[ND], D *part, D *red_smem) {
+    // red_smem: (blockDim.x/32) * ND entries.  Warp sums in the per-thread type P,
+    // block sums in D, both in a fixed order.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        P w = warp_sum(v[d]);
+        if (lane == 0) red_smem[warp * ND + d] = to_d(w);
+    }
+    __syncthreads();
+    if (threadIdx.x < ND) {
+        const int d = threadIdx.x;
+        D s = red_smem[d];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = dadd(s, red_smem[w * ND + d]);
+        part[(size_t)blockIdx.x * ND + d] = s;
+    }
+}
+
+// Returns true in exactly one block (the last); that block's threads then see all partials.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return am_last;
+}
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ cplx ldcg(const cplx *p) {
+    double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return {v.x, v.y};
+}
+
+// In the last block: totals[d] = sum over blocks of part[b * ND + d], fixed order.
+template <class D, int ND>
+__device__ __forceinline__ void final_sum(const D *part, D *totals_smem, unsigned *ticket) {
+    if (threadIdx.x < ND) {
+        const int d = threadIdx.x;
+        D s = ldcg(part + d);
+        for (int b = 1; b < (int)gridDim.x; ++b) s = dadd(s, ldcg(part + (size_t)b * ND + d));
+        totals_smem[d] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+}  // namespace tg

@@ -1,0 +1,524 @@
+// Templated device kernels of the tg library: stencil products, the BiCGStab iteration,
+// residuals, tall-skinny products and reductions.  T is the vector element type:
+// double (float64 path), float (inner iteration of the float32 + refinement path) or
+// cplx (complex128 lattice).
+#pragma once
+
+#include "tg_common.cuh"
+
+namespace tg {
+
+// ----------------------------------------------------------------------------- elementwise
+__device__ __forceinline__ double axpy(double a, double x, double y) { return fma(a, x, y); }
+__device__ __forceinline__ float axpy(float a, float x, float y) { return fmaf(a, x, y); }
+__device__ __forceinline__ cplx axpy(cplx a, cplx x, cplx y) {
+    return {fma(a.re, x.re, fma(-a.im, x.im, y.re)), fma(a.re, x.im, fma(a.im, x.re, y.im))};
+}
+__device__ __forceinline__ double sub(double a, double b) { return a - b; }
+__device__ __forceinline__ float sub(float a, float b) { return a - b; }
+__device__ __forceinline__ cplx sub(cplx a, cplx b) { return a - b; }
+__device__ __forceinline__ double neg(double a) { return -a; }
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ cplx neg(cplx a) { return -a; }
+
+// kernel-side scalar of a reduction result
+template <class T> struct KS;
+template <> struct KS<double> { __device__ static double of(double d) { return d; } };
+template <> struct KS<float> { __device__ static float of(double d) { return (float)d; } };
+template <> struct KS<cplx> { __device__ static cplx of(cplx d) { return d; } };
+
+__host__ __device__ __forceinline__ double dabs(double a) { return fabs(a); }
+__host__ __device__ __forceinline__ double dabs(cplx a) { return hypot(a.re, a.im); }
+__host__ __device__ __forceinline__ double dreal(double a) { return a; }
+__host__ __device__ __forceinline__ double dreal(cplx a) { return a.re; }
+__host__ __device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
+__host__ __device__ __forceinline__ cplx ddiv(cplx a, cplx b) { return cdiv(a, b); }
+__host__ __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
+__host__ __device__ __forceinline__ cplx dmul(cplx a, cplx b) { return a * b; }
+__host__ __device__ __forceinline__ double dsub(double a, double b) { return a - b; }
+__host__ __device__ __forceinline__ cplx dsub(cplx a, cplx b) { return a - b; }
+__host__ __device__ __forceinline__ bool dfinite(double a) { return isfinite(a); }
+__host__ __device__ __forceinline__ bool dfinite(cplx a) { return isfinite(a.re) && isfinite(a.im); }
+
+template <class T> struct Part { using P = T; };          // per-thread partial type
+template <> struct Part<float> { using P = float; };
+
+// ----------------------------------------------------------------------------- y = A x
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_apply(DevOp op, DevOp32 o32, const T *__restrict__ x,
+                                                     T *__restrict__ y) {
+    const int n = op.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = Apply<T>::at(op, o32, i, [&](int j) { return x[j]; });
+}
+
+// ----------------------------------------------------------------------------- norms
+// out[0] = ||a||^2 (and out[1] = <a, b> when b != nullptr); deterministic.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_dot(const T *__restrict__ a, const T *__restrict__ b, int n,
+                                                   typename ST<T>::D *part, unsigned *ticket,
+                                                   typename ST<T>::D *out) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    __shared__ D red[(kThreads / 32) * 2];
+    __shared__ D tot[2];
+    P acc[2] = {ST<T>::zero(), ST<T>::zero()};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T ai = a[i];
+        acc[0] = ST<T>::fma_cm(ai, ai, acc[0]);
+        if (b) acc[1] = ST<T>::fma_cm(ai, b[i], acc[1]);
+    }
+    block_reduce_store<P, D, 2>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 2>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            out[0] = tot[0];
+            out[1] = tot[1];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- true residual
+// r = b - A x in the outer precision (double / cplx); out[0] = ||r||^2, out[1] = ||b||^2.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_residual(DevOp op, const T *__restrict__ b, const T *__restrict__ x,
+                                                        T *__restrict__ r, typename ST<T>::D *part,
+                                                        unsigned *ticket, typename ST<T>::D *out) {
+    using D = typename ST<T>::D;
+    __shared__ D red[(kThreads / 32) * 2];
+    __shared__ D tot[2];
+    DevOp32 o32{};
+    T acc[2] = {ST<T>::zero(), ST<T>::zero()};
+    const int n = op.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T ax = Apply<T>::at(op, o32, i, [&](int j) { return x[j]; });
+        T bi = b[i];
+        T ri = sub(bi, ax);
+        r[i] = ri;
+        acc[0] = ST<T>::fma_cm(ri, ri, acc[0]);
+        acc[1] = ST<T>::fma_cm(bi, bi, acc[1]);
+    }
+    block_reduce_store<T, D, 2>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 2>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            out[0] = tot[0];
+            out[1] = tot[1];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- BiCGStab
+// Device-resident state of one BiCGStab cycle.  Kernels of an iteration read the
+// scalars they need from here; the last block of each reduction writes the next ones,
+// so the host only launches and, once per batch of iterations, reads `status`.
+template <class D>
+struct BiState {
+    D rho;          // <r_hat, r> for the current r
+    D alpha, omega, beta;
+    D rho_next;
+    double rr;      // ||r||^2 (last full step)
+    double ss;      // ||s||^2 (last half step)
+    double target2; // (rticyc ||r_cycle_start||)^2
+    int mvps;       // operator applications in this cycle
+    int cap;        // at most this many (INT_MAX: no cap)
+    int iters;
+    int status;     // 0 running, 1 converged, 2 breakdown, 3 capped, 4 NaN
+    int half;       // a half-step exit is pending: the t-kernel skips, the x-kernel applies omega = 0
+    int pending;    // status to take when the pending half step is applied
+};
+
+constexpr double kTiny = 1e-300;
+
+// r_hat = r, p = r; rho = <r, r>.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_bi_init(const T *__restrict__ r, T *__restrict__ rh,
+                                                       T *__restrict__ p, int n, double target2, int cap,
+                                                       typename ST<T>::D *part, unsigned *ticket,
+                                                       BiState<typename ST<T>::D> *st) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    __shared__ D red[(kThreads / 32)];
+    __shared__ D tot[1];
+    P acc[1] = {ST<T>::zero()};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T ri = r[i];
+        rh[i] = ri;
+        p[i] = ri;
+        acc[0] = ST<T>::fma_cm(ri, ri, acc[0]);
+    }
+    block_reduce_store<P, D, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            D rho = tot[0];
+            st->rho = rho;
+            st->rr = dreal(rho);
+            st->ss = 0.0;
+            st->target2 = target2;
+            st->mvps = 0;
+            st->cap = cap;
+            st->iters = 0;
+            st->half = 0;
+            st->pending = 0;
+            st->alpha = st->omega = st->beta = st->rho_next = rho;
+            if (!dfinite(rho)) st->status = 4;
+            else if (dreal(rho) <= target2) st->status = 1;
+            else if (dabs(rho) < kTiny) st->status = 2;
+            else st->status = 0;
+        }
+    }
+}
+
+// v = A p; sigma = <r_hat, v>; alpha = rho / sigma.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_bi_v(DevOp op, DevOp32 o32, const T *__restrict__ p,
+                                                    const T *__restrict__ rh, T *__restrict__ v,
+                                                    typename ST<T>::D *part, unsigned *ticket,
+                                                    BiState<typename ST<T>::D> *st) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    if (st->status != 0) return;
+    __shared__ D red[(kThreads / 32)];
+    __shared__ D tot[1];
+    P acc[1] = {ST<T>::zero()};
+    const int n = op.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T y = Apply<T>::at(op, o32, i, [&](int j) { return p[j]; });
+        v[i] = y;
+        acc[0] = ST<T>::fma_cm(rh[i], y, acc[0]);
+    }
+    block_reduce_store<P, D, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            D sigma = tot[0];
+            st->mvps += 1;
+            if (!dfinite(sigma)) st->status = 4;
+            else if (dabs(sigma) < kTiny) st->status = 2;
+            else st->alpha = ddiv(st->rho, sigma);
+        }
+    }
+}
+
+// s = r - alpha v; ||s||^2; half-step convergence / cap test.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_bi_s(const T *__restrict__ r, const T *__restrict__ v,
+                                                    T *__restrict__ s, int n, typename ST<T>::D *part,
+                                                    unsigned *ticket, BiState<typename ST<T>::D> *st) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    if (st->status != 0) return;
+    __shared__ D red[(kThreads / 32)];
+    __shared__ D tot[1];
+    const T malpha = neg(KS<T>::of(st->alpha));
+    P acc[1] = {ST<T>::zero()};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T si = axpy(malpha, v[i], r[i]);
+        s[i] = si;
+        acc[0] = ST<T>::fma_cm(si, si, acc[0]);
+    }
+    block_reduce_store<P, D, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            double ss = dreal(tot[0]);
+            st->ss = ss;
+            if (!isfinite(ss)) st->status = 4;
+            else if (ss <= st->target2) { st->half = 1; st->pending = 1; }
+            else if (st->mvps >= st->cap) { st->half = 1; st->pending = 3; }
+        }
+    }
+}
+
+// t = A s; <t,s>, <t,t>, <r_hat,s>, <r_hat,t>; omega = <t,s>/<t,t>;
+// rho_next = <r_hat, s - omega t> = <r_hat,s> - omega <r_hat,t>; beta = (rho_next/rho)(alpha/omega).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_bi_t(DevOp op, DevOp32 o32, const T *__restrict__ s,
+                                                    const T *__restrict__ rh, T *__restrict__ t,
+                                                    typename ST<T>::D *part, unsigned *ticket,
+                                                    BiState<typename ST<T>::D> *st) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    if (st->status != 0 || st->half) return;
+    __shared__ D red[(kThreads / 32) * 4];
+    __shared__ D tot[4];
+    P acc[4] = {ST<T>::zero(), ST<T>::zero(), ST<T>::zero(), ST<T>::zero()};
+    const int n = op.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T ti = Apply<T>::at(op, o32, i, [&](int j) { return s[j]; });
+        t[i] = ti;
+        T si = s[i], ri = rh[i];
+        acc[0] = ST<T>::fma_cm(ti, si, acc[0]);
+        acc[1] = ST<T>::fma_cm(ti, ti, acc[1]);
+        acc[2] = ST<T>::fma_cm(ri, si, acc[2]);
+        acc[3] = ST<T>::fma_cm(ri, ti, acc[3]);
+    }
+    block_reduce_store<P, D, 4>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 4>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            st->mvps += 1;
+            double tt = dreal(tot[1]);
+            if (!isfinite(tt) || !dfinite(tot[0])) {
+                st->status = 4;
+            } else if (tt < kTiny) {
+                st->half = 1;
+                st->pending = 2;
+            } else {
+                D omega = ddiv(tot[0], D(tot[1]));
+                st->omega = omega;
+                D rn = dsub(tot[2], dmul(omega, tot[3]));
+                st->rho_next = rn;
+                if (dabs(omega) >= kTiny)
+                    st->beta = dmul(ddiv(rn, st->rho), ddiv(st->alpha, omega));
+            }
+        }
+    }
+}
+
+// Full step: x += alpha p + omega s; r = s - omega t; p = r + beta (p - omega v); ||r||^2.
+// Pending half step: x += alpha p; r = s.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restrict__ r, T *__restrict__ p,
+                                                    const T *__restrict__ s, const T *__restrict__ t,
+                                                    const T *__restrict__ v, int n, typename ST<T>::D *part,
+                                                    unsigned *ticket, BiState<typename ST<T>::D> *st) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    if (st->status != 0) return;
+    __shared__ D red[(kThreads / 32)];
+    __shared__ D tot[1];
+    const T alpha = KS<T>::of(st->alpha);
+    if (st->half) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            x[i] = axpy(alpha, p[i], x[i]);
+            r[i] = s[i];
+        }
+        if (last_block(ticket)) {
+            if (threadIdx.x == 0) {
+                *ticket = 0u;
+                st->rr = st->ss;
+                st->status = st->pending;
+                st->iters += 1;
+            }
+        }
+        return;
+    }
+    const T omega = KS<T>::of(st->omega);
+    const T momega = neg(omega);
+    const T beta = KS<T>::of(st->beta);
+    P acc[1] = {ST<T>::zero()};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        T si = s[i];
+        T pi = p[i];
+        x[i] = axpy(omega, si, axpy(alpha, pi, x[i]));
+        T ri = axpy(momega, t[i], si);
+        r[i] = ri;
+        p[i] = axpy(beta, axpy(momega, v[i], pi), ri);
+        acc[0] = ST<T>::fma_cm(ri, ri, acc[0]);
+    }
+    block_reduce_store<P, D, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            double rr = dreal(tot[0]);
+            st->rr = rr;
+            st->iters += 1;
+            st->rho = st->rho_next;
+            if (!isfinite(rr)) st->status = 4;
+            else if (rr <= st->target2) st->status = 1;
+            else if (dabs(st->omega) < kTiny) st->status = 2;
+            else if (dabs(st->rho_next) < kTiny) st->status = 2;
+            else if (st->mvps >= st->cap) st->status = 3;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- tall-skinny
+// Partial products of h = V^H w over row tiles: part[block][c] = sum over the block's rows
+// of conj(V[row, c]) w[row], c < ncol.  One warp per column group, 32-row tiles.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ V, size_t ldv, int ncol,
+                                                           const T *__restrict__ w, int n,
+                                                           typename ST<T>::D *part) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    constexpr int kMaxPerWarp = 17;   // 8 warps x 17 columns >= 129
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    P acc[kMaxPerWarp];
+#pragma unroll
+    for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = ST<T>::zero();
+    for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
+        const int row = row0 + lane;
+        if (row < n) {
+            const T wi = w[row];
+#pragma unroll
+            for (int q = 0; q < kMaxPerWarp; ++q) {
+                const int c = warp + 8 * q;
+                if (c < ncol) acc[q] = ST<T>::fma_cm(V[(size_t)c * ldv + row], wi, acc[q]);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxPerWarp; ++q) {
+        const int c = warp + 8 * q;
+        P s = warp_sum(acc[q]);
+        if (lane == 0 && c < ncol) part[(size_t)blockIdx.x * ncol + c] = to_d(s);
+    }
+}
+
+// out[e] (+)= scale * sum_b part[b * nent + e], in block order (deterministic).
+// mode 0: out = sum; mode 1: out += sum.
+template <class D>
+__global__ void k_sum_part(const D *__restrict__ part, int nblk, int nent, D *out, int mode) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+        D s = part[e];
+        for (int b = 1; b < nblk; ++b) s = dadd(s, part[(size_t)b * nent + e]);
+        out[e] = mode ? dadd(out[e], s) : s;
+    }
+}
+
+// w[row] += sign * sum_c V[row, c] h[c]   (h: device, D type, ncol <= 129)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gemv_n(const T *__restrict__ V, size_t ldv, int ncol,
+                                                      const typename ST<T>::D *__restrict__ h, double sign,
+                                                      T *__restrict__ w, int n) {
+    using D = typename ST<T>::D;
+    __shared__ D hs[130];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        T acc = ST<T>::zero();
+        for (int c = 0; c < ncol; ++c) acc = axpy(KS<T>::of(hs[c]), V[(size_t)c * ldv + row], acc);
+        w[row] = sign > 0 ? dadd(w[row], acc) : sub(w[row], acc);
+    }
+}
+
+// Projection update: x += B1 d; r -= B2 e.  (B1, B2: n x k; d, e: device D vectors.)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_proj_update(const T *__restrict__ B1, const T *__restrict__ B2,
+                                                           size_t ld, int k,
+                                                           const typename ST<T>::D *__restrict__ d,
+                                                           const typename ST<T>::D *__restrict__ e,
+                                                           T *__restrict__ x, T *__restrict__ r, int n) {
+    using D = typename ST<T>::D;
+    __shared__ D ds[130], es[130];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        ds[c] = d[c];
+        es[c] = e[c];
+    }
+    __syncthreads();
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        T ax = ST<T>::zero(), ar = ST<T>::zero();
+        for (int c = 0; c < k; ++c) {
+            ax = axpy(KS<T>::of(ds[c]), B1[(size_t)c * ld + row], ax);
+            ar = axpy(KS<T>::of(es[c]), B2[(size_t)c * ld + row], ar);
+        }
+        x[row] = dadd(x[row], ax);
+        r[row] = sub(r[row], ar);
+    }
+}
+
+// Out (n x q) = In (n x p) * S (p x q), S column-major with leading dimension lds.
+// 32-row tiles of In staged in shared memory (column-major [p][32]).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_tsm(const T *__restrict__ In, size_t ldi, int p,
+                                                   const T *__restrict__ S, int lds, int q,
+                                                   T *__restrict__ Out, size_t ldo, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tile = reinterpret_cast<T *>(smem_raw);
+    for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * p; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;
+            const int row = row0 + r;
+            tile[c * 32 + r] = row < n ? In[(size_t)c * ldi + row] : ST<T>::zero();
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < 32 * q; o += blockDim.x) {
+            const int r = o & 31, c = o >> 5;
+            const int row = row0 + r;
+            T acc = ST<T>::zero();
+            const T *sc = S + (size_t)c * lds;
+            for (int i = 0; i < p; ++i) acc = axpy(sc[i], tile[i * 32 + r], acc);
+            if (row < n) Out[(size_t)c * ldo + row] = acc;
+        }
+    }
+}
+
+// Partial Gram products G = A^H B over 32-row tiles: part[block][i + j*k] for the
+// entries the block owns (all k*k; sym = 1 computes i <= j only and leaves the rest 0).
+template <class T, int kEPT>
+__global__ void __launch_bounds__(kThreads) k_gram_part(const T *__restrict__ A, const T *__restrict__ B,
+                                                         size_t ld, int k, int n, int sym,
+                                                         typename ST<T>::D *part) {
+    // kEPT entries per thread: kThreads * kEPT >= k * k
+    using D = typename ST<T>::D;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *ta = reinterpret_cast<T *>(smem_raw);
+    T *tb = ta + 32 * k;
+    D acc[kEPT];
+#pragma unroll
+    for (int e = 0; e < kEPT; ++e) acc[e] = D{};
+    const int nent = k * k;
+    for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;
+            const int row = row0 + r;
+            ta[c * 32 + r] = row < n ? A[(size_t)c * ld + row] : ST<T>::zero();
+            tb[c * 32 + r] = row < n ? B[(size_t)c * ld + row] : ST<T>::zero();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kEPT; ++q) {
+            const int e = threadIdx.x + q * kThreads;
+            if (e < nent) {
+                const int i = e % k, j = e / k;
+                if (!sym || i <= j) {
+                    typename Part<T>::P s = ST<T>::zero();
+                    for (int r = 0; r < 32; ++r) s = ST<T>::fma_cm(ta[i * 32 + r], tb[j * 32 + r], s);
+                    acc[q] = dadd(acc[q], to_d(s));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kEPT; ++q) {
+        const int e = threadIdx.x + q * kThreads;
+        if (e < nent) part[(size_t)blockIdx.x * nent + e] = acc[q];
+    }
+}
+
+// ----------------------------------------------------------------------------- misc vector ops
+__device__ __forceinline__ double scal(double s, double a) { return s * a; }
+__device__ __forceinline__ float scal(double s, float a) { return (float)s * a; }
+__device__ __forceinline__ cplx scal(double s, cplx a) { return s * a; }
+
+template <class T>
+__global__ void k_scale_by(T *__restrict__ w, int n, const double *__restrict__ inv) {
+    // w *= inv[0]
+    const double s = inv[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = scal(s, w[i]);
+}
+
+// Hbar column j of an Arnoldi step: H[i] = h1[i] + h2[i] (i <= j), H[j+1] = ||w||,
+// inv[0] = 1 / ||w|| (0 if w vanished: an invariant subspace was found).
+template <class T>
+__global__ void k_arnoldi_finish(const typename ST<T>::D *h1, const typename ST<T>::D *h2,
+                                 const typename ST<T>::D *nrm2, int j, T *Hcol, double *inv) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) Hcol[i] = dadd(h1[i], h2[i]);
+    if (threadIdx.x == 0) {
+        const double nn = sqrt(dreal(nrm2[0]));
+        T hv = ST<T>::zero();
+        *reinterpret_cast<double *>(&hv) = nn;
+        Hcol[j + 1] = hv;
+        inv[0] = nn > 0 ? 1.0 / nn : 0.0;
+    }
+}
+
+
+
+
+}  // namespace tg

@@ -1,0 +1,1059 @@
+// Single-CTA float64 kernels for the small dense problems of the method:
+//   - the GMRES-DR restart step (Section 2.1): least squares min ||c - Hbar d||, harmonic
+//     Ritz pairs of Hbar (eigenpairs of H_m + |h_{m+1,m}|^2 f e_m^T, H_m^H f = e_m),
+//     selection of the k smallest, orthonormal basis P_k of their span, the restart
+//     matrices P_{k+1}, Hbar_k = P_{k+1}^H Hbar P_k, c_k = P_{k+1}^H (c - Hbar d);
+//   - Cholesky and triangular inverse for CholQR2 (the projection set-up);
+//   - Gauss-Jordan inverse of the Galerkin matrix H = V^H A V;
+//   - incremental Givens least squares for GMRES(m) cycles;
+//   - the k x k solve of each projection.
+// The eigenvalue algorithms are the textbook ones (Golub & Van Loan, Matrix Computations,
+// Sections 7.4-7.6): Householder reduction to Hessenberg form, Francis double-shift QR
+// (real matrices, real Schur form with 2 x 2 blocks for complex pairs) or Wilkinson
+// single-shift QR (complex matrices), with accumulated Schur vectors, and eigenvectors
+// by back substitution on the (quasi-)triangular factor.  One thread block of
+// kSmallThreads threads; every matrix lives in a global scratch area (L1/L2 resident).
+#include <cfloat>
+#include <cmath>
+#include "tg_small.cuh"
+
+namespace tg {
+
+namespace {
+
+constexpr double kEps = DBL_EPSILON;
+
+__device__ __forceinline__ double sq(double a) { return a * a; }
+
+// ----------------------------------------------------------------------------- generic helpers
+template <class T> struct Cx;
+template <> struct Cx<double> {
+    __device__ static double cj(double a) { return a; }
+    __device__ static double ab2(double a) { return a * a; }
+    __device__ static double mul(double a, double b) { return a * b; }
+    __device__ static double div(double a, double b) { return a / b; }
+    __device__ static double re(double a) { return a; }
+    __device__ static double zero() { return 0.0; }
+    __device__ static double one() { return 1.0; }
+    __device__ static double sc(double s, double a) { return s * a; }
+};
+template <> struct Cx<cplx> {
+    __device__ static cplx cj(cplx a) { return conj(a); }
+    __device__ static double ab2(cplx a) { return abs2(a); }
+    __device__ static cplx mul(cplx a, cplx b) { return a * b; }
+    __device__ static cplx div(cplx a, cplx b) { return cdiv(a, b); }
+    __device__ static double re(cplx a) { return a.re; }
+    __device__ static cplx zero() { return {0.0, 0.0}; }
+    __device__ static cplx one() { return {1.0, 0.0}; }
+    __device__ static cplx sc(double s, cplx a) { return s * a; }
+};
+
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ cplx add(cplx a, cplx b) { return a + b; }
+__device__ __forceinline__ double subt(double a, double b) { return a - b; }
+__device__ __forceinline__ cplx subt(cplx a, cplx b) { return a - b; }
+
+// Householder vector for x[0..len-1] (strided): v with v[0] = 1 and tau such that
+// (I - tau v v^H) x = beta e_1.  Written to v[], returns tau (0 if x is already beta e_1).
+template <class T>
+__device__ T house(const T *x, int stride, int len, T *v, T *beta_out) {
+    double nrm2 = 0.0;
+    for (int i = 1; i < len; ++i) nrm2 += Cx<T>::ab2(x[i * stride]);
+    T x0 = x[0];
+    if (nrm2 == 0.0) {
+        v[0] = Cx<T>::one();
+        for (int i = 1; i < len; ++i) v[i] = Cx<T>::zero();
+        *beta_out = x0;
+        return Cx<T>::zero();
+    }
+    double a0 = sqrt(Cx<T>::ab2(x0));
+    double alpha = sqrt(Cx<T>::ab2(x0) + nrm2);
+    // beta = -phase(x0) * alpha
+    T ph = a0 > 0 ? Cx<T>::sc(1.0 / a0, x0) : Cx<T>::one();
+    T beta = Cx<T>::sc(-alpha, ph);
+    T v0 = subt(x0, beta);                       // x0 + phase * alpha
+    for (int i = 1; i < len; ++i) v[i] = Cx<T>::div(x[i * stride], v0);
+    v[0] = Cx<T>::one();
+    *beta_out = beta;
+    // tau = (beta - x0) / beta
+    return Cx<T>::div(subt(beta, x0), beta);
+}
+
+// ----------------------------------------------------------------------------- least squares
+// Householder QR of the (rows x m) matrix W (copy of Hbar) and of the right-hand side;
+// d = R^{-1} (Q^H c)[0..m-1].  All threads participate.
+template <class T>
+__device__ void lsq_solve(T *W, int ldw, int rows, int m, T *rhs, T *d, T *v) {
+    __shared__ T tau_s;
+    __shared__ T beta_s;
+    for (int j = 0; j < m; ++j) {
+        const int len = rows - j;
+        if (threadIdx.x == 0) {
+            T beta;
+            tau_s = house<T>(W + j + (size_t)j * ldw, 1, len, v, &beta);
+            beta_s = beta;
+        }
+        __syncthreads();
+        const T tau = tau_s;
+        // apply to columns j+1..m-1 and to rhs (column index m)
+        for (int c = j + 1 + threadIdx.x; c <= m; c += blockDim.x) {
+            T *col = (c < m) ? (W + (size_t)c * ldw) : rhs;
+            T s = Cx<T>::zero();
+            for (int i = 0; i < len; ++i) s = add(s, Cx<T>::mul(Cx<T>::cj(v[i]), col[j + i]));
+            s = Cx<T>::mul(tau, s);      // H col = col - tau v (v^H col), H x = beta e_1
+            for (int i = 0; i < len; ++i) col[j + i] = subt(col[j + i], Cx<T>::mul(v[i], s));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            W[j + (size_t)j * ldw] = beta_s;
+            for (int i = 1; i < len; ++i) W[j + i + (size_t)j * ldw] = Cx<T>::zero();
+        }
+        __syncthreads();
+    }
+    // back substitution (thread 0; m <= 128)
+    if (threadIdx.x == 0) {
+        for (int i = m - 1; i >= 0; --i) {
+            T s = rhs[i];
+            for (int c = i + 1; c < m; ++c) s = subt(s, Cx<T>::mul(W[i + (size_t)c * ldw], d[c]));
+            T rii = W[i + (size_t)i * ldw];
+            d[i] = Cx<T>::ab2(rii) > 0 ? Cx<T>::div(s, rii) : Cx<T>::zero();
+        }
+    }
+    __syncthreads();
+}
+
+// Solve A^H f = e_last for the m x m matrix A (column-major, ld lda) by Gaussian
+// elimination with partial pivoting on a copy B = A^H.
+template <class T>
+__device__ void solve_adjoint_last(const T *A, int lda, int m, T *B, T *f, int *piv) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e % m, j = e / m;
+        B[i + (size_t)j * m] = Cx<T>::cj(A[j + (size_t)i * lda]);
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) f[i] = (i == m - 1) ? Cx<T>::one() : Cx<T>::zero();
+    __syncthreads();
+    __shared__ int p_s;
+    for (int j = 0; j < m; ++j) {
+        if (threadIdx.x == 0) {
+            int p = j;
+            double best = Cx<T>::ab2(B[j + (size_t)j * m]);
+            for (int i = j + 1; i < m; ++i) {
+                double a = Cx<T>::ab2(B[i + (size_t)j * m]);
+                if (a > best) { best = a; p = i; }
+            }
+            p_s = p;
+            piv[j] = p;
+            if (p != j) {
+                for (int c = 0; c < m; ++c) {
+                    T t = B[j + (size_t)c * m];
+                    B[j + (size_t)c * m] = B[p + (size_t)c * m];
+                    B[p + (size_t)c * m] = t;
+                }
+                T t = f[j]; f[j] = f[p]; f[p] = t;
+            }
+        }
+        __syncthreads();
+        const T pivv = B[j + (size_t)j * m];
+        const bool ok = Cx<T>::ab2(pivv) > 0;
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+            if (!ok) break;
+            T l = Cx<T>::div(B[i + (size_t)j * m], pivv);
+            for (int c = j + 1; c < m; ++c) B[i + (size_t)c * m] = subt(B[i + (size_t)c * m], Cx<T>::mul(l, B[j + (size_t)c * m]));
+            f[i] = subt(f[i], Cx<T>::mul(l, f[j]));
+            B[i + (size_t)j * m] = Cx<T>::zero();
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int i = m - 1; i >= 0; --i) {
+            T s = f[i];
+            for (int c = i + 1; c < m; ++c) s = subt(s, Cx<T>::mul(B[i + (size_t)c * m], f[c]));
+            T bii = B[i + (size_t)i * m];
+            f[i] = Cx<T>::ab2(bii) > 0 ? Cx<T>::div(s, bii) : Cx<T>::zero();
+        }
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- Hessenberg form
+// A (m x m, ld m) <- Q^H A Q upper Hessenberg; Z <- Q (Z must hold I on entry).
+template <class T>
+__device__ void hessenberg(T *A, int m, T *Z, T *v) {
+    __shared__ T tau_s;
+    for (int j = 0; j + 2 < m; ++j) {
+        const int len = m - j - 1;
+        if (threadIdx.x == 0) {
+            T beta;
+            tau_s = house<T>(A + (j + 1) + (size_t)j * m, 1, len, v, &beta);
+        }
+        __syncthreads();
+        const T tau = tau_s;
+        if (Cx<T>::ab2(tau) == 0.0) { __syncthreads(); continue; }
+        // left: rows j+1..m-1, columns j..m-1: A <- H A = A - tau v (v^H A)
+        for (int c = j + threadIdx.x; c < m; c += blockDim.x) {
+            T *col = A + (size_t)c * m + j + 1;
+            T s = Cx<T>::zero();
+            for (int i = 0; i < len; ++i) s = add(s, Cx<T>::mul(Cx<T>::cj(v[i]), col[i]));
+            s = Cx<T>::mul(tau, s);
+            for (int i = 0; i < len; ++i) col[i] = subt(col[i], Cx<T>::mul(v[i], s));
+        }
+        __syncthreads();
+        // right: all rows, columns j+1..m-1: A <- A H^H = A - conj(tau) (A v) v^H; Z <- Z H^H
+        for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
+            T *M = rr < m ? A : Z;
+            const int r = rr < m ? rr : rr - m;
+            T s = Cx<T>::zero();
+            for (int i = 0; i < len; ++i) s = add(s, Cx<T>::mul(M[r + (size_t)(j + 1 + i) * m], v[i]));
+            s = Cx<T>::mul(s, Cx<T>::cj(tau));
+            for (int i = 0; i < len; ++i)
+                M[r + (size_t)(j + 1 + i) * m] = subt(M[r + (size_t)(j + 1 + i) * m], Cx<T>::mul(s, Cx<T>::cj(v[i])));
+        }
+        __syncthreads();
+    }
+    // clean below the subdiagonal
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e % m, j = e / m;
+        if (i > j + 1) A[e] = Cx<T>::zero();
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- real Schur form
+// Francis double-shift QR on the real upper Hessenberg H (m x m, ld m), accumulating Z.
+// Returns 0 on success, 1 if an eigenvalue failed to converge in 40 m sweeps.
+__device__ int real_schur(double *H, int m, double *Z) {
+    __shared__ int hi_s, l_s, status_s, act_s;
+    __shared__ double vv[3], tau3;
+    __shared__ double x_s, y_s, z_s;
+    if (threadIdx.x == 0) { hi_s = m - 1; status_s = 0; }
+    __syncthreads();
+    int its = 0, total = 0;
+    while (true) {
+        // thread 0 finds the active block and decides what to do
+        if (threadIdx.x == 0) {
+            int hi = hi_s;
+            act_s = 0;
+            if (hi < 0) act_s = -1;
+            else {
+                int l = hi;
+                while (l > 0) {
+                    double s = fabs(H[(l - 1) + (size_t)(l - 1) * m]) + fabs(H[l + (size_t)l * m]);
+                    if (s == 0.0) s = 1.0;
+                    if (fabs(H[l + (size_t)(l - 1) * m]) <= kEps * s) {
+                        H[l + (size_t)(l - 1) * m] = 0.0;
+                        break;
+                    }
+                    --l;
+                }
+                l_s = l;
+                if (l == hi) { hi_s = hi - 1; act_s = 1; }
+                else if (l == hi - 1) { act_s = 2; }   // 2x2 block: standardise below
+                else act_s = 3;                         // QR sweep on l..hi
+            }
+        }
+        __syncthreads();
+        const int act = act_s;
+        if (act < 0) break;
+        if (act == 1) { its = 0; continue; }
+        const int hi = hi_s, l = l_s;
+        if (act == 2) {
+            // 2x2 block [a b; c d] at (hi-1, hi): real eigenvalues -> rotate to triangular form
+            __shared__ double cs_s, sn_s;
+            __shared__ int rot_s;
+            if (threadIdx.x == 0) {
+                double a = H[(hi - 1) + (size_t)(hi - 1) * m], b = H[(hi - 1) + (size_t)hi * m];
+                double c = H[hi + (size_t)(hi - 1) * m], d = H[hi + (size_t)hi * m];
+                double p = 0.5 * (a - d);
+                double disc = p * p + b * c;
+                rot_s = 0;
+                if (disc >= 0.0 && c != 0.0) {
+                    // real eigenvalues: lam - d = p + sign(p) sqrt(disc) (no cancellation);
+                    // (lam - d, c) is an eigenvector of the block, and the rotation whose
+                    // first column it is makes the block upper triangular
+                    double e0 = p + copysign(sqrt(disc), p), e1 = c;
+                    double nr = hypot(e0, e1);
+                    if (nr > 0) {
+                        cs_s = e0 / nr;
+                        sn_s = e1 / nr;
+                        rot_s = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (rot_s) {
+                const double cs = cs_s, sn = sn_s;
+                // rows hi-1, hi: H <- G^T H for columns hi-1..m-1
+                for (int c = hi - 1 + threadIdx.x; c < m; c += blockDim.x) {
+                    double h1 = H[(hi - 1) + (size_t)c * m], h2 = H[hi + (size_t)c * m];
+                    H[(hi - 1) + (size_t)c * m] = cs * h1 + sn * h2;
+                    H[hi + (size_t)c * m] = -sn * h1 + cs * h2;
+                }
+                __syncthreads();
+                // columns hi-1, hi: H <- H G for rows 0..hi, Z <- Z G
+                for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
+                    double *M = rr < m ? H : Z;
+                    const int r = rr < m ? rr : rr - m;
+                    if (M == H && r > hi) continue;
+                    double h1 = M[r + (size_t)(hi - 1) * m], h2 = M[r + (size_t)hi * m];
+                    M[r + (size_t)(hi - 1) * m] = cs * h1 + sn * h2;
+                    M[r + (size_t)hi * m] = -sn * h1 + cs * h2;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) H[hi + (size_t)(hi - 1) * m] = 0.0;
+            }
+            if (threadIdx.x == 0) hi_s = hi - 2;
+            __syncthreads();
+            its = 0;
+            continue;
+        }
+        // ---- double-shift sweep on rows/cols l..hi
+        ++its;
+        ++total;
+        if (total > 40 * m) {
+            if (threadIdx.x == 0) status_s = 1;
+            __syncthreads();
+            break;
+        }
+        if (threadIdx.x == 0) {
+            double s, t;
+            if (its % 10 == 0) {
+                // exceptional shift
+                double w = fabs(H[hi + (size_t)(hi - 1) * m]) + fabs(H[(hi - 1) + (size_t)(hi - 2 >= 0 ? hi - 2 : 0) * m]);
+                s = 1.5 * w + H[hi + (size_t)hi * m];
+                t = w * w;
+            } else {
+                double a = H[(hi - 1) + (size_t)(hi - 1) * m], b = H[(hi - 1) + (size_t)hi * m];
+                double c = H[hi + (size_t)(hi - 1) * m], d = H[hi + (size_t)hi * m];
+                s = a + d;
+                t = a * d - b * c;
+            }
+            double h00 = H[l + (size_t)l * m], h01 = H[l + (size_t)(l + 1) * m];
+            double h10 = H[(l + 1) + (size_t)l * m], h11 = H[(l + 1) + (size_t)(l + 1) * m];
+            x_s = h00 * h00 + h01 * h10 - s * h00 + t;
+            y_s = h10 * (h00 + h11 - s);
+            z_s = (l + 2 <= hi) ? h10 * H[(l + 2) + (size_t)(l + 1) * m] : 0.0;
+        }
+        __syncthreads();
+        for (int kk = l; kk <= hi - 1; ++kk) {
+            const int nr = (kk <= hi - 2) ? 3 : 2;
+            if (threadIdx.x == 0) {
+                double x[3] = {x_s, y_s, z_s};
+                double beta;
+                double v[3];
+                tau3 = house<double>(x, 1, nr, v, &beta);
+                vv[0] = 1.0; vv[1] = v[1]; vv[2] = nr == 3 ? v[2] : 0.0;
+            }
+            __syncthreads();
+            const double tau = tau3;
+            if (tau != 0.0) {
+                const double v1 = vv[1], v2 = vv[2];
+                // rows kk..kk+nr-1, columns max(l, kk-1)..m-1
+                const int c0 = kk > l ? kk - 1 : l;
+                for (int c = c0 + threadIdx.x; c < m; c += blockDim.x) {
+                    double h0 = H[kk + (size_t)c * m], h1 = H[kk + 1 + (size_t)c * m];
+                    double h2 = nr == 3 ? H[kk + 2 + (size_t)c * m] : 0.0;
+                    double s = tau * (h0 + v1 * h1 + v2 * h2);
+                    H[kk + (size_t)c * m] = h0 - s;
+                    H[kk + 1 + (size_t)c * m] = h1 - s * v1;
+                    if (nr == 3) H[kk + 2 + (size_t)c * m] = h2 - s * v2;
+                }
+                __syncthreads();
+                // columns kk..kk+nr-1: rows 0..min(kk+3, hi) of H, all rows of Z
+                const int rmax = (kk + 3 < hi) ? kk + 3 : hi;
+                for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
+                    double *M = rr < m ? H : Z;
+                    const int r = rr < m ? rr : rr - m;
+                    if (M == H && r > rmax) continue;
+                    double h0 = M[r + (size_t)kk * m], h1 = M[r + (size_t)(kk + 1) * m];
+                    double h2 = nr == 3 ? M[r + (size_t)(kk + 2) * m] : 0.0;
+                    double s = tau * (h0 + h1 * v1 + h2 * v2);
+                    M[r + (size_t)kk * m] = h0 - s;
+                    M[r + (size_t)(kk + 1) * m] = h1 - s * v1;
+                    if (nr == 3) M[r + (size_t)(kk + 2) * m] = h2 - s * v2;
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0 && kk < hi - 1) {
+                x_s = H[(kk + 1) + (size_t)kk * m];
+                y_s = H[(kk + 2) + (size_t)kk * m];
+                z_s = (kk + 3 <= hi) ? H[(kk + 3) + (size_t)kk * m] : 0.0;
+            }
+            __syncthreads();
+        }
+        // zero the entries below the subdiagonal created by rounding
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = e % m, j = e / m;
+            if (i > j + 1) H[e] = 0.0;
+        }
+        __syncthreads();
+    }
+    return status_s;
+}
+
+// ----------------------------------------------------------------------------- complex Schur form
+// Wilkinson single-shift QR on the complex upper Hessenberg H, accumulating Z.
+__device__ int complex_schur(cplx *H, int m, cplx *Z) {
+    __shared__ int hi_s, l_s, act_s, status_s;
+    __shared__ double gc_s;
+    __shared__ cplx gs_s, x_s, y_s;
+    if (threadIdx.x == 0) { hi_s = m - 1; status_s = 0; }
+    __syncthreads();
+    int its = 0, total = 0;
+    while (true) {
+        if (threadIdx.x == 0) {
+            int hi = hi_s;
+            act_s = 0;
+            if (hi <= 0) act_s = -1;
+            else {
+                int l = hi;
+                while (l > 0) {
+                    double s = cabs_(H[(l - 1) + (size_t)(l - 1) * m]) + cabs_(H[l + (size_t)l * m]);
+                    if (s == 0.0) s = 1.0;
+                    if (cabs_(H[l + (size_t)(l - 1) * m]) <= kEps * s) {
+                        H[l + (size_t)(l - 1) * m] = {0.0, 0.0};
+                        break;
+                    }
+                    --l;
+                }
+                l_s = l;
+                if (l == hi) { hi_s = hi - 1; act_s = 1; }
+                else act_s = 2;
+            }
+        }
+        __syncthreads();
+        const int act = act_s;
+        if (act < 0) break;
+        if (act == 1) { its = 0; continue; }
+        ++its;
+        ++total;
+        if (total > 40 * m) {
+            if (threadIdx.x == 0) status_s = 1;
+            __syncthreads();
+            break;
+        }
+        const int hi = hi_s, l = l_s;
+        if (threadIdx.x == 0) {
+            cplx a = H[(hi - 1) + (size_t)(hi - 1) * m], b = H[(hi - 1) + (size_t)hi * m];
+            cplx c = H[hi + (size_t)(hi - 1) * m], d = H[hi + (size_t)hi * m];
+            cplx mu;
+            if (its % 10 == 0) {
+                mu = d + mkc(1.5 * cabs_(c), 0.0);
+            } else {
+                // eigenvalue of [a b; c d] closer to d
+                cplx p = 0.5 * (a - d);
+                cplx disc = p * p + b * c;
+                // principal square root
+                double r = cabs_(disc);
+                double sr = sqrt(0.5 * (r + disc.re));
+                double si = sqrt(fmax(0.0, 0.5 * (r - disc.re)));
+                if (disc.im < 0) si = -si;
+                cplx sq_ = mkc(sr, si);
+                cplx e1 = p + sq_, e2 = p - sq_;
+                mu = d + ((abs2(e1) < abs2(e2)) ? e1 : e2);
+            }
+            x_s = H[l + (size_t)l * m] - mu;
+            y_s = H[(l + 1) + (size_t)l * m];
+        }
+        __syncthreads();
+        for (int kk = l; kk <= hi - 1; ++kk) {
+            if (threadIdx.x == 0) {
+                cplx x = x_s, y = y_s;
+                double nx = cabs_(x), ny = cabs_(y);
+                double nr = hypot(nx, ny);
+                if (nr == 0.0) { gc_s = 1.0; gs_s = {0.0, 0.0}; }
+                else if (nx == 0.0) { gc_s = 0.0; gs_s = conj(y) * (1.0 / ny); }
+                else {
+                    // G = [c s; -conj(s) c], G [x; y] = [r; 0]: c = |x|/nr, s = (x/|x|) conj(y)/nr
+                    gc_s = nx / nr;
+                    gs_s = (x * (1.0 / nx)) * conj(y) * (1.0 / nr);
+                }
+            }
+            __syncthreads();
+            const double gc = gc_s;
+            const cplx gs = gs_s;
+            const int c0 = kk > l ? kk - 1 : l;
+            for (int c = c0 + threadIdx.x; c < m; c += blockDim.x) {
+                cplx h1 = H[kk + (size_t)c * m], h2 = H[kk + 1 + (size_t)c * m];
+                H[kk + (size_t)c * m] = gc * h1 + gs * h2;
+                H[kk + 1 + (size_t)c * m] = gc * h2 - conj(gs) * h1;
+            }
+            __syncthreads();
+            const int rmax = (kk + 2 < hi) ? kk + 2 : hi;
+            for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
+                cplx *M = rr < m ? H : Z;
+                const int r = rr < m ? rr : rr - m;
+                if (M == H && r > rmax) continue;
+                // M <- M G^H: columns kk, kk+1
+                cplx h1 = M[r + (size_t)kk * m], h2 = M[r + (size_t)(kk + 1) * m];
+                M[r + (size_t)kk * m] = gc * h1 + conj(gs) * h2;
+                M[r + (size_t)(kk + 1) * m] = gc * h2 - gs * h1;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && kk < hi - 1) {
+                x_s = H[(kk + 1) + (size_t)kk * m];
+                y_s = H[(kk + 2) + (size_t)kk * m];
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            int i = e % m, j = e / m;
+            if (i > j + 1) H[e] = {0.0, 0.0};
+        }
+        __syncthreads();
+    }
+    return status_s;
+}
+
+// ----------------------------------------------------------------------------- eigenvalues
+// From the real Schur form T: eigenvalue j as (re, im).  2 x 2 blocks are the complex pairs.
+__device__ void real_schur_eigs(const double *T, int m, double *wr, double *wi) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const bool lower = (j + 1 < m) && T[(j + 1) + (size_t)j * m] != 0.0;   // j is top of a block
+        const bool upper = (j > 0) && T[j + (size_t)(j - 1) * m] != 0.0;       // j is bottom of a block
+        if (lower || upper) {
+            const int t = lower ? j : j - 1;
+            double a = T[t + (size_t)t * m], b = T[t + (size_t)(t + 1) * m];
+            double c = T[(t + 1) + (size_t)t * m], d = T[(t + 1) + (size_t)(t + 1) * m];
+            double p = 0.5 * (a - d);
+            double disc = p * p + b * c;
+            double im = sqrt(fmax(-disc, 0.0));
+            wr[j] = 0.5 * (a + d);
+            wi[j] = lower ? im : -im;
+        } else {
+            wr[j] = T[j + (size_t)j * m];
+            wi[j] = 0.0;
+        }
+    }
+    __syncthreads();
+}
+
+// Back substitution for the eigenvector of eigenvalue (lr, li) at Schur position j of the
+// real quasi-triangular T (one thread).  Output y (complex, length m, zero below j).
+__device__ void real_schur_vector(const double *T, int m, int j, double lr, double li, cplx *y,
+                                  double tnorm) {
+    const double small = fmax(kEps * tnorm, 1e-300);
+    const cplx lam = mkc(lr, li);
+    for (int i = 0; i < m; ++i) y[i] = {0.0, 0.0};
+    int top;
+    if (li == 0.0) {
+        y[j] = {1.0, 0.0};
+        top = j - 1;
+    } else {
+        // 2x2 block at (t, t+1) containing j
+        const bool jtop = (j + 1 < m) && T[(j + 1) + (size_t)j * m] != 0.0;
+        const int t = jtop ? j : j - 1;
+        double a = T[t + (size_t)t * m], b = T[t + (size_t)(t + 1) * m];
+        double c = T[(t + 1) + (size_t)t * m], d = T[(t + 1) + (size_t)(t + 1) * m];
+        if (fabs(b) >= fabs(c)) {
+            y[t] = {1.0, 0.0};
+            y[t + 1] = cdiv(lam - mkc(a, 0.0), mkc(b, 0.0));      // (a - lam) y0 + b y1 = 0
+        } else {
+            y[t + 1] = {1.0, 0.0};
+            y[t] = cdiv(lam - mkc(d, 0.0), mkc(c, 0.0));          // c y0 + (d - lam) y1 = 0
+        }
+        top = t - 1;
+        j = t + 1;
+    }
+    int i = top;
+    while (i >= 0) {
+        const bool blk = (i > 0) && T[i + (size_t)(i - 1) * m] != 0.0;   // rows (i-1, i) form a block
+        if (!blk) {
+            cplx s = {0.0, 0.0};
+            for (int l = i + 1; l <= j; ++l) s = s + T[i + (size_t)l * m] * y[l];
+            cplx den = mkc(T[i + (size_t)i * m], 0.0) - lam;
+            if (cabs_(den) < small) den = mkc(small, 0.0);
+            y[i] = cdiv(-s, den);
+            i -= 1;
+        } else {
+            const int t = i - 1;
+            cplx s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
+            for (int l = i + 1; l <= j; ++l) {
+                s0 = s0 + T[t + (size_t)l * m] * y[l];
+                s1 = s1 + T[i + (size_t)l * m] * y[l];
+            }
+            // [a-lam b; c d-lam] [y_t; y_i] = -[s0; s1]
+            cplx a = mkc(T[t + (size_t)t * m], 0.0) - lam, b = mkc(T[t + (size_t)i * m], 0.0);
+            cplx c = mkc(T[i + (size_t)t * m], 0.0), d = mkc(T[i + (size_t)i * m], 0.0) - lam;
+            cplx det = a * d - b * c;
+            if (cabs_(det) < small * small) det = mkc(small * small, 0.0);
+            y[t] = cdiv(-(d * s0) + b * s1, det);
+            y[i] = cdiv(c * s0 - a * s1, det);
+            i -= 2;
+        }
+    }
+}
+
+__device__ void complex_schur_vector(const cplx *T, int m, int j, cplx *y, double tnorm) {
+    const double small = fmax(kEps * tnorm, 1e-300);
+    const cplx lam = T[j + (size_t)j * m];
+    for (int i = 0; i < m; ++i) y[i] = {0.0, 0.0};
+    y[j] = {1.0, 0.0};
+    for (int i = j - 1; i >= 0; --i) {
+        cplx s = {0.0, 0.0};
+        for (int l = i + 1; l <= j; ++l) s = s + T[i + (size_t)l * m] * y[l];
+        cplx den = T[i + (size_t)i * m] - lam;
+        if (cabs_(den) < small) den = mkc(small, 0.0);
+        y[i] = cdiv(-s, den);
+    }
+}
+
+// order: by |theta|, then Re, then Im >= 0 first (one thread, insertion sort)
+__device__ bool ritz_less(double ar, double ai, double br, double bi) {
+    double ma = hypot(ar, ai), mb = hypot(br, bi);
+    if (ma != mb) return ma < mb;
+    if (ar != br) return ar < br;
+    int ka = ai >= 0 ? 0 : 1, kb = bi >= 0 ? 0 : 1;
+    return ka < kb;
+}
+
+}  // namespace
+
+// ============================================================================= kernels
+
+// Cholesky G = R^H R (G Hermitian positive definite, upper triangle given, k x k) and
+// Rinv = R^{-1}.  info[0] = 0 on success, j+1 if the j-th pivot is not positive.
+template <class D>
+__global__ void k_chol_inv(const D *G, int k, D *R, D *Rinv, int *info) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        int i = e % k, j = e / k;
+        R[e] = i <= j ? G[e] : Cx<D>::zero();
+        Rinv[e] = Cx<D>::zero();
+    }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            double djj = Cx<D>::re(R[j + (size_t)j * k]);
+            for (int i = 0; i < j; ++i) djj -= Cx<D>::ab2(R[i + (size_t)j * k]);
+            if (!(djj > 0.0) && !bad) bad = j + 1;
+            R[j + (size_t)j * k] = Cx<D>::sc(sqrt(fmax(djj, 1e-300)), Cx<D>::one());
+        }
+        __syncthreads();
+        const D rjj = R[j + (size_t)j * k];
+        for (int c = j + 1 + threadIdx.x; c < k; c += blockDim.x) {
+            D s = R[j + (size_t)c * k];
+            for (int i = 0; i < j; ++i) s = subt(s, Cx<D>::mul(Cx<D>::cj(R[i + (size_t)j * k]), R[i + (size_t)c * k]));
+            R[j + (size_t)c * k] = Cx<D>::div(s, rjj);
+        }
+        __syncthreads();
+    }
+    // Rinv: solve R X = I column by column (thread per column)
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        for (int i = c; i >= 0; --i) {
+            D s = (i == c) ? Cx<D>::one() : Cx<D>::zero();
+            for (int l = i + 1; l <= c; ++l) s = subt(s, Cx<D>::mul(R[i + (size_t)l * k], Rinv[l + (size_t)c * k]));
+            Rinv[i + (size_t)c * k] = Cx<D>::div(s, R[i + (size_t)i * k]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) info[0] = bad;
+}
+
+// Inverse of a general k x k matrix by Gauss-Jordan with partial pivoting (W: scratch
+// 2 k^2).  info[0] = 0, or j+1 for a zero pivot.
+template <class D>
+__global__ void k_inverse(const D *H, int k, D *Hinv, D *W, int *info) {
+    __shared__ int p_s, bad;
+    D *A = W;
+    D *B = W + (size_t)k * k;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        A[e] = H[e];
+        B[e] = (e % k == e / k) ? Cx<D>::one() : Cx<D>::zero();
+    }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        if (threadIdx.x == 0) {
+            int p = j;
+            double best = Cx<D>::ab2(A[j + (size_t)j * k]);
+            for (int i = j + 1; i < k; ++i)
+                if (Cx<D>::ab2(A[i + (size_t)j * k]) > best) { best = Cx<D>::ab2(A[i + (size_t)j * k]); p = i; }
+            if (best == 0.0 && !bad) bad = j + 1;
+            p_s = p;
+        }
+        __syncthreads();
+        const int p = p_s;
+        if (p != j) {
+            for (int c = threadIdx.x; c < k; c += blockDim.x) {
+                D t = A[j + (size_t)c * k]; A[j + (size_t)c * k] = A[p + (size_t)c * k]; A[p + (size_t)c * k] = t;
+                t = B[j + (size_t)c * k]; B[j + (size_t)c * k] = B[p + (size_t)c * k]; B[p + (size_t)c * k] = t;
+            }
+        }
+        __syncthreads();
+        const D piv = A[j + (size_t)j * k];
+        if (Cx<D>::ab2(piv) == 0.0) { __syncthreads(); continue; }
+        // scale row j
+        for (int c = threadIdx.x; c < k; c += blockDim.x) {
+            A[j + (size_t)c * k] = Cx<D>::div(A[j + (size_t)c * k], piv);
+            B[j + (size_t)c * k] = Cx<D>::div(B[j + (size_t)c * k], piv);
+        }
+        __syncthreads();
+        // eliminate column j from the other rows (thread per row)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            if (i == j) continue;
+            D f = A[i + (size_t)j * k];
+            for (int c = 0; c < k; ++c) {
+                A[i + (size_t)c * k] = subt(A[i + (size_t)c * k], Cx<D>::mul(f, A[j + (size_t)c * k]));
+                B[i + (size_t)c * k] = subt(B[i + (size_t)c * k], Cx<D>::mul(f, B[j + (size_t)c * k]));
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) Hinv[e] = B[e];
+    if (threadIdx.x == 0) info[0] = bad;
+}
+
+// out = M c (k x k times k), one thread per row.
+template <class D>
+__global__ void k_small_gemv(const D *M, int k, const D *c, D *out) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        D s = Cx<D>::zero();
+        for (int j = 0; j < k; ++j) s = add(s, Cx<D>::mul(M[i + (size_t)j * k], c[j]));
+        out[i] = s;
+    }
+}
+
+// ----------------------------------------------------------------------------- GMRES-DR restart
+// See tg_small.cuh for the argument layout.
+template <class T>
+__global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a) {
+    const int m = a.m;
+    const int rows = m + 1;
+    const int ldh = a.ldh;
+    T *W = a.work;                        // (m+1) x m (least squares copy), later m x m eigen matrix
+    T *Z = W + (size_t)rows * m;          // m x m Schur vectors
+    T *B = Z + (size_t)m * m;             // m x m scratch (LU, eigenvectors)
+    T *vtmp = B + (size_t)m * m;          // 2 (m+1) vectors
+    T *f = vtmp + 2 * (m + 1);
+    T *res = a.res;
+    __shared__ int piv_s[kMaxM + 1];
+
+    // ---- 1. least squares: d = argmin ||c - Hbar d||, res = c - Hbar d
+    for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+        int i = e % rows, j = e / rows;
+        W[i + (size_t)j * rows] = a.H[i + (size_t)j * ldh];
+    }
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) vtmp[m + 1 + i] = a.c[i];
+    __syncthreads();
+    lsq_solve<T>(W, rows, rows, m, vtmp + (m + 1), a.d, vtmp);
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        T s = a.c[i];
+        for (int j = 0; j < m; ++j) s = subt(s, Cx<T>::mul(a.H[i + (size_t)j * ldh], a.d[j]));
+        res[i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < rows; ++i) s += Cx<T>::ab2(res[i]);
+        a.info->rnorm = sqrt(s);
+    }
+
+    // ---- 2. f = H_m^{-H} e_m and the harmonic matrix M = H_m + |h|^2 f e_m^T (in W, ld m)
+    solve_adjoint_last<T>(a.H, ldh, m, B, f, piv_s);
+    const T hm = a.H[m + (size_t)(m - 1) * ldh];
+    const double hm2 = Cx<T>::ab2(hm);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e % m, j = e / m;
+        T v = a.H[i + (size_t)j * ldh];
+        if (j == m - 1) v = add(v, Cx<T>::sc(hm2, f[i]));
+        W[e] = v;
+        Z[e] = (i == j) ? Cx<T>::one() : Cx<T>::zero();
+    }
+    __syncthreads();
+    // z = [-|h|^2 f; h] (restart direction), kept in a.z
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) a.z[i] = (i < m) ? Cx<T>::sc(-hm2, f[i]) : hm;
+
+    // ---- 3. eigen-decomposition of M: Hessenberg, Schur, eigenvalues
+    hessenberg<T>(W, m, Z, vtmp);
+    int st;
+    double *wr = a.wr, *wi = a.wi;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        st = real_schur(reinterpret_cast<double *>(W), m, reinterpret_cast<double *>(Z));
+        real_schur_eigs(reinterpret_cast<double *>(W), m, wr, wi);
+    } else {
+        st = complex_schur(reinterpret_cast<cplx *>(W), m, reinterpret_cast<cplx *>(Z));
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            cplx t = reinterpret_cast<cplx *>(W)[j + (size_t)j * m];
+            wr[j] = t.re;
+            wi[j] = t.im;
+        }
+        __syncthreads();
+    }
+    double tnorm = 0.0;
+    {
+        __shared__ double tn_s;
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int e = 0; e < m * m; ++e) s = fmax(s, sqrt(Cx<T>::ab2(W[e])));
+            tn_s = s;
+        }
+        __syncthreads();
+        tnorm = tn_s;
+    }
+
+    // ---- 4. order and select
+    __shared__ int kk_s;
+    int *ord = a.order;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < m; ++i) ord[i] = i;
+        for (int i = 1; i < m; ++i) {
+            int v = ord[i], j = i - 1;
+            while (j >= 0 && ritz_less(wr[v], wi[v], wr[ord[j]], wi[ord[j]])) { ord[j + 1] = ord[j]; --j; }
+            ord[j + 1] = v;
+        }
+        int kk = a.k;
+        if (sizeof(T) == sizeof(double) && kk < m) {
+            int t = ord[kk - 1];
+            if (wi[t] > 0.0) kk += 1;     // keep both members of the conjugate pair
+        }
+        kk_s = kk;
+        a.info->status = st;
+        for (int i = 0; i < m; ++i) {
+            a.theta[2 * i] = wr[ord[i]];
+            a.theta[2 * i + 1] = wi[ord[i]];
+        }
+    }
+    __syncthreads();
+    const int kk = kk_s;
+
+    // ---- 5. eigenvectors of the kept pairs: g = Z y (complex), unit norm; residuals
+    // a.gwork holds the kept eigenvectors as complex columns (m x kk)
+    cplx *G = a.gwork;
+    cplx *Y = a.ywork;
+    for (int q = threadIdx.x; q < kk; q += blockDim.x) {
+        const int j = ord[q];
+        cplx *y = Y + (size_t)q * m;
+        if constexpr (sizeof(T) == sizeof(double))
+            real_schur_vector(reinterpret_cast<const double *>(W), m, j, wr[j], wi[j], y, tnorm);
+        else
+            complex_schur_vector(reinterpret_cast<const cplx *>(W), m, j, y, tnorm);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * kk; e += blockDim.x) {
+        const int i = e % m, q = e / m;
+        const cplx *y = Y + (size_t)q * m;
+        cplx s = {0.0, 0.0};
+        for (int l = 0; l < m; ++l) {
+            T zl = Z[i + (size_t)l * m];
+            cplx zc;
+            if constexpr (sizeof(T) == sizeof(double)) zc = mkc(*reinterpret_cast<const double *>(&zl), 0.0);
+            else zc = *reinterpret_cast<const cplx *>(&zl);
+            s = s + zc * y[l];
+        }
+        G[i + (size_t)q * m] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kk; q += blockDim.x) {
+        cplx *g = G + (size_t)q * m;
+        double nr = 0.0;
+        for (int i = 0; i < m; ++i) nr += abs2(g[i]);
+        nr = sqrt(nr);
+        for (int i = 0; i < m; ++i) g[i] = g[i] * (1.0 / nr);
+        // residual ||Hbar g - theta [g; 0]||
+        const cplx th = mkc(a.theta[2 * q], a.theta[2 * q + 1]);
+        double r2 = 0.0;
+        for (int i = 0; i < rows; ++i) {
+            cplx s = {0.0, 0.0};
+            for (int j = 0; j < m; ++j) {
+                T hij = a.H[i + (size_t)j * ldh];
+                cplx hc;
+                if constexpr (sizeof(T) == sizeof(double)) hc = mkc(*reinterpret_cast<const double *>(&hij), 0.0);
+                else hc = *reinterpret_cast<const cplx *>(&hij);
+                s = s + hc * g[j];
+            }
+            if (i < m) s = s - th * g[i];
+            r2 += abs2(s);
+        }
+        a.eres[q] = sqrt(r2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nconv = 0;
+        for (int q = 0; q < a.nev && q < kk; ++q)
+            if (a.eres[q] <= a.rtolev * hypot(a.theta[2 * q], a.theta[2 * q + 1])) ++nconv;
+        a.info->nconv = nconv;
+        a.info->kk = kk;
+    }
+
+    // ---- 6. P_k: orthonormal basis of the kept span (real: Re/Im of pairs), m x kk
+    //          then P_{k+1} = orth([[P_k; 0], z]), stored (m+1) x (kk+1) with ld m+1.
+    T *P = a.P;
+    __shared__ int ncol_s;
+    if (threadIdx.x == 0) {
+        int col = 0;
+        for (int q = 0; q < kk; ++q) {
+            const cplx *g = G + (size_t)q * m;
+            const double im = a.theta[2 * q + 1];
+            if constexpr (sizeof(T) == sizeof(double)) {
+                double *Pd = reinterpret_cast<double *>(P);
+                if (im == 0.0) {
+                    // a real eigenvector computed in complex arithmetic has a common phase;
+                    // rotate it onto the real axis via its largest entry
+                    int imax = 0;
+                    double best = -1.0;
+                    for (int i = 0; i < m; ++i) if (abs2(g[i]) > best) { best = abs2(g[i]); imax = i; }
+                    cplx ph = conj(g[imax]) * (1.0 / sqrt(best));
+                    for (int i = 0; i < m; ++i) Pd[i + (size_t)col * rows] = (g[i] * ph).re;
+                    Pd[m + (size_t)col * rows] = 0.0;
+                    ++col;
+                } else if (im > 0.0) {
+                    for (int i = 0; i < m; ++i) {
+                        Pd[i + (size_t)col * rows] = g[i].re;
+                        Pd[i + (size_t)(col + 1) * rows] = g[i].im;
+                    }
+                    Pd[m + (size_t)col * rows] = 0.0;
+                    Pd[m + (size_t)(col + 1) * rows] = 0.0;
+                    col += 2;
+                }
+            } else {
+                cplx *Pc = reinterpret_cast<cplx *>(P);
+                for (int i = 0; i < m; ++i) Pc[i + (size_t)col * rows] = g[i];
+                Pc[m + (size_t)col * rows] = {0.0, 0.0};
+                ++col;
+            }
+        }
+        ncol_s = col;
+    }
+    __syncthreads();
+    const int nc = ncol_s;     // == kk
+    // append z as column kk
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) P[i + (size_t)nc * rows] = a.z[i];
+    __syncthreads();
+    // modified Gram-Schmidt, two passes, over the nc + 1 columns (length m+1)
+    __shared__ double nrm_s;
+    __shared__ T proj_s;
+    for (int c = 0; c <= nc; ++c) {
+        T *pc = P + (size_t)c * rows;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int q = 0; q < c; ++q) {
+                const T *pq = P + (size_t)q * rows;
+                if (threadIdx.x == 0) {
+                    T s = Cx<T>::zero();
+                    for (int i = 0; i < rows; ++i) s = add(s, Cx<T>::mul(Cx<T>::cj(pq[i]), pc[i]));
+                    proj_s = s;
+                }
+                __syncthreads();
+                const T s = proj_s;
+                for (int i = threadIdx.x; i < rows; i += blockDim.x) pc[i] = subt(pc[i], Cx<T>::mul(s, pq[i]));
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < rows; ++i) s += Cx<T>::ab2(pc[i]);
+            nrm_s = sqrt(s);
+        }
+        __syncthreads();
+        const double inv = nrm_s > 0 ? 1.0 / nrm_s : 0.0;
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) pc[i] = Cx<T>::sc(inv, pc[i]);
+        __syncthreads();
+    }
+
+    // ---- 7. Hnew = P_{k+1}^H Hbar P_k  ((kk+1) x kk, ld m+1 into a.Hnew), cnew = P_{k+1}^H res
+    // T1 = Hbar P_k ((m+1) x kk) into W
+    for (int e = threadIdx.x; e < rows * nc; e += blockDim.x) {
+        const int i = e % rows, q = e / rows;
+        T s = Cx<T>::zero();
+        for (int j = 0; j < m; ++j) s = add(s, Cx<T>::mul(a.H[i + (size_t)j * ldh], P[j + (size_t)q * rows]));
+        W[i + (size_t)q * rows] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (nc + 1) * nc; e += blockDim.x) {
+        const int i = e % (nc + 1), q = e / (nc + 1);
+        T s = Cx<T>::zero();
+        for (int l = 0; l < rows; ++l) s = add(s, Cx<T>::mul(Cx<T>::cj(P[l + (size_t)i * rows]), W[l + (size_t)q * rows]));
+        a.Hnew[i + (size_t)q * ldh] = s;
+    }
+    for (int i = threadIdx.x; i <= nc; i += blockDim.x) {
+        T s = Cx<T>::zero();
+        for (int l = 0; l < rows; ++l) s = add(s, Cx<T>::mul(Cx<T>::cj(P[l + (size_t)i * rows]), res[l]));
+        a.cnew[i] = s;
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- GMRES(m) Givens step
+// Column j of the Arnoldi Hessenberg (h[0..j+1], ld = m+1) is rotated by the previous
+// rotations, a new rotation zeroes h[j+1]; g (the least-squares right-hand side) is
+// updated; state->resid = |g[j+1]|; state->done = 1 when resid <= target or h[j,j] = 0.
+template <class D>
+__global__ void k_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (state->done) return;
+    D *h = H + (size_t)j * ldh;
+    for (int i = 0; i < j; ++i) {
+        D a = h[i], b = h[i + 1];
+        h[i] = add(Cx<D>::mul(Cx<D>::cj(cs[i]), a), Cx<D>::mul(Cx<D>::cj(sn[i]), b));
+        h[i + 1] = subt(Cx<D>::mul(cs[i], b), Cx<D>::mul(sn[i], a));
+    }
+    D a = h[j], b = h[j + 1];
+    double den = sqrt(Cx<D>::ab2(a) + Cx<D>::ab2(b));
+    if (den == 0.0) {
+        cs[j] = Cx<D>::one();
+        sn[j] = Cx<D>::zero();
+    } else {
+        cs[j] = Cx<D>::sc(1.0 / den, a);
+        sn[j] = Cx<D>::sc(1.0 / den, b);
+    }
+    h[j] = Cx<D>::sc(den, Cx<D>::one());
+    h[j + 1] = Cx<D>::zero();
+    g[j + 1] = Cx<D>::sc(-1.0, Cx<D>::mul(sn[j], g[j]));
+    g[j] = Cx<D>::mul(Cx<D>::cj(cs[j]), g[j]);
+    double resid = sqrt(Cx<D>::ab2(g[j + 1]));
+    state->resid = resid;
+    state->steps = j + 1;
+    if (!(resid > state->target) || den == 0.0 || !isfinite(resid)) state->done = 1;
+}
+
+// y = R^{-1} g[0..kj-1] for the rotated (upper triangular) Hessenberg.
+template <class D>
+__global__ void k_givens_solve(const D *H, int ldh, const D *g, D *y, const GivensState *state) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int kj = state->steps;
+    for (int i = kj - 1; i >= 0; --i) {
+        D s = g[i];
+        for (int c = i + 1; c < kj; ++c) s = subt(s, Cx<D>::mul(H[i + (size_t)c * ldh], y[c]));
+        D hii = H[i + (size_t)i * ldh];
+        y[i] = Cx<D>::ab2(hii) > 0 ? Cx<D>::div(s, hii) : Cx<D>::zero();
+    }
+}
+
+// ----------------------------------------------------------------------------- launchers
+template <class D>
+void launch_chol_inv(const D *G, int k, D *R, D *Rinv, int *info, cudaStream_t s) {
+    k_chol_inv<D><<<1, kSmallThreads, 0, s>>>(G, k, R, Rinv, info);
+}
+template <class D>
+void launch_inverse(const D *H, int k, D *Hinv, D *W, int *info, cudaStream_t s) {
+    k_inverse<D><<<1, kSmallThreads, 0, s>>>(H, k, Hinv, W, info);
+}
+template <class D>
+void launch_small_gemv(const D *M, int k, const D *c, D *out, cudaStream_t s) {
+    k_small_gemv<D><<<1, kSmallThreads, 0, s>>>(M, k, c, out);
+}
+template <class T>
+void launch_gmresdr_restart(const GdrArgs<T> &a, cudaStream_t s) {
+    k_gmresdr_restart<T><<<1, kSmallThreads, 0, s>>>(a);
+}
+template <class D>
+void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s) {
+    k_givens_step<D><<<1, 1, 0, s>>>(H, ldh, j, cs, sn, g, state);
+}
+template <class D>
+void launch_givens_solve(const D *H, int ldh, const D *g, D *y, const GivensState *state, cudaStream_t s) {
+    k_givens_solve<D><<<1, 1, 0, s>>>(H, ldh, g, y, state);
+}
+
+#define TG_INST(D)                                                                                   \
+    template void launch_chol_inv<D>(const D *, int, D *, D *, int *, cudaStream_t);                 \
+    template void launch_inverse<D>(const D *, int, D *, D *, int *, cudaStream_t);                  \
+    template void launch_small_gemv<D>(const D *, int, const D *, D *, cudaStream_t);                \
+    template void launch_gmresdr_restart<D>(const GdrArgs<D> &, cudaStream_t);                       \
+    template void launch_givens_step<D>(D *, int, int, D *, D *, D *, GivensState *, cudaStream_t);  \
+    template void launch_givens_solve<D>(const D *, int, const D *, D *, const GivensState *, cudaStream_t);
+TG_INST(double)
+TG_INST(cplx)
+#undef TG_INST
+
+}  // namespace tg

@@ -1,0 +1,59 @@
+// Declarations of the single-CTA float64 small dense kernels (tg_small.cu).
+#pragma once
+
+#include "tg_common.cuh"
+
+namespace tg {
+
+constexpr int kSmallThreads = 256;
+constexpr int kMaxM = 128;          // largest GMRES-DR subspace dimension m
+
+struct GdrInfo {
+    double rnorm;   // ||c - Hbar d||
+    int nconv;      // kept pairs (first nev) with residual <= rtolev |theta|
+    int kk;         // kept pairs (k or k+1)
+    int status;     // 0, or 1 if the QR iteration did not converge
+};
+
+// Arguments of the GMRES-DR restart kernel (all pointers device memory).
+template <class T>
+struct GdrArgs {
+    const T *H;      // Hbar, (m+1) x m, leading dimension ldh
+    int ldh;
+    const T *c;      // least-squares right-hand side, m+1
+    int m, k, nev;
+    double rtolev;
+    T *d;            // out: least-squares solution, m
+    T *res;          // out: c - Hbar d, m+1
+    T *z;            // out: restart direction [-|h|^2 f; h], m+1
+    double *theta;   // out: 2m doubles, harmonic Ritz values (re, im) in selection order
+    double *wr, *wi; // scratch: m each
+    int *order;      // scratch: m
+    double *eres;    // out: residual norms of the kept pairs (up to m)
+    T *P;            // out: P_{k+1}, (m+1) x (kk+1), ld m+1; its first kk columns (m rows) are P_k
+    T *Hnew;         // out: P_{k+1}^H Hbar P_k, (kk+1) x kk, leading dimension ldh
+    T *cnew;         // out: P_{k+1}^H res, kk+1
+    T *work;         // scratch: (m+1) m + 2 m^2 + 3 m + 2 elements of T
+    cplx *ywork;     // scratch: m * m complex
+    cplx *gwork;     // scratch: m * m complex
+    GdrInfo *info;
+};
+
+struct GivensState {
+    double target;  // stop when |g[j+1]| <= target
+    double resid;
+    int steps;      // columns processed
+    int done;
+};
+
+// Host launchers (one block of kSmallThreads threads each, queued on stream s).
+template <class D> void launch_chol_inv(const D *G, int k, D *R, D *Rinv, int *info, cudaStream_t s);
+template <class D> void launch_inverse(const D *H, int k, D *Hinv, D *W, int *info, cudaStream_t s);
+template <class D> void launch_small_gemv(const D *M, int k, const D *c, D *out, cudaStream_t s);
+template <class T> void launch_gmresdr_restart(const GdrArgs<T> &a, cudaStream_t s);
+template <class D>
+void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s);
+template <class D>
+void launch_givens_solve(const D *H, int ldh, const D *g, D *y, const GivensState *state, cudaStream_t s);
+
+}  // namespace tg

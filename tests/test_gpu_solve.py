@@ -1,0 +1,192 @@
+"""End-to-end GPU solves against the oracle (through the C ABI).
+
+Bars (from the method's stated targets):
+  * relative residual ||b - A x|| / ||b|| <= rtol, recomputed here in float64 by the
+    oracle's operator;
+  * ||x - x*|| / ||x*|| <= 1e-6 with x* = A^{-1} b (the plain definition, sparse LU);
+    these runs use rtol = 1e-10 because at 1e-8 the error bound
+    rtol / (lambda_min ||x|| / ||b||) is about 8.6e-7 for the 127^2 problem, too close
+    to 1e-6 to separate rounding from error;
+  * coarse GMRES-DR: harmonic Ritz values close to the closed-form eigenvalues of the
+    coarse operator; the run stops with nev pairs converged;
+  * adjoint: dL/dkappa against the oracle's gradient from direct solves (1e-5).
+"""
+import numpy as np
+import pytest
+
+import tg_inputs as gi
+from oracle import adjoint, krylov, transfer, twogrid
+from oracle.operators import CD2D, CD3D, U1_4D, VARK2D, Operator as OOp, cd2d_eigenvalues, coarse_operator
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_03070_gb300 import build
+    build.build()
+    from paper_2005_03070_gb300 import tg as mod
+    mod.load()
+    return mod
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def two_grid(tg, top, b, m, k, rtolev=1e-4, method="bicgstab", precision="f64", rtol=1e-8, ncyc=0,
+             restart_mvps=60, proj="minres", m3=20):
+    bt = cu(b)
+    xc, defl, cst, cstatus = top.coarse_gmresdr(bt, m, k, rtolev=rtolev, rtol=1e-8, max_cycles=300, proj=proj,
+                                               precision=precision)
+    x = top.prolong(xc)
+    status, stats = top.solve(bt, x, defl, method=method, precision=precision, rtol=rtol, ncyc=ncyc,
+                              restart_mvps=restart_mvps, m3=m3, history=200)
+    return host(x), status, stats[0], cst, defl
+
+
+def test_cfg0_two_grid_bicgstab_fp64(tg):
+    N = 127
+    top, oop = tg.Operator("cd2d", N, (1.0,)), OOp(CD2D, N, (1.0,))
+    b = gi.rhs(oop.n, 0)
+    xs = twogrid.exact_solution(oop, b)
+    x, status, st, cst, defl = two_grid(tg, top, b, 30, 15, rtol=1e-10)
+    assert status == tg.TG_OK, st
+    assert cst["kk"] >= 15 and cst["eig_converged"] >= 15
+    assert np.linalg.norm(b - oop.apply(x)) / np.linalg.norm(b) <= 1e-10
+    assert rel(x, xs) <= 1e-6
+    # at the timed tolerance
+    x8, status8, st8, _, _ = two_grid(tg, top, b, 30, 15, rtol=1e-8)
+    assert status8 == tg.TG_OK
+    assert np.linalg.norm(b - oop.apply(x8)) / np.linalg.norm(b) <= 1e-8
+    # deflation helps: fewer products than plain restarted BiCGStab
+    xp = cu(np.zeros(oop.n))
+    _, plain = top.solve(cu(b), xp, None, rtol=1e-8, ncyc=0, restart_mvps=60)
+    assert st8["mvps"] < plain[0]["mvps"]
+
+
+def test_cfg0_cycle_schedule_ncyc(tg):
+    N = 127
+    top, oop = tg.Operator("cd2d", N, (1.0,)), OOp(CD2D, N, (1.0,))
+    b = gi.rhs(oop.n, 1)
+    x, status, st, _, _ = two_grid(tg, top, b, 30, 15, rtol=1e-8, ncyc=20, restart_mvps=0)
+    assert status == tg.TG_OK
+    assert np.linalg.norm(b - oop.apply(x)) / np.linalg.norm(b) <= 1e-8
+    assert st["cycles"] <= 20
+
+
+def test_cfg0_two_grid_fp32_ir(tg):
+    N = 127
+    top, oop = tg.Operator("cd2d", N, (1.0,)), OOp(CD2D, N, (1.0,))
+    b = gi.rhs(oop.n, 2)
+    xs = twogrid.exact_solution(oop, b)
+    x, status, st, _, _ = two_grid(tg, top, b, 30, 15, precision="f32_ir", rtol=1e-10)
+    assert status == tg.TG_OK, st
+    assert np.linalg.norm(b - oop.apply(x)) / np.linalg.norm(b) <= 1e-10
+    assert rel(x, xs) <= 1e-6
+
+
+@pytest.mark.parametrize("proj", ["minres", "galerkin"])
+def test_two_grid_gmres_proj(tg, proj):
+    N = 63
+    top, oop = tg.Operator("cd2d", N, (1.0,)), OOp(CD2D, N, (1.0,))
+    b = gi.rhs(oop.n, 3)
+    xs = twogrid.exact_solution(oop, b)
+    x, status, st, _, _ = two_grid(tg, top, b, 20, 8, method="gmres", rtol=1e-10, proj=proj, m3=20)
+    assert status == tg.TG_OK, st
+    assert rel(x, xs) <= 1e-6
+
+
+def test_cfg1_shape_small_3d(tg):
+    N = 31
+    beta = (2.0, 1.0, 0.5)
+    top, oop = tg.Operator("cd3d", N, beta), OOp(CD3D, N, beta)
+    b = gi.rhs(oop.n, 4)
+    xs = twogrid.exact_solution(oop, b)
+    for method in ("bicgstab", "gmres"):
+        x, status, st, _, _ = two_grid(tg, top, b, 30, 10, method=method, rtol=1e-10, ncyc=10, restart_mvps=0)
+        assert status == tg.TG_OK, (method, st)
+        assert rel(x, xs) <= 1e-6
+
+
+def test_coarse_gmresdr_eigenvalues(tg):
+    N = 63
+    top = tg.Operator("cd2d", N, (1.0,))
+    b = gi.rhs(N * N, 5)
+    xc, defl, st, status = top.coarse_gmresdr(cu(b), 30, 10, nev=6, rtolev=1e-8, rtol=1e-10, max_cycles=400)
+    assert status == tg.TG_OK, st
+    assert st["eig_converged"] >= 6
+    # the coarse solution solves the restricted problem
+    opc = coarse_operator(OOp(CD2D, N, (1.0,)))
+    bc = transfer.restrict(b, N, 2)
+    xcc = host(xc)
+    assert np.linalg.norm(bc - opc.apply(xcc)) / np.linalg.norm(bc) <= 1e-9
+    # the prolonged basis spans the smallest coarse eigenvectors, prolonged
+    lam, W = np.linalg.eig(opc.sparse().toarray())
+    order = np.argsort(lam.real)
+    Y = host(defl.copy(0)).T
+    Q = np.linalg.qr(Y)[0]
+    for j in order[:4]:
+        w = transfer.prolong2d(W[:, j].real, opc.N)
+        assert np.linalg.norm(w - Q @ (Q.T @ w)) / np.linalg.norm(w) <= 1e-6
+    del lam
+    assert np.allclose(np.sort(np.linalg.eigvals(opc.sparse().toarray()).real)[:6], cd2d_eigenvalues(31, 1.0)[:6])
+
+
+def test_lattice_two_grid(tg):
+    L = 8
+    links = gi.u1_links(L, 2)
+    top = tg.Operator("u1_4d", L, links=cu(links), mass=0.5)
+    oop = OOp(U1_4D, L, links=links, mass=0.5)
+    b = gi.rhs(oop.n, 6).astype(np.complex128)
+    xs = twogrid.exact_solution(oop, b)
+    x, status, st, cst, _ = two_grid(tg, top, b, 20, 8, rtol=1e-10, ncyc=10, restart_mvps=0)
+    assert status == tg.TG_OK, (st, cst)
+    assert rel(x, xs) <= 1e-6
+
+
+def test_adjoint_gradient(tg):
+    N = 31
+    kap = gi.kappa_grf(N, 3)
+    top = tg.Operator("vark2d", N, (1.0,), kappa=cu(kap))
+    oop = OOp(VARK2D, N, (1.0,), kap)
+    b = gi.rhs(oop.n, 7)
+    xstar = gi.random_dense(oop.n, 8) * 1e-3
+    L, grad_o, x_o, lam_o = adjoint.loss_and_gradient(oop, b, xstar)
+    # forward two-grid solve, then the adjoint with left vectors from GMRES-DR on A^T
+    x, status, st, _, _ = two_grid(tg, top, b, 20, 8, rtol=1e-11, ncyc=10, restart_mvps=0)
+    assert status == tg.TG_OK
+    g = cu(x - xstar)
+    _, defl_l, _, _ = top.coarse_gmresdr(g, 20, 8, rtolev=1e-4, transpose=True, want_xc=False)
+    lam = cu(np.zeros(oop.n))
+    dk = cu(np.zeros((N + 2) ** 2))
+    status, ast = top.adjoint_solve(defl_l, g, lam, cu(x), dk, rtol=1e-11, ncyc=10, restart_mvps=0)
+    assert status == tg.TG_OK, ast
+    assert rel(host(lam), lam_o) <= 1e-6
+    gk = host(dk)
+    assert rel(gk, grad_o) <= 1e-5
+    # the contraction alone, on the oracle's x and lambda, agrees to rounding
+    gk2 = host(top.kappa_gradient(cu(x_o), cu(lam_o)))
+    assert rel(gk2, grad_o) <= 1e-12
+
+
+def test_bad_arguments_and_status(tg):
+    top = tg.Operator("cd2d", 15, (1.0,))
+    b = cu(gi.rhs(225, 0))
+    x = cu(np.zeros(225))
+    with pytest.raises(tg.TgError):
+        top.solve(b, x, None, rtol=2.0)
+    st, stats = top.solve(b, x, None, rtol=1e-12, ncyc=0, restart_mvps=5, max_mvps=10)
+    assert st == tg.TG_NOT_CONVERGED and stats[0]["mvps"] == 10
