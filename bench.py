@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark of the two-grid deflated Krylov solve on GB300: fine-grid solves per second
+to relative residual 1e-8.
+
+One step is one pass of the whole path over one synthetic right-hand side:
+coarse GMRES-DR(m,k) (Section 2.1) on the restricted right-hand side, prolongation of
+the k eigenvectors and of the coarse solution (Section 3, phase 1), A Y and its CholQR2
+factorisation, then BiCGStab(ncyc)-Proj(k) (Section 4.1) on the fine grid until
+||b - A x|| / ||b|| <= 1e-8 (verified in float64 by the library at exit).
+
+Default workload (cd3d_255): -Lap u + beta . grad u on the unit cube, beta = (2, 1, 0.5),
+7-point centred differences, fine grid 255^3 (16,581,375 unknowns), coarse grid 127^3,
+30 eigenvectors prolonged trilinearly, b ~ N(0, 1), float64 throughout.
+
+  python bench.py [--steps K] [--warmup W] [--workload cd3d_255|cd2d_127] [--impl tg|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N ranks each rank solves its own
+right-hand side (independent replicas: the path has no data-path exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cd3d_255": dict(kind="cd3d", N=255, beta=(2.0, 1.0, 0.5), m=60, k=30, nev=30, rtolev=1e-2, rtol_c=1e-8,
+                     max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20,
+                     restart_mvps=0, m3=20),
+    "cd2d_127": dict(kind="cd2d", N=127, beta=(1.0,), m=30, k=15, nev=15, rtolev=1e-4, rtol_c=1e-8,
+                     max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=0,
+                     restart_mvps=60, m3=20),
+}
+L2_BYTES = 129 * 1024 * 1024
+FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz
+# DRAM bytes per launch of the dominant kernel from an ncu capture (see profiles/), per
+# workload and kernel class; None when the kernel changed after the capture.
+NCU_TRAFFIC = {}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", self.device_id, "--query-gpu=" + ",".join(self.FIELDS),
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                mhz.append(float(s[0]))
+                mx = float(s[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, s[3:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_tg(args, wl, rank, world):
+    import numpy as np
+    import torch
+
+    import tg_inputs as gi
+    from paper_2005_03070_gb300 import build as tgbuild
+    tgbuild.build()
+    from paper_2005_03070_gb300 import tg
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    op = tg.Operator(wl["kind"], wl["N"], wl["beta"])
+    n = op.n
+    b_host = torch.from_numpy(gi.rhs(n, seed=rank)).pin_memory()
+    b = b_host.to(dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if n * 8 < L2_BYTES else None
+
+    def step(bvec, precision):
+        xc, defl, cst, _ = op.coarse_gmresdr(bvec, wl["m"], wl["k"], nev=wl["nev"], rtolev=wl["rtolev"],
+                                            rtol=wl["rtol_c"], max_cycles=wl["max_cycles"], proj=wl["proj"],
+                                            precision=precision)
+        x = op.prolong(xc)
+        status, st = op.solve(bvec, x, defl, method=wl["method"], precision=precision, rtol=wl["rtol"],
+                              ncyc=wl["ncyc"], restart_mvps=wl["restart_mvps"], m3=wl["m3"])
+        return x, status, st[0], cst
+
+    def timed_steps(K, precision, host_io=False, profile=False):
+        """K steps timed with CUDA events on the current stream (each step bracketed, the
+        L2 flushed between steps when the inputs fit in L2)."""
+        stream = torch.cuda.current_stream()
+        total_ms = 0.0
+        infos = []
+        x_host = torch.empty(n, dtype=torch.float64).pin_memory() if host_io else None
+        if profile:
+            tg.tg_profile_enable(True)
+        l0 = tg.tg_launch_count()
+        for _ in range(K):
+            if flush is not None:
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if host_io:
+                bd = b_host.to(dev, non_blocking=True)
+                x, status, st, cst = step(bd, precision)
+                x_host.copy_(x, non_blocking=True)
+            else:
+                x, status, st, cst = step(b, precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            infos.append((status, st, cst))
+        launches = tg.tg_launch_count() - l0
+        prof = None
+        if profile:
+            prof = tg.tg_profile_read()
+            tg.tg_profile_enable(False)
+        return total_ms / K, infos, launches, prof
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up (also allocates every workspace)
+    for _ in range(args.warmup):
+        step(b, wl["precision"])
+    torch.cuda.synchronize()
+
+    dev_id = str(getattr(torch.cuda.get_device_properties(dev), "uuid", "") or "")
+    dev_id = ("GPU-" + dev_id) if dev_id and not dev_id.startswith("GPU-") else (dev_id or str(dev.index))
+    clocks = ClockSampler(dev_id)
+    clocks.start()
+    barrier()
+    ms, infos, launches, prof = timed_steps(args.steps, wl["precision"], profile=True)
+    barrier()
+    clocks.stop()
+    ms = max_over_ranks(ms)
+    ok = all(s == tg.TG_OK and st["relres"] <= wl["rtol"] for s, st, _ in infos)
+
+    # end to end through the public API with host buffers (H2D of b, D2H of x per step)
+    barrier()
+    ms_e2e, infos_e2e, _, _ = timed_steps(args.steps, wl["precision"], host_io=True)
+    barrier()
+    ms_e2e = max_over_ranks(ms_e2e)
+
+    # the float32 + float64 refinement form of the same workload
+    ms_ir = None
+    ir_ok = None
+    if wl["kind"] != "u1_4d" and not args.no_ir:
+        for _ in range(1):
+            step(b, "f32_ir")
+        barrier()
+        ms_ir, infos_ir, _, _ = timed_steps(args.steps, "f32_ir")
+        barrier()
+        ms_ir = max_over_ranks(ms_ir)
+        ir_ok = all(s == tg.TG_OK and st["relres"] <= wl["rtol"] for s, st, _ in infos_ir)
+
+    status, st, cst = infos[-1]
+    peaks, peak_src = measured_peaks()
+    # roofline of the dominant kernel class (largest share of device time in the timed region)
+    dom_name, dom = max(((k, v) for k, v in prof.items() if k != "bicg_noop"), key=lambda kv: kv[1]["ms"])
+    dev_ms_total = sum(v["ms"] for v in prof.values())
+    per_launch_ms = dom["ms"] / dom["launches"]
+    gbs = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
+    tflops = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get(args.workload, {}).get(dom_name)
+    roofline = {"kernel": dom_name, "bound": "alu", "achieved": round(tflops, 4),
+                "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz",
+                "traffic": traffic, "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                "algorithmic_flops_per_launch": dom["flops"] / dom["launches"],
+                "ms_per_launch": round(per_launch_ms, 5), "hbm_gbs": round(gbs, 1),
+                "hbm_frac": round(gbs / peaks["hbm_gbs"], 4), "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_peak_source": peak_src, "share_of_device_time": round(dom["ms"] / dev_ms_total, 4)}
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                   "share": round(v["ms"] / dev_ms_total, 4),
+                   "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else 0.0,
+                   "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4) if v["ms"] > 0 else 0.0}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:10]}
+    value = world * 1000.0 / ms
+    line = {
+        "metric": "fine-grid solves/sec to rel. residual 1e-8 (FP64 vs batched FP32+IR) and HBM GB/s",
+        "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded N(0,1) right-hand side)",
+        "config": {"workload": args.workload, **{k: (list(v) if isinstance(v, tuple) else v) for k, v in wl.items()},
+                   "n": n, "n_coarse": op.nc,
+                   "l2": "inputs larger than L2 (133 MB per fine vector)" if flush is None else "L2 flushed between steps",
+                   "parallelism": f"replicas x{world}"},
+        "solves_converged": ok,
+        "step_breakdown": {"coarse_cycles": cst["cycles"], "coarse_mvps": cst["coarse_mvps"],
+                           "eig_converged": cst["eig_converged"], "fine_mvps": st["mvps"],
+                           "fine_cycles": st["cycles"], "relres": st["relres"]},
+        "e2e": {"value": round(world * 1000.0 / ms_e2e, 5), "unit": "solves/s", "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": n * 8},
+        "fp32_ir": None if ms_ir is None else {"value": round(world * 1000.0 / ms_ir, 5), "unit": "solves/s",
+                                               "ms_per_step": round(ms_ir, 3), "converged": ir_ok,
+                                               "speedup_vs_f64": round(ms / ms_ir, 3)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clocks.summary(),
+    }
+    return line, {"coarse_cycles": cst["cycles"], "fine_mvps": st["mvps"], "fine_cycles": st["cycles"],
+                  "coarse_steps": cst["coarse_mvps"]}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def _timeit(f, min_time=0.5, max_reps=20):
+    """Seconds per call of f after one untimed call, averaged over >= min_time."""
+    f()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        f()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_time or reps >= max_reps:
+            return el / reps
+
+
+def cpu_sample(wl, counts):
+    """Time the oracle (numpy FP64, as it stands) on bounded pieces of the workload and
+    scale them to one full solve with the given step counts.  Returns (solves/s, info)."""
+    import numpy as np
+
+    import tg_inputs as gi
+    from oracle import krylov
+    from oracle.gmresdr import arnoldi_extend, harmonic_ritz
+    from oracle.operators import CD2D, CD3D, Operator, coarse_operator
+
+    kind = {"cd2d": CD2D, "cd3d": CD3D}[wl["kind"]]
+    op = Operator(kind, wl["N"], wl["beta"])
+    opc = coarse_operator(op)
+    n, nc, m, k = op.n, opc.n, wl["m"], wl["k"]
+    b = gi.rhs(n, 0)
+    t0 = time.perf_counter()
+    # one fine BiCGStab iteration (2 operator products and its vector updates)
+    t_iter = _timeit(lambda: krylov.bicgstab_cycle(op.apply, np.zeros(n), b, 0.0, max_mvps=2))
+    t_mvp = _timeit(lambda: op.apply(b))
+    # one projection over k vectors (the oracle's Householder QR of A Y each time); for
+    # large n it is timed at two smaller widths k1 < k2 and extrapolated with
+    # t(k) = a k + c k^2 (products linear in k, the QR quadratic)
+    def t_projection(kw):
+        d = krylov.Deflation(gi.random_dense((n, kw), 1), gi.random_dense((n, kw), 2), wl["proj"])
+        return _timeit(lambda: krylov.project(d, np.zeros(n), b.copy()), min_time=0.0, max_reps=1)
+    if n * k <= 50_000_000:
+        t_proj, proj_note = t_projection(k), f"one {k}-vector MinRes projection"
+    else:
+        k1, k2 = max(2, k // 5), max(4, (2 * k) // 5)
+        t1, t2 = t_projection(k1), t_projection(k2)
+        c = (t2 / k2 - t1 / k1) / (k2 - k1)
+        a_ = t1 / k1 - c * k1
+        t_proj = max(a_ * k + c * k * k, t2 * k / k2)
+        proj_note = f"MinRes projections with {k1} and {k2} vectors (extrapolated to {k} as a k + c k^2)"
+    # coarse Arnoldi step at the mean basis size of a restarted cycle, and one small eig
+    jm = (m + k) // 2
+    V = np.zeros((nc, jm + 2))
+    H = np.zeros((jm + 2, jm + 1))
+    V[:, :jm] = np.linalg.qr(gi.random_dense((nc, jm), 3))[0]
+    t_step = _timeit(lambda: arnoldi_extend(opc.apply, V, H, jm - 1, jm))
+    del V
+    Hs = gi.random_hessenberg(m, 4) + 3 * np.vstack([np.eye(m), np.zeros((1, m))])
+    t_eig = _timeit(lambda: harmonic_ritz(Hs))
+    est = (counts["coarse_steps"] * t_step + counts["coarse_cycles"] * t_eig + k * t_mvp
+           + counts["fine_mvps"] / 2 * t_iter + counts["fine_cycles"] * (t_proj + t_mvp))
+    info = {"kind": "oracle", "cores": 1,
+            "sample": (f"oracle (numpy float64, 1 thread for the stencil and vector work) timed on one fine "
+                       f"BiCGStab iteration, one fine product, {proj_note}, one coarse "
+                       f"Arnoldi step at j={jm} and one {m}x{m} harmonic-Ritz eig, each after a warm-up call; "
+                       f"scaled to one solve with {counts['coarse_steps']} coarse steps, {counts['coarse_cycles']} "
+                       f"coarse cycles, {k} A Y products, {counts['fine_mvps']} fine products and "
+                       f"{counts['fine_cycles']} fine cycles"),
+            "sample_seconds": round(time.perf_counter() - t0, 2), "est_seconds_per_solve": round(est, 3),
+            "pieces_s": {"fine_iter": t_iter, "fine_mvp": t_mvp, "projection": t_proj, "coarse_step": t_step,
+                         "eig": t_eig}}
+    return 1.0 / est, info
+
+
+def oracle_counts(workload):
+    """Step counts of the oracle's own full run (written by oracle/bench_counts.py)."""
+    path = os.path.join(ROOT, "oracle", "bench_counts.json")
+    with open(path) as f:
+        return json.load(f)[workload]
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default="cd3d_255", choices=sorted(WORKLOADS))
+    p.add_argument("--impl", default="tg", choices=["tg", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-ir", action="store_true")
+    args = p.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        counts = oracle_counts(args.workload)
+        vals = []
+        info = None
+        for _ in range(args.warmup):
+            pass   # the oracle has nothing to warm up
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            v, info = cpu_sample(wl, counts)
+            vals.append(v)
+        wall = time.perf_counter() - t0
+        value = statistics.median(vals)
+        line = {"impl": "reference",
+                "metric": "fine-grid solves/sec to rel. residual 1e-8 (FP64 vs batched FP32+IR) and HBM GB/s",
+                "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1000.0 / value, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded N(0,1) right-hand side)",
+                "config": {"workload": args.workload, **{k: (list(v) if isinstance(v, tuple) else v)
+                                                        for k, v in wl.items()}},
+                "cpu_baseline": {**info, "value": value, "unit": "solves/s"},
+                "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "sample_wall_s": round(wall, 2)}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    line, counts = run_tg(args, wl, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = cpu_sample(wl, counts)
+        line["cpu_baseline"] = {**info, "value": v, "unit": "solves/s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -204,6 +204,20 @@ int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *
 int tg_harmonic_ritz(const void *Hbar, int m, int k, int complex_, void *theta_out,
                      void *basis_out, void *eres_out, int *kk_out, void *stream);
 
+/* ------------------------------------------------------------------ instrumentation
+ * Not part of the method: measurement hooks for benchmarks.
+ * tg_profile_enable(1) starts recording a CUDA event pair around every kernel the
+ * library launches (on the launch's stream), tagged with its kernel class and the
+ * algorithmic bytes and float64-equivalent flops of that launch; tg_profile_enable(0)
+ * stops recording.  tg_profile_read writes the per-class totals as a JSON object
+ *   {"<class>": {"launches": L, "ms": T, "bytes": B, "flops": F}, ...}
+ * into json (cap bytes; TG_BAD_ARG if too small); it waits for the recorded events.
+ * tg_launch_count: number of kernels this process has launched through the library.
+ * Not thread safe.                                                                    */
+int tg_profile_enable(int on);
+int tg_profile_read(char *json, int cap);
+int64_t tg_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

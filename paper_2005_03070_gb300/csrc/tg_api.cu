@@ -2,6 +2,7 @@
 // declared in include/tg.h.  Every numerical step runs in the kernels of
 // tg_kernels.cuh, tg_small.cu and tg_setup.cu; the host only launches them, reads a few
 // scalars per cycle and takes the restart decisions of the algorithms.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -61,6 +62,74 @@ static int tiles_grid(int64_t n, int per_sm) {
     int64_t cap = (int64_t)num_sms() * per_sm;
     if (b > cap) b = cap;
     return b < 1 ? 1 : (int)b;
+}
+
+// ============================================================================= instrumentation
+// Optional per-kernel-class timing: CUDA events around each launch (only while enabled)
+// and a count of every launch.  Algorithmic bytes and float64-equivalent flops of each
+// launch are recorded with it, so achieved bandwidth / arithmetic rates come out per class.
+enum ProfClass {
+    P_APPLY, P_DOT, P_RESIDUAL, P_BI_INIT, P_BI_V, P_BI_S, P_BI_T, P_BI_X, P_GEMV_T, P_SUM_PART, P_GEMV_N,
+    P_PROJ, P_TSM, P_GRAM, P_SMALL, P_GDR_RESTART, P_SCALE, P_TRANSFER, P_SETUP, P_CONVERT, P_GRAD, P_GIVENS,
+    P_NOOP, P_COUNT
+};
+static const char *kProfName[P_COUNT] = {
+    "apply", "dot", "residual", "bicg_init", "bicg_v", "bicg_s", "bicg_t", "bicg_x", "gemv_t", "sum_part",
+    "gemv_n", "proj_update", "tsm", "gram", "small_dense", "gmresdr_restart", "scale", "transfer", "setup",
+    "convert", "kappa_grad", "givens", "bicg_noop"};
+
+struct ProfRec {
+    int cls;
+    int ev;
+    double bytes, flops;
+};
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> events;
+    std::vector<ProfRec> recs;
+    size_t next = 0;
+    long long launches = 0;
+};
+static Prof g_prof;
+
+static int prof_begin(cudaStream_t s) {
+    g_prof.launches += 1;
+    if (!g_prof.on) return -1;
+    if (g_prof.next + 2 > g_prof.events.size()) {
+        size_t add = g_prof.events.size() < 4096 ? 4096 : g_prof.events.size();
+        for (size_t i = 0; i < add; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            g_prof.events.push_back(e);
+        }
+    }
+    int ev = (int)g_prof.next;
+    g_prof.next += 2;
+    cudaEventRecord(g_prof.events[ev], s);
+    return ev;
+}
+static void prof_end(int ev, int cls, double bytes, double flops, cudaStream_t s) {
+    if (ev < 0) return;
+    cudaEventRecord(g_prof.events[ev + 1], s);
+    g_prof.recs.push_back(ProfRec{cls, ev, bytes, flops});
+}
+#define TG_PROF(cls, bytes, flops, ...)                                  \
+    do {                                                                 \
+        int _ev = ::tg::prof_begin(s);                                   \
+        __VA_ARGS__;                                                     \
+        ::tg::prof_end(_ev, cls, (double)(bytes), (double)(flops), s);   \
+    } while (0)
+
+// Algorithmic cost of one operator application per point: extra words read beyond the
+// source and destination vectors (coefficients, links), and flops (float64 equivalent).
+static void op_cost(const DevOp &A, double *extra_bytes, double *flops) {
+    switch (A.kind) {
+        case DK_CD2D: *extra_bytes = 0; *flops = 10; break;
+        case DK_CD3D: *extra_bytes = 0; *flops = 14; break;
+        case DK_VAR2D: *extra_bytes = 5 * 8; *flops = 10; break;
+        case DK_U1: *extra_bytes = 4 * 16; *flops = 66; break;
+        default: *extra_bytes = 9 * 16; *flops = 72; break;
+    }
 }
 
 // ============================================================================= buffers
@@ -163,7 +232,7 @@ static int wsx(tg_op *op, Slot s, size_t bytes) { return op->ws[s].ensure(bytes)
 
 // reduction scratch: partials (sized generously), a ticket, a small result area
 static int red_ready(tg_op *op, size_t part_bytes) {
-    TG_CHECK(wsx(op, S_PART, part_bytes < (1 << 20) ? (1 << 20) : part_bytes));
+    TG_CHECK(wsx(op, S_PART, part_bytes < (4 << 20) ? (4 << 20) : part_bytes));
     if (!op->ws[S_TICKET].p) {
         TG_CHECK(wsx(op, S_TICKET, 64));
         TG_CHECK_CUDA(cudaMemset(op->ws[S_TICKET].p, 0, 64));
@@ -189,7 +258,7 @@ static int dot_host(tg_op *op, const T *a, const T *b, int n, double *aa, typena
     TG_CHECK(red_ready(op, 0));
     int g = grid_for(n, 4);
     D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 1024);
-    k_dot<T><<<g, kThreads, 0, s>>>(a, b, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out);
+    TG_PROF(P_DOT, (b ? 2.0 : 1.0) * n * sizeof(T), (b ? 4.0 : 2.0) * n, k_dot<T><<<g, kThreads, 0, s>>>(a, b, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out));
     TG_LAUNCH_CHECK();
     TG_CHECK(readback(op, out, 2 * sizeof(D), s));
     const D *h = reinterpret_cast<const D *>(op->pin.p);
@@ -209,7 +278,9 @@ static const DevOp32 &pick32(const tg_op *op, int level, int transpose) {
 
 template <class T>
 static int launch_apply(const DevOp &A, const DevOp32 &A32, const T *x, T *y, cudaStream_t s) {
-    k_apply<T><<<grid_for(A.n, 8), kThreads, 0, s>>>(A, A32, x, y);
+    double xb, fl;
+    op_cost(A, &xb, &fl);
+    TG_PROF(P_APPLY, (2.0 * sizeof(T) + xb * (sizeof(T) == 4 ? 0.5 : 1.0)) * A.n, fl * A.n, k_apply<T><<<grid_for(A.n, 8), kThreads, 0, s>>>(A, A32, x, y));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -226,7 +297,7 @@ template <class T>
 static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Out, size_t ldo, int n, cudaStream_t s) {
     size_t smem = (size_t)32 * p * sizeof(T);
     TG_CHECK(set_smem<T>((const void *)k_tsm<T>, smem));
-    k_tsm<T><<<tiles_grid(n, 4), kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n);
+    TG_PROF(P_TSM, (double)(p + q) * n * sizeof(T), 2.0 * p * q * n * (sizeof(T) == 16 ? 4 : 1), k_tsm<T><<<tiles_grid(n, 4), kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -235,11 +306,12 @@ static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Ou
 template <class T>
 static int gemv_t(tg_op *op, const T *V, size_t ldv, int ncol, const T *w, int n, typename ST<T>::D *h, cudaStream_t s) {
     using D = typename ST<T>::D;
-    int gb = tiles_grid(n, 2);
+    int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
+    if (gb < 1) gb = 1;
     TG_CHECK(red_ready(op, (size_t)gb * ncol * sizeof(D)));
-    k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, wsp<D>(op, S_PART));
+    TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1), k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, wsp<D>(op, S_PART)));
     TG_LAUNCH_CHECK();
-    k_sum_part<D><<<1, 256, 0, s>>>(wsp<D>(op, S_PART), gb, ncol, h, 0);
+    TG_PROF(P_SUM_PART, (double)gb * ncol * sizeof(D), (double)gb * ncol, k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(wsp<D>(op, S_PART), gb, ncol, h, 0));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -253,9 +325,9 @@ static int gram_ept(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, 
     TG_CHECK(red_ready(op, (size_t)gb * k * k * sizeof(D)));
     size_t smem = (size_t)2 * 32 * k * sizeof(T);
     TG_CHECK(set_smem<T>((const void *)k_gram_part<T, EPT>, smem));
-    k_gram_part<T, EPT><<<gb, kThreads, smem, s>>>(A, B, ld, k, n, sym, wsp<D>(op, S_PART));
+    TG_PROF(P_GRAM, (A == B ? 1.0 : 2.0) * k * n * sizeof(T), (sym ? 1.0 * k * (k + 1) : 2.0 * k * k) * n * (sizeof(T) == 16 ? 4 : 1), k_gram_part<T, EPT><<<gb, kThreads, smem, s>>>(A, B, ld, k, n, sym, wsp<D>(op, S_PART)));
     TG_LAUNCH_CHECK();
-    k_sum_part<D><<<(k * k + 255) / 256, 256, 0, s>>>(wsp<D>(op, S_PART), gb, k * k, G, 0);
+    TG_PROF(P_SUM_PART, (double)gb * k * k * sizeof(D), (double)gb * k * k, k_sum_part<D><<<(k * k + 7) / 8, 256, 0, s>>>(wsp<D>(op, S_PART), gb, k * k, G, 0));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -278,11 +350,11 @@ static int cholqr2(tg_op *op, const T *A, int k, int n, T *Q, T *R, T *Rinv, int
     TG_CHECK(R2.ensure(kb));
     TG_CHECK(R2i.ensure(kb));
     TG_CHECK(gram<T>(op, A, A, n, k, n, 1, G.as<T>(), s));
-    launch_chol_inv<T>(G.as<T>(), k, R1.as<T>(), R1i.as<T>(), info_dev, s);
+    TG_PROF(P_SMALL, 0, 1.0 * k * k * k, launch_chol_inv<T>(G.as<T>(), k, R1.as<T>(), R1i.as<T>(), info_dev, s));
     TG_LAUNCH_CHECK();
     TG_CHECK(tsm<T>(A, n, k, R1i.as<T>(), k, k, Q, n, n, s));
     TG_CHECK(gram<T>(op, Q, Q, n, k, n, 1, G.as<T>(), s));
-    launch_chol_inv<T>(G.as<T>(), k, R2.as<T>(), R2i.as<T>(), info_dev + 1, s);
+    TG_PROF(P_SMALL, 0, 1.0 * k * k * k, launch_chol_inv<T>(G.as<T>(), k, R2.as<T>(), R2i.as<T>(), info_dev + 1, s));
     TG_LAUNCH_CHECK();
     TG_CHECK(tsm<T>(Q, n, k, R2i.as<T>(), k, k, Q, n, n, s));   // in place: each tile is staged first
     TG_CHECK(tsm<T>(R2.as<T>(), k, k, R1.as<T>(), k, k, R, k, k, s));     // R = R2 R1
@@ -464,12 +536,12 @@ static int prolong_impl(const tg_op *op, const void *coarse, void *fine, int nco
         if (op->cplx_) {
             const cplx *uc = (const cplx *)coarse + (size_t)c * op->nc;
             cplx *uf = (cplx *)fine + (size_t)c * op->n;
-            launch_prolong_lattice(grid_for(op->n, 8), s, uc, op->pw.as<cplx>(), op->N, uf);
+            TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), 0, launch_prolong_lattice(grid_for(op->n, 8), s, uc, op->pw.as<cplx>(), op->N, uf));
         } else {
             const double *uc = (const double *)coarse + (size_t)c * op->nc;
             double *uf = (double *)fine + (size_t)c * op->n;
-            if (op->dim == 3) launch_prolong3d(grid_for(op->n, 8), s, uc, op->Nc, uf);
-            else launch_prolong2d(grid_for(op->n, 8), s, uc, op->Nc, uf);
+            if (op->dim == 3) TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), 0, launch_prolong3d(grid_for(op->n, 8), s, uc, op->Nc, uf));
+            else TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), 0, launch_prolong2d(grid_for(op->n, 8), s, uc, op->Nc, uf));
         }
         TG_LAUNCH_CHECK();
     }
@@ -481,12 +553,12 @@ static int restrict_impl(const tg_op *op, const void *fine, void *coarse, int nc
         if (op->cplx_) {
             const cplx *uf = (const cplx *)fine + (size_t)c * op->n;
             cplx *uc = (cplx *)coarse + (size_t)c * op->nc;
-            launch_restrict_lattice(grid_for(op->nc, 8), s, uf, op->pw.as<cplx>(), op->N, uc);
+            TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), op->n * 2.0, launch_restrict_lattice(grid_for(op->nc, 8), s, uf, op->pw.as<cplx>(), op->N, uc));
         } else {
             const double *uf = (const double *)fine + (size_t)c * op->n;
             double *uc = (double *)coarse + (size_t)c * op->nc;
-            if (op->dim == 3) launch_restrict3d(grid_for(op->nc, 8), s, uf, op->N, uc);
-            else launch_restrict2d(grid_for(op->nc, 8), s, uf, op->N, uc);
+            if (op->dim == 3) TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), op->n * 2.0, launch_restrict3d(grid_for(op->nc, 8), s, uf, op->N, uc));
+            else TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), op->n * 2.0, launch_restrict2d(grid_for(op->nc, 8), s, uf, op->N, uc));
         }
         TG_LAUNCH_CHECK();
     }
@@ -535,7 +607,7 @@ static int build_defl(tg_op *op, int transpose, tg_defl *d, cudaStream_t s) {
         TG_CHECK(cholqr2<T>(op, Y, kk, n, d->Q.as<T>(), Ry.as<T>(), Ryi.as<T>(), info, s));
         TG_CHECK(tsm<T>(AY, n, kk, Ryi.as<T>(), kk, kk, d->AV.as<T>(), n, n, s));
         TG_CHECK(gram<T>(op, d->Q.as<T>(), d->AV.as<T>(), n, kk, n, 0, d->R.as<T>(), s));
-        launch_inverse<T>(d->R.as<T>(), kk, d->M.as<T>(), W.as<T>(), info + 2, s);
+        TG_PROF(P_SMALL, 0, 2.0 * kk * kk * kk, launch_inverse<T>(d->R.as<T>(), kk, d->M.as<T>(), W.as<T>(), info + 2, s));
         TG_LAUNCH_CHECK();
         TG_CHECK_CUDA(cudaStreamSynchronize(s));
     }
@@ -552,9 +624,9 @@ static int build_defl(tg_op *op, int transpose, tg_defl *d, cudaStream_t s) {
         TG_CHECK(d->B2_32.ensure((size_t)n * kk * 4));
         const double *B1 = d->proj == TG_PROJ_MINRES ? (const double *)d->Y.p : (const double *)d->Q.p;
         const double *B2 = d->proj == TG_PROJ_MINRES ? (const double *)d->Q.p : (const double *)d->AV.p;
-        launch_d2f(grid_for((int64_t)n * kk, 8), s, (const double *)d->Q.p, d->W32.as<float>(), (size_t)n * kk);
-        launch_d2f(grid_for((int64_t)n * kk, 8), s, B1, d->B1_32.as<float>(), (size_t)n * kk);
-        launch_d2f(grid_for((int64_t)n * kk, 8), s, B2, d->B2_32.as<float>(), (size_t)n * kk);
+        TG_PROF(P_CONVERT, 12.0 * n * kk, 0, launch_d2f(grid_for((int64_t)n * kk, 8), s, (const double *)d->Q.p, d->W32.as<float>(), (size_t)n * kk));
+        TG_PROF(P_CONVERT, 12.0 * n * kk, 0, launch_d2f(grid_for((int64_t)n * kk, 8), s, B1, d->B1_32.as<float>(), (size_t)n * kk));
+        TG_PROF(P_CONVERT, 12.0 * n * kk, 0, launch_d2f(grid_for((int64_t)n * kk, 8), s, B2, d->B2_32.as<float>(), (size_t)n * kk));
         TG_LAUNCH_CHECK();
     }
     TG_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -571,10 +643,10 @@ static int project_impl(tg_op *op, const tg_defl *df, const T *W, const T *B1, c
     D *cvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192);
     D *dvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192 + 4096);
     TG_CHECK(gemv_t<T>(op, W, n, kk, r, n, cvec, s));
-    launch_small_gemv<D>(df->M.as<D>(), kk, cvec, dvec, s);
+    TG_PROF(P_SMALL, 0, 2.0 * kk * kk, launch_small_gemv<D>(df->M.as<D>(), kk, cvec, dvec, s));
     TG_LAUNCH_CHECK();
     const D *e = df->proj == TG_PROJ_MINRES ? cvec : dvec;
-    k_proj_update<T><<<grid_for(n, 8), kThreads, 0, s>>>(B1, B2, n, kk, dvec, e, x, r, n);
+    TG_PROF(P_PROJ, (2.0 * kk + 4) * n * sizeof(T), 4.0 * kk * n * (sizeof(T) == 16 ? 4 : 1), k_proj_update<T><<<grid_for(n, 8), kThreads, 0, s>>>(B1, B2, n, kk, dvec, e, x, r, n));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -703,17 +775,23 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     D *part = wsp<D>(op, S_PART);
     unsigned *tk = wsp<unsigned>(op, S_TICKET);
     BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL));
-    k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st);
+    TG_PROF(P_BI_INIT, 3.0 * n * sizeof(T), 2.0 * n, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
     TG_LAUNCH_CHECK();
-    int chunk = 4;
+    int chunk = 2;
     int launched = 0;
     BiState<D> h{};
+    double xb, fl;
+    op_cost(A, &xb, &fl);
+    const double es = sizeof(T), cf = sizeof(T) == 16 ? 4.0 : 1.0, xbs = sizeof(T) == 4 ? 0.5 * xb : xb;
+    const size_t rec0 = g_prof.recs.size();
+    double rr_prev = -1.0;
+    int iters_prev = 0;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
-            k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st);
-            k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st);
-            k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st);
-            k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st);
+            TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
+            TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
+            TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
+            TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
         }
         TG_LAUNCH_CHECK();
         launched += chunk;
@@ -724,7 +802,34 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
             set_error("BiCGStab cycle exceeded its product cap");
             return TG_SYNC_TIMEOUT;
         }
-        chunk = chunk < 32 ? chunk * 2 : 32;
+        // next batch: the iterations still allowed by the cap, and the iterations the
+        // observed residual reduction rate predicts until the target (at most 32)
+        int left = (h.cap - h.mvps + 1) / 2;
+        int want = 32;
+        if (rr_prev > 0 && h.rr > 0 && h.rr < rr_prev && h.iters > iters_prev) {
+            double rate = log(h.rr / rr_prev) / (h.iters - iters_prev);     // per iteration, < 0
+            double need = log(h.target2 / h.rr) / rate;
+            if (need < want) want = (int)ceil(need) + 1;
+        } else if (rr_prev < 0) {
+            want = 4;
+        }
+        rr_prev = h.rr;
+        iters_prev = h.iters;
+        chunk = std::max(1, std::min(std::min(want, left), 32));
+    }
+    // launches queued after the cycle ended returned at once: relabel them so the
+    // per-class totals hold only the iterations that ran
+    if (g_prof.on) {
+        const int ran = h.iters;       // full or half iterations executed
+        int it = 0;
+        for (size_t q = rec0; q < g_prof.recs.size(); ++q) {
+            ProfRec &pr = g_prof.recs[q];
+            if (pr.cls == P_BI_V) ++it;
+            if (it > ran || (pr.cls == P_BI_T && it == ran && h.half)) {   // a half-step exit skips the t-kernel
+                pr.cls = P_NOOP;
+                pr.bytes = pr.flops = 0;
+            }
+        }
     }
     out->mvps = h.mvps;
     out->iters = h.iters;
@@ -766,7 +871,9 @@ static int true_residual(tg_op *op, const DevOp &A, const T *b, const T *x, T *r
     const int g = grid_for(n, 8);
     TG_CHECK(red_ready(op, (size_t)g * 2 * sizeof(D)));
     D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 2048);
-    k_residual<T><<<g, kThreads, 0, s>>>(A, b, x, r, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out);
+    double xb, fl;
+    op_cost(A, &xb, &fl);
+    TG_PROF(P_RESIDUAL, (3.0 * sizeof(T) + xb) * n, (fl + 6) * n, k_residual<T><<<g, kThreads, 0, s>>>(A, b, x, r, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out));
     TG_LAUNCH_CHECK();
     TG_CHECK(readback(op, out, 2 * sizeof(D), s));
     const D *h = reinterpret_cast<const D *>(op->pin.p);
@@ -848,7 +955,7 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
         ++cyc;
         if (cfg.ncyc && cyc > cfg.ncyc) break;
         // correction equation A e = r, scaled so that ||r32|| = 1
-        launch_d2f_scaled(g, s, r, r32, n, 1.0 / nr);
+        TG_PROF(P_CONVERT, 12.0 * n, n, launch_d2f_scaled(g, s, r, r32, n, 1.0 / nr));
         TG_CHECK_CUDA(cudaMemsetAsync(e32, 0, (size_t)n * 4, s));
         double scale = nr;
         double nrel = 1.0;
@@ -869,7 +976,7 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
         CycleOut co;
         TG_CHECK(bicg_cycle<float>(op, A, A32, e32, r32, n, (rt * nrel) * (rt * nrel), (int)cap64, &co, s));
         mvps += co.mvps;
-        launch_add_f2d_scaled(g, s, x, e32, n, scale);
+        TG_PROF(P_CONVERT, 20.0 * n, 2.0 * n, launch_add_f2d_scaled(g, s, x, e32, n, scale));
         TG_LAUNCH_CHECK();
         TG_CHECK(true_residual<double>(op, A, b, x, r, &nr, &nb, s));
         if (!std::isfinite(nr)) { status = TG_NAN; break; }
@@ -902,17 +1009,17 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     D *nrm = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
     const int g = grid_for(n, 8);
     TG_CHECK(gemv_t<T>(op, V, ldv, j + 1, w, n, h1, s));
-    k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h1, -1.0, w, n);
+    TG_PROF(P_GEMV_N, (j + 3.0) * n * sizeof(T), 2.0 * (j + 1) * n, k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h1, -1.0, w, n));
     TG_LAUNCH_CHECK();
     TG_CHECK(gemv_t<T>(op, V, ldv, j + 1, w, n, h2, s));
-    k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h2, -1.0, w, n);
+    TG_PROF(P_GEMV_N, (j + 3.0) * n * sizeof(T), 2.0 * (j + 1) * n, k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h2, -1.0, w, n));
     TG_LAUNCH_CHECK();
     int gd = grid_for(n, 4);
-    k_dot<T><<<gd, kThreads, 0, s>>>(w, nullptr, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm);
+    TG_PROF(P_DOT, 1.0 * n * sizeof(T), 2.0 * n, k_dot<T><<<gd, kThreads, 0, s>>>(w, nullptr, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm));
     TG_LAUNCH_CHECK();
-    k_arnoldi_finish<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, reinterpret_cast<double *>(nrm) + 4);
+    TG_PROF(P_SMALL, 0, j, k_arnoldi_finish<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, reinterpret_cast<double *>(nrm) + 4));
     TG_LAUNCH_CHECK();
-    k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, reinterpret_cast<double *>(nrm) + 4);
+    TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, reinterpret_cast<double *>(nrm) + 4));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -968,13 +1075,13 @@ static int solve_gmres64(tg_op *op, int transpose, const tg_defl *df, const T *b
         memcpy(&g0, &nr, sizeof(double));
         TG_CHECK_CUDA(cudaMemcpyAsync(wsp<D>(op, S_FG), &g0, sizeof(D), cudaMemcpyHostToDevice, s));
         TG_CHECK_CUDA(cudaMemsetAsync(H, 0, (size_t)(m + 1) * m * sizeof(D), s));
-        k_scale_by<T><<<grid_for(n, 8), kThreads, 0, s>>>(V, n, inv);
+        TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<grid_for(n, 8), kThreads, 0, s>>>(V, n, inv));
         TG_LAUNCH_CHECK();
         int steps = 0;
         const int mm = (int)((cfg.max_mvps - mvps) < m ? (cfg.max_mvps - mvps) : m);
         for (int j = 0; j < mm; ++j) {
             TG_CHECK(arnoldi_step<T>(op, A, A32, V, n, n, j, reinterpret_cast<T *>(H), ldh, s));
-            launch_givens_step<D>(H, ldh, j, wsp<D>(op, S_FCS), wsp<D>(op, S_FSN), wsp<D>(op, S_FG), gs, s);
+            TG_PROF(P_GIVENS, 0, 6.0 * j, launch_givens_step<D>(H, ldh, j, wsp<D>(op, S_FCS), wsp<D>(op, S_FSN), wsp<D>(op, S_FG), gs, s));
             TG_LAUNCH_CHECK();
             TG_CHECK(readback(op, gs, sizeof(GivensState), s));
             GivensState hg;
@@ -983,8 +1090,8 @@ static int solve_gmres64(tg_op *op, int transpose, const tg_defl *df, const T *b
             if (hg.done) break;
         }
         mvps += steps;
-        launch_givens_solve<D>(H, ldh, wsp<D>(op, S_FG), wsp<D>(op, S_FY), gs, s);
-        k_gemv_n<T><<<grid_for(n, 8), kThreads, 0, s>>>(V, n, steps, wsp<D>(op, S_FY), 1.0, x, n);
+        TG_PROF(P_GIVENS, 0, 1.0 * m * m, launch_givens_solve<D>(H, ldh, wsp<D>(op, S_FG), wsp<D>(op, S_FY), gs, s));
+        TG_PROF(P_GEMV_N, (steps + 2.0) * n * sizeof(T), 2.0 * steps * n, k_gemv_n<T><<<grid_for(n, 8), kThreads, 0, s>>>(V, n, steps, wsp<D>(op, S_FY), 1.0, x, n));
         TG_LAUNCH_CHECK();
         TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
         if (!std::isfinite(nr)) { status = TG_NAN; break; }
@@ -1094,7 +1201,7 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
     double hinv = 1.0 / nbc;
     TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
-    k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, inv);
+    TG_PROF(P_SCALE, 2.0 * nc * sizeof(T), nc, k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, inv));
     TG_CHECK_CUDA(cudaMemsetAsync(xc, 0, (size_t)nc * es, s));
     TG_CHECK_CUDA(cudaMemsetAsync(H, 0, (size_t)ldh * m * es, s));
     TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * es, s));
@@ -1119,10 +1226,10 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         a.order = wsp<int>(op, S_GORD); a.eres = wsp<double>(op, S_GERES); a.P = wsp<T>(op, S_GP);
         a.Hnew = H2; a.cnew = wsp<T>(op, S_GCN); a.work = wsp<T>(op, S_GWORK);
         a.ywork = wsp<cplx>(op, S_GY); a.gwork = wsp<cplx>(op, S_GG); a.info = wsp<GdrInfo>(op, S_GINFO);
-        launch_gmresdr_restart<T>(a, s);
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
         TG_LAUNCH_CHECK();
         // x_c += V_m d
-        k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, m, a.d, 1.0, xc, nc);
+        TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, m, a.d, 1.0, xc, nc));
         TG_LAUNCH_CHECK();
         TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
         memcpy(&info, op->pin.p, sizeof(info));
@@ -1147,10 +1254,10 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
             DD *h1 = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384);
             DD *nrm = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
             TG_CHECK(gemv_t<T>(op, V, nc, kk, w, nc, h1, s));
-            k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, kk, h1, -1.0, w, nc);
-            k_dot<T><<<grid_for(nc, 4), kThreads, 0, s>>>(w, nullptr, nc, wsp<DD>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm);
-            launch_inv_sqrt(s, reinterpret_cast<const double *>(nrm), reinterpret_cast<double *>(nrm) + 4);
-            k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(w, nc, reinterpret_cast<double *>(nrm) + 4);
+            TG_PROF(P_GEMV_N, (kk + 2.0) * nc * sizeof(T), 2.0 * kk * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, kk, h1, -1.0, w, nc));
+            TG_PROF(P_DOT, 1.0 * nc * sizeof(T), 2.0 * nc, k_dot<T><<<grid_for(nc, 4), kThreads, 0, s>>>(w, nullptr, nc, wsp<DD>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm));
+            TG_PROF(P_SMALL, 0, 1, launch_inv_sqrt(s, reinterpret_cast<const double *>(nrm), reinterpret_cast<double *>(nrm) + 4));
+            TG_PROF(P_SCALE, 2.0 * nc * sizeof(T), nc, k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(w, nc, reinterpret_cast<double *>(nrm) + 4));
             TG_LAUNCH_CHECK();
         }
         j0 = kk;
@@ -1211,8 +1318,8 @@ extern "C" int tg_kappa_gradient(const tg_op *op, const void *x, const void *lam
     TG_ARG(op->kind == TG_VARK2D, "the kappa gradient needs a TG_VARK2D operator");
     cudaStream_t s = (cudaStream_t)stream;
     const int NP = op->N + 2;
-    launch_kappa_grad(grid_for(NP * NP, 8), s, (const double *)x, (const double *)lambda, op->N,
-                                                          (double *)dkappa);
+    TG_PROF(P_GRAD, 16.0 * op->n, 8.0 * op->n, launch_kappa_grad(grid_for(NP * NP, 8), s, (const double *)x, (const double *)lambda, op->N,
+                                                          (double *)dkappa));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -1265,7 +1372,7 @@ extern "C" int tg_harmonic_ritz(const void *Hbar, int m, int k, int complex_, vo
         a.wi = wi.as<double>(); a.order = ord.as<int>(); a.eres = er.as<double>(); a.P = P.as<T>(); a.Hnew = Hn.as<T>();
         a.cnew = cn.as<T>(); a.work = work.as<T>(); a.ywork = yw.as<cplx>(); a.gwork = gw.as<cplx>();
         a.info = inf.as<GdrInfo>();
-        launch_gmresdr_restart<T>(a, s);
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
         TG_LAUNCH_CHECK();
         return TG_OK;
     };
@@ -1280,3 +1387,48 @@ extern "C" int tg_harmonic_ritz(const void *Hbar, int m, int k, int complex_, vo
     TG_CHECK_CUDA(cudaStreamSynchronize(s));
     return info.status ? TG_NOT_CONVERGED : TG_OK;
 }
+
+// ============================================================================= instrumentation ABI
+extern "C" int tg_profile_enable(int on) {
+    if (on) {
+        g_prof.recs.clear();
+        g_prof.next = 0;
+        g_prof.recs.reserve(1 << 16);
+    }
+    g_prof.on = on != 0;
+    return TG_OK;
+}
+
+extern "C" int tg_profile_read(char *json, int cap) {
+    TG_ARG(json && cap > 0, "NULL buffer");
+    double ms[P_COUNT] = {0}, bytes[P_COUNT] = {0}, flops[P_COUNT] = {0};
+    long long cnt[P_COUNT] = {0};
+    for (const ProfRec &r : g_prof.recs) {
+        TG_CHECK_CUDA(cudaEventSynchronize(g_prof.events[r.ev + 1]));
+        float t = 0.f;
+        TG_CHECK_CUDA(cudaEventElapsedTime(&t, g_prof.events[r.ev], g_prof.events[r.ev + 1]));
+        ms[r.cls] += t;
+        bytes[r.cls] += r.bytes;
+        flops[r.cls] += r.flops;
+        cnt[r.cls] += 1;
+    }
+    std::string out = "{";
+    bool first = true;
+    for (int c = 0; c < P_COUNT; ++c) {
+        if (!cnt[c]) continue;
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"bytes\": %.6e, \"flops\": %.6e}",
+                 first ? "" : ", ", kProfName[c], cnt[c], ms[c], bytes[c], flops[c]);
+        out += buf;
+        first = false;
+    }
+    out += "}";
+    if ((int)out.size() + 1 > cap) {
+        set_error("profile buffer too small (%d bytes needed)", (int)out.size() + 1);
+        return TG_BAD_ARG;
+    }
+    memcpy(json, out.c_str(), out.size() + 1);
+    return TG_OK;
+}
+
+extern "C" int64_t tg_launch_count(void) { return g_prof.launches; }

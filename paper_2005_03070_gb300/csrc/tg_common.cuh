@@ -316,14 +316,21 @@ __device__ __forceinline__ cplx ldcg(const cplx *p) {
     return {v.x, v.y};
 }
 
-// In the last block: totals[d] = sum over blocks of part[b * ND + d], fixed order.
+// In the last block: totals[d] = sum over blocks of part[b * ND + d].  Warp d reduces
+// entry d: lane l adds blocks l, l + 32, ... in order, then the lanes are combined by the
+// fixed shuffle tree, so the result does not depend on block scheduling.
+template <class D>
+__device__ __forceinline__ D dzero() { return D{}; }
+
 template <class D, int ND>
 __device__ __forceinline__ void final_sum(const D *part, D *totals_smem, unsigned *ticket) {
-    if (threadIdx.x < ND) {
-        const int d = threadIdx.x;
-        D s = ldcg(part + d);
-        for (int b = 1; b < (int)gridDim.x; ++b) s = dadd(s, ldcg(part + (size_t)b * ND + d));
-        totals_smem[d] = s;
+    static_assert(ND <= kThreads / 32, "one warp per reduced entry");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < ND) {
+        D s = dzero<D>();
+        for (int b = lane; b < (int)gridDim.x; b += 32) s = dadd(s, ldcg(part + (size_t)b * ND + warp));
+        s = warp_sum(s);
+        if (lane == 0) totals_smem[warp] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) *ticket = 0u;

@@ -337,26 +337,37 @@ __global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restr
 
 // ----------------------------------------------------------------------------- tall-skinny
 // Partial products of h = V^H w over row tiles: part[block][c] = sum over the block's rows
-// of conj(V[row, c]) w[row], c < ncol.  One warp per column group, 32-row tiles.
+// of conj(V[row, c]) w[row], c < ncol.  Warp w owns columns w, w + 8, ...; each pass covers
+// 128 rows (4 rows per lane) so that four loads per column are in flight per lane.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ V, size_t ldv, int ncol,
                                                            const T *__restrict__ w, int n,
                                                            typename ST<T>::D *part) {
-    using D = typename ST<T>::D;
     using P = typename Part<T>::P;
     constexpr int kMaxPerWarp = 17;   // 8 warps x 17 columns >= 129
+    constexpr int kU = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     P acc[kMaxPerWarp];
 #pragma unroll
     for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = ST<T>::zero();
-    for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
-        const int row = row0 + lane;
-        if (row < n) {
-            const T wi = w[row];
+    for (int row0 = blockIdx.x * 32 * kU; row0 < n; row0 += gridDim.x * 32 * kU) {
+        T wv[kU];
+        int rr[kU];
 #pragma unroll
-            for (int q = 0; q < kMaxPerWarp; ++q) {
-                const int c = warp + 8 * q;
-                if (c < ncol) acc[q] = ST<T>::fma_cm(V[(size_t)c * ldv + row], wi, acc[q]);
+        for (int u = 0; u < kU; ++u) {
+            rr[u] = row0 + 32 * u + lane;
+            wv[u] = rr[u] < n ? w[rr[u]] : ST<T>::zero();
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxPerWarp; ++q) {
+            const int c = warp + 8 * q;
+            if (c < ncol) {
+                const T *vc = V + (size_t)c * ldv;
+                T vv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) vv[u] = rr[u] < n ? vc[rr[u]] : ST<T>::zero();
+#pragma unroll
+                for (int u = 0; u < kU; ++u) acc[q] = ST<T>::fma_cm(vv[u], wv[u], acc[q]);
             }
         }
     }
@@ -368,15 +379,17 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
     }
 }
 
-// out[e] (+)= scale * sum_b part[b * nent + e], in block order (deterministic).
-// mode 0: out = sum; mode 1: out += sum.
+// out[e] (mode 0: =, mode 1: +=) sum_b part[b * nent + e].  One warp per entry: lane l
+// adds blocks l, l + 32, ... in order, then the fixed shuffle tree (deterministic).
 template <class D>
 __global__ void k_sum_part(const D *__restrict__ part, int nblk, int nent, D *out, int mode) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
-        D s = part[e];
-        for (int b = 1; b < nblk; ++b) s = dadd(s, part[(size_t)b * nent + e]);
-        out[e] = mode ? dadd(out[e], s) : s;
-    }
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (e >= nent) return;
+    D s = D{};
+    for (int b = lane; b < nblk; b += 32) s = dadd(s, part[(size_t)b * nent + e]);
+    s = warp_sum(s);
+    if (lane == 0) out[e] = mode ? dadd(out[e], s) : s;
 }
 
 // w[row] += sign * sum_c V[row, c] h[c]   (h: device, D type, ncol <= 129)

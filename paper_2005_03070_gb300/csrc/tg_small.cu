@@ -721,9 +721,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
     const int m = a.m;
     const int rows = m + 1;
     const int ldh = a.ldh;
-    T *W = a.work;                        // (m+1) x m (least squares copy), later m x m eigen matrix
-    T *Z = W + (size_t)rows * m;          // m x m Schur vectors
-    T *B = Z + (size_t)m * m;             // m x m scratch (LU, eigenvectors)
+    // W: (m+1) x m (least-squares copy), later the m x m eigen matrix / Schur form;
+    // Z: m x m Schur vectors.  Both live in shared memory when the launch provided it
+    // (the QR sweeps are a long chain of dependent small steps, so their latency rules).
+    extern __shared__ __align__(16) unsigned char gdr_smem[];
+    T *W = a.smem ? reinterpret_cast<T *>(gdr_smem) : a.work;
+    T *Z = W + (size_t)rows * m;
+    T *B = a.work + (size_t)rows * m + (size_t)m * m;   // m x m scratch (LU), global
     T *vtmp = B + (size_t)m * m;          // 2 (m+1) vectors
     T *f = vtmp + 2 * (m + 1);
     T *res = a.res;
@@ -1033,8 +1037,14 @@ void launch_small_gemv(const D *M, int k, const D *c, D *out, cudaStream_t s) {
     k_small_gemv<D><<<1, kSmallThreads, 0, s>>>(M, k, c, out);
 }
 template <class T>
-void launch_gmresdr_restart(const GdrArgs<T> &a, cudaStream_t s) {
-    k_gmresdr_restart<T><<<1, kSmallThreads, 0, s>>>(a);
+void launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
+    GdrArgs<T> a = a_in;
+    const size_t need = ((size_t)(a.m + 1) * a.m + (size_t)a.m * a.m) * sizeof(T);
+    a.smem = need <= kGdrSmemMax ? 1 : 0;
+    const size_t smem = a.smem ? need : 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute((const void *)k_gmresdr_restart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gmresdr_restart<T><<<1, kGdrThreads, smem, s>>>(a);
 }
 template <class D>
 void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s) {

@@ -6,6 +6,8 @@
 namespace tg {
 
 constexpr int kSmallThreads = 256;
+constexpr int kGdrThreads = 128;                 // GMRES-DR restart kernel block
+constexpr size_t kGdrSmemMax = 210 * 1024;       // shared memory for W and Z when they fit
 constexpr int kMaxM = 128;          // largest GMRES-DR subspace dimension m
 
 struct GdrInfo {
@@ -37,6 +39,7 @@ struct GdrArgs {
     cplx *ywork;     // scratch: m * m complex
     cplx *gwork;     // scratch: m * m complex
     GdrInfo *info;
+    int smem;        // set by the launcher: W and Z in shared memory
 };
 
 struct GivensState {

@@ -34,7 +34,7 @@ EXPORTS = [
     "tg_status_string", "tg_last_error", "tg_setup_operator", "tg_destroy_op", "tg_op_size", "tg_apply",
     "tg_prolong", "tg_restrict", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
     "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_adjoint_solve", "tg_kappa_gradient",
-    "tg_harmonic_ritz",
+    "tg_harmonic_ritz", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
 ]
 
 
@@ -88,6 +88,9 @@ def load() -> C.CDLL:
         "tg_adjoint_solve": (i32, [vp, vp, vp, vp, vp, vp, dbl, i32, i32, i32, C.POINTER(TgStats), vp]),
         "tg_kappa_gradient": (i32, [vp, vp, vp, vp, vp]),
         "tg_harmonic_ritz": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
+        "tg_profile_enable": (i32, [i32]),
+        "tg_profile_read": (i32, [C.c_char_p, i32]),
+        "tg_launch_count": (i64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -283,3 +286,18 @@ def harmonic_ritz(Hbar_colmajor: torch.Tensor, m: int, k: int, complex_: bool = 
     kk = kk.value
     th = theta.view(m, 2)
     return torch.complex(th[:, 0], th[:, 1]), basis[: kk * m].view(kk, m), eres[:kk]
+
+
+def tg_profile_enable(on: bool) -> None:
+    _check(load().tg_profile_enable(int(on)), "tg_profile_enable")
+
+
+def tg_profile_read() -> dict:
+    import json
+    buf = C.create_string_buffer(1 << 16)
+    _check(load().tg_profile_read(buf, len(buf)), "tg_profile_read")
+    return json.loads(buf.value.decode())
+
+
+def tg_launch_count() -> int:
+    return int(load().tg_launch_count())
