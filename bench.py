@@ -37,6 +37,10 @@ WORKLOADS = {
     "cd3d_255": dict(kind="cd3d", N=255, beta=(2.0, 1.0, 0.5), m=60, k=30, nev=30, rtolev=1e-2, rtol_c=1e-8,
                      max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20,
                      restart_mvps=0, m3=20),
+    # a smaller case of the same kernels for profiler captures (coarse basis 418 MB > L2)
+    "cd3d_191": dict(kind="cd3d", N=191, beta=(2.0, 1.0, 0.5), m=60, k=30, nev=30, rtolev=1e-2, rtol_c=1e-8,
+                     max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20,
+                     restart_mvps=0, m3=20),
     "cd2d_127": dict(kind="cd2d", N=127, beta=(1.0,), m=30, k=15, nev=15, rtolev=1e-4, rtol_c=1e-8,
                      max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=0,
                      restart_mvps=60, m3=20),

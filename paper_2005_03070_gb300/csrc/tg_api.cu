@@ -71,12 +71,12 @@ static int tiles_grid(int64_t n, int per_sm) {
 enum ProfClass {
     P_APPLY, P_DOT, P_RESIDUAL, P_BI_INIT, P_BI_V, P_BI_S, P_BI_T, P_BI_X, P_GEMV_T, P_SUM_PART, P_GEMV_N,
     P_PROJ, P_TSM, P_GRAM, P_SMALL, P_GDR_RESTART, P_SCALE, P_TRANSFER, P_SETUP, P_CONVERT, P_GRAD, P_GIVENS,
-    P_NOOP, P_COUNT
+    P_NOOP, P_REORTH, P_COUNT
 };
 static const char *kProfName[P_COUNT] = {
     "apply", "dot", "residual", "bicg_init", "bicg_v", "bicg_s", "bicg_t", "bicg_x", "gemv_t", "sum_part",
     "gemv_n", "proj_update", "tsm", "gram", "small_dense", "gmresdr_restart", "scale", "transfer", "setup",
-    "convert", "kappa_grad", "givens", "bicg_noop"};
+    "convert", "kappa_grad", "givens", "bicg_noop", "reorth_pass"};
 
 struct ProfRec {
     int cls;
@@ -84,6 +84,7 @@ struct ProfRec {
     double bytes, flops;
 };
 struct Prof {
+    long long gdr_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     bool on = false;
     std::vector<cudaEvent_t> events;
     std::vector<ProfRec> recs;
@@ -1001,25 +1002,41 @@ template <class T>
 static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int n, int j, T *H, int ldh,
                         cudaStream_t s) {
     using D = typename ST<T>::D;
+    // w = A v_j; classical Gram-Schmidt with selective re-orthogonalisation (the second
+    // pass runs only when the first cancelled more than half of ||w||^2; decided on the
+    // device, so the host never waits)
     T *w = V + (size_t)(j + 1) * ldv;
     TG_CHECK(launch_apply<T>(A, A32, V + (size_t)j * ldv, w, s));
     TG_CHECK(red_ready(op, 0));
-    D *h1 = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384);
-    D *h2 = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384 + 4096);
-    D *nrm = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
+    char *sm = wsp<char>(op, S_SMALL);
+    D *h1 = reinterpret_cast<D *>(sm + 16384);           // j+2 entries: V_j^H w and ||w||^2
+    D *h2 = reinterpret_cast<D *>(sm + 16384 + 4096);
+    double *nrm = reinterpret_cast<double *>(sm + 16384 + 8192);
+    double *inv = nrm + 4;
+    int *flag = reinterpret_cast<int *>(sm + 16384 + 8192 + 64);
     const int g = grid_for(n, 8);
-    TG_CHECK(gemv_t<T>(op, V, ldv, j + 1, w, n, h1, s));
-    TG_PROF(P_GEMV_N, (j + 3.0) * n * sizeof(T), 2.0 * (j + 1) * n, k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h1, -1.0, w, n));
-    TG_LAUNCH_CHECK();
-    TG_CHECK(gemv_t<T>(op, V, ldv, j + 1, w, n, h2, s));
-    TG_PROF(P_GEMV_N, (j + 3.0) * n * sizeof(T), 2.0 * (j + 1) * n, k_gemv_n<T><<<g, kThreads, 0, s>>>(V, ldv, j + 1, h2, -1.0, w, n));
-    TG_LAUNCH_CHECK();
-    int gd = grid_for(n, 4);
-    TG_PROF(P_DOT, 1.0 * n * sizeof(T), 2.0 * n, k_dot<T><<<gd, kThreads, 0, s>>>(w, nullptr, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm));
-    TG_LAUNCH_CHECK();
-    TG_PROF(P_SMALL, 0, j, k_arnoldi_finish<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, reinterpret_cast<double *>(nrm) + 4));
-    TG_LAUNCH_CHECK();
-    TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, reinterpret_cast<double *>(nrm) + 4));
+    const int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
+    const int ncol = j + 1;
+    D *part = wsp<D>(op, S_PART);
+    unsigned *tk = wsp<unsigned>(op, S_TICKET);
+    TG_CHECK(red_ready(op, (size_t)gb * (ncol + 1) * sizeof(D)));
+    part = wsp<D>(op, S_PART);
+    // pass 1: h1 = [V_j, w]^H w
+    TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * (ncol + 1) * n * (sizeof(T) == 16 ? 4 : 1),
+            k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol + 1, w, n, part));
+    TG_PROF(P_SUM_PART, (double)gb * (ncol + 1) * sizeof(D), (double)gb * (ncol + 1),
+            k_sum_part<D><<<(ncol + 1 + 7) / 8, 256, 0, s>>>(part, gb, ncol + 1, h1, 0));
+    TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
+            k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h1, w, n, nullptr, part, tk, nrm, h1 + ncol, flag, 0.5));
+    // pass 2 (only when flagged)
+    // (the device decides; these launches return at once when not needed, so they are
+    // timed in their own class without algorithmic bytes)
+    TG_PROF(P_REORTH, 0.0, 0.0, k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, part, flag));
+    TG_PROF(P_REORTH, 0.0, 0.0, k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gb, ncol, h2, 0, flag));
+    TG_PROF(P_REORTH, 0.0, 0.0,
+            k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h2, w, n, flag, part, tk, nrm, nullptr, nullptr, 0.0));
+    TG_PROF(P_SMALL, 0, j, k_arnoldi_finish2<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, inv));
+    TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, inv));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -1233,6 +1250,8 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         TG_LAUNCH_CHECK();
         TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
         memcpy(&info, op->pin.p, sizeof(info));
+        if (g_prof.on)
+            for (int q = 0; q < 8; ++q) g_prof.gdr_phase[q] += info.phase[q];
         kk = info.kk;
         if (info.status != 0) {
             set_error("harmonic Ritz QR iteration did not converge");
@@ -1393,6 +1412,7 @@ extern "C" int tg_profile_enable(int on) {
     if (on) {
         g_prof.recs.clear();
         g_prof.next = 0;
+        for (int q = 0; q < 8; ++q) g_prof.gdr_phase[q] = 0;
         g_prof.recs.reserve(1 << 16);
     }
     g_prof.on = on != 0;
@@ -1421,6 +1441,13 @@ extern "C" int tg_profile_read(char *json, int cap) {
                  first ? "" : ", ", kProfName[c], cnt[c], ms[c], bytes[c], flops[c]);
         out += buf;
         first = false;
+    }
+    {
+        char buf[256];
+        snprintf(buf, sizeof(buf), "%s\"gmresdr_restart_phase_cycles\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld]",
+                 first ? "" : ", ", g_prof.gdr_phase[0], g_prof.gdr_phase[1], g_prof.gdr_phase[2], g_prof.gdr_phase[3],
+                 g_prof.gdr_phase[4], g_prof.gdr_phase[5], g_prof.gdr_phase[6], g_prof.gdr_phase[7]);
+        out += buf;
     }
     out += "}";
     if ((int)out.size() + 1 > cap) {

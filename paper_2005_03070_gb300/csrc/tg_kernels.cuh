@@ -342,8 +342,9 @@ __global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restr
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ V, size_t ldv, int ncol,
                                                            const T *__restrict__ w, int n,
-                                                           typename ST<T>::D *part) {
+                                                           typename ST<T>::D *part, const int *cond = nullptr) {
     using P = typename Part<T>::P;
+    if (cond && !*cond) return;     // a skipped re-orthogonalisation pass
     constexpr int kMaxPerWarp = 17;   // 8 warps x 17 columns >= 129
     constexpr int kU = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -374,18 +375,25 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
 #pragma unroll
     for (int q = 0; q < kMaxPerWarp; ++q) {
         const int c = warp + 8 * q;
-        P s = warp_sum(acc[q]);
-        if (lane == 0 && c < ncol) part[(size_t)blockIdx.x * ncol + c] = to_d(s);
+        if (c < ncol) {       // reduce only the columns this warp owns
+            P s = warp_sum(acc[q]);
+            if (lane == 0) part[(size_t)blockIdx.x * ncol + c] = to_d(s);
+        }
     }
 }
 
 // out[e] (mode 0: =, mode 1: +=) sum_b part[b * nent + e].  One warp per entry: lane l
 // adds blocks l, l + 32, ... in order, then the fixed shuffle tree (deterministic).
 template <class D>
-__global__ void k_sum_part(const D *__restrict__ part, int nblk, int nent, D *out, int mode) {
+__global__ void k_sum_part(const D *__restrict__ part, int nblk, int nent, D *out, int mode,
+                           const int *cond = nullptr) {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (e >= nent) return;
+    if (cond && !*cond) {           // skipped pass: its coefficients are zero
+        if (lane == 0 && !mode) out[e] = D{};
+        return;
+    }
     D s = D{};
     for (int b = lane; b < nblk; b += 32) s = dadd(s, part[(size_t)b * nent + e]);
     s = warp_sum(s);
@@ -405,6 +413,60 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n(const T *__restrict__ V, si
         T acc = ST<T>::zero();
         for (int c = 0; c < ncol; ++c) acc = axpy(KS<T>::of(hs[c]), V[(size_t)c * ldv + row], acc);
         w[row] = sign > 0 ? dadd(w[row], acc) : sub(w[row], acc);
+    }
+}
+
+// Arnoldi orthogonalisation pass: w -= V h (ncol columns), then ||w||^2 (deterministic);
+// the last block writes nrm2_out[0] and, when flag_out is given, the selective
+// re-orthogonalisation decision (Daniel, Gragg, Kaufman and Stewart): a second pass is
+// needed when the pass cancelled more than half of ||w||^2, i.e. ||w_new||^2 < eta2 ||w||^2
+// with ||w||^2 = real(nrm2_before[0]).  cond: skip the whole kernel when *cond == 0.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gemv_n_norm(const T *__restrict__ V, size_t ldv, int ncol,
+                                                           const typename ST<T>::D *__restrict__ h,
+                                                           T *__restrict__ w, int n, const int *cond,
+                                                           typename ST<T>::D *part, unsigned *ticket,
+                                                           double *nrm2_out,
+                                                           const typename ST<T>::D *nrm2_before,
+                                                           int *flag_out, double eta2) {
+    using D = typename ST<T>::D;
+    using P = typename Part<T>::P;
+    if (cond && !*cond) return;
+    __shared__ D hs[130];
+    __shared__ D red[(kThreads / 32)];
+    __shared__ D tot[1];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    P acc[1] = {ST<T>::zero()};
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        T a = ST<T>::zero();
+        for (int c = 0; c < ncol; ++c) a = axpy(KS<T>::of(hs[c]), V[(size_t)c * ldv + row], a);
+        const T wv = sub(w[row], a);
+        w[row] = wv;
+        acc[0] = ST<T>::fma_cm(wv, wv, acc[0]);
+    }
+    block_reduce_store<P, D, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<D, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            const double nn = dreal(tot[0]);
+            nrm2_out[0] = nn;
+            if (flag_out) flag_out[0] = (nn < eta2 * dreal(nrm2_before[0])) ? 1 : 0;
+        }
+    }
+}
+
+// Hbar column j: H[i] = h1[i] + h2[i] (i <= j), H[j+1] = sqrt(nrm2[0]), inv[0] = 1/H[j+1].
+template <class T>
+__global__ void k_arnoldi_finish2(const typename ST<T>::D *h1, const typename ST<T>::D *h2, const double *nrm2,
+                                  int j, T *Hcol, double *inv) {
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) Hcol[i] = dadd(h1[i], h2[i]);
+    if (threadIdx.x == 0) {
+        const double nn = sqrt(nrm2[0]);
+        T hv = ST<T>::zero();
+        *reinterpret_cast<double *>(&hv) = nn;
+        Hcol[j + 1] = hv;
+        inv[0] = nn > 0 ? 1.0 / nn : 0.0;
     }
 }
 

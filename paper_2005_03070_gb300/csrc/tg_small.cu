@@ -79,47 +79,86 @@ __device__ T house(const T *x, int stride, int len, T *v, T *beta_out) {
     return Cx<T>::div(subt(beta, x0), beta);
 }
 
+// Block-parallel Householder vector: the same reflector as house(), with the norm summed
+// by all threads (fixed order: per-thread strided partials, then warp shuffles, then
+// warps in order) and one reciprocal instead of a division per element.  x and v may
+// not overlap.  Every thread of the block must call it; returns tau, *beta_out.
+template <class T>
+__device__ T house_par(const T *x, int len, T *v, T *beta_out) {
+    __shared__ double red_s[32];
+    __shared__ T tau_sh, beta_sh, inv_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double p = 0.0;
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) p += Cx<T>::ab2(x[i]);
+    p = warp_sum(p);
+    if (lane == 0) red_s[warp] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double nrm2 = 0.0;
+        for (int w = 0; w < nw; ++w) nrm2 += red_s[w];
+        T x0 = x[0];
+        if (nrm2 == 0.0) {
+            tau_sh = Cx<T>::zero();
+            beta_sh = x0;
+            inv_sh = Cx<T>::zero();
+        } else {
+            double a0 = sqrt(Cx<T>::ab2(x0));
+            double alpha = sqrt(Cx<T>::ab2(x0) + nrm2);
+            T ph = a0 > 0 ? Cx<T>::sc(1.0 / a0, x0) : Cx<T>::one();
+            T beta = Cx<T>::sc(-alpha, ph);
+            T v0 = subt(x0, beta);
+            T iv0 = Cx<T>::div(Cx<T>::one(), v0);
+            beta_sh = beta;
+            inv_sh = iv0;
+            // tau = (beta - x0) / beta = -v0 / beta
+            tau_sh = Cx<T>::div(Cx<T>::sc(-1.0, v0), beta);
+        }
+    }
+    __syncthreads();
+    const T inv = inv_sh;
+    const bool zero = Cx<T>::ab2(tau_sh) == 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x)
+        v[i] = i == 0 ? Cx<T>::one() : (zero ? Cx<T>::zero() : Cx<T>::mul(x[i], inv));
+    *beta_out = beta_sh;
+    const T tau = tau_sh;
+    __syncthreads();
+    return tau;
+}
+
 // ----------------------------------------------------------------------------- least squares
 // Householder QR of the (rows x m) matrix W (copy of Hbar) and of the right-hand side;
 // d = R^{-1} (Q^H c)[0..m-1].  All threads participate.
 template <class T>
 __device__ void lsq_solve(T *W, int ldw, int rows, int m, T *rhs, T *d, T *v) {
-    __shared__ T tau_s;
-    __shared__ T beta_s;
     for (int j = 0; j < m; ++j) {
         const int len = rows - j;
-        if (threadIdx.x == 0) {
-            T beta;
-            tau_s = house<T>(W + j + (size_t)j * ldw, 1, len, v, &beta);
-            beta_s = beta;
-        }
-        __syncthreads();
-        const T tau = tau_s;
-        // apply to columns j+1..m-1 and to rhs (column index m)
+        T beta;
+        const T tau = house_par<T>(W + j + (size_t)j * ldw, len, v, &beta);
+        // apply H = I - tau v v^H to columns j+1..m-1 and to rhs (column index m)
         for (int c = j + 1 + threadIdx.x; c <= m; c += blockDim.x) {
             T *col = (c < m) ? (W + (size_t)c * ldw) : rhs;
             T s = Cx<T>::zero();
             for (int i = 0; i < len; ++i) s = add(s, Cx<T>::mul(Cx<T>::cj(v[i]), col[j + i]));
-            s = Cx<T>::mul(tau, s);      // H col = col - tau v (v^H col), H x = beta e_1
+            s = Cx<T>::mul(tau, s);
             for (int i = 0; i < len; ++i) col[j + i] = subt(col[j + i], Cx<T>::mul(v[i], s));
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            W[j + (size_t)j * ldw] = beta_s;
-            for (int i = 1; i < len; ++i) W[j + i + (size_t)j * ldw] = Cx<T>::zero();
-        }
+        for (int i = threadIdx.x; i < len; i += blockDim.x) W[j + i + (size_t)j * ldw] = i == 0 ? beta : Cx<T>::zero();
         __syncthreads();
     }
-    // back substitution (thread 0; m <= 128)
-    if (threadIdx.x == 0) {
-        for (int i = m - 1; i >= 0; --i) {
-            T s = rhs[i];
-            for (int c = i + 1; c < m; ++c) s = subt(s, Cx<T>::mul(W[i + (size_t)c * ldw], d[c]));
+    // back substitution R d = rhs, column oriented: d_i, then all rows above updated at once
+    __shared__ T di_s;
+    for (int i = m - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) {
             T rii = W[i + (size_t)i * ldw];
-            d[i] = Cx<T>::ab2(rii) > 0 ? Cx<T>::div(s, rii) : Cx<T>::zero();
+            di_s = Cx<T>::ab2(rii) > 0 ? Cx<T>::div(rhs[i], rii) : Cx<T>::zero();
+            d[i] = di_s;
         }
+        __syncthreads();
+        const T di = di_s;
+        for (int r = threadIdx.x; r < i; r += blockDim.x) rhs[r] = subt(rhs[r], Cx<T>::mul(W[r + (size_t)i * ldw], di));
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // Solve A^H f = e_last for the m x m matrix A (column-major, ld lda) by Gaussian
@@ -133,62 +172,70 @@ __device__ void solve_adjoint_last(const T *A, int lda, int m, T *B, T *f, int *
     for (int i = threadIdx.x; i < m; i += blockDim.x) f[i] = (i == m - 1) ? Cx<T>::one() : Cx<T>::zero();
     __syncthreads();
     __shared__ int p_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = 0; j < m; ++j) {
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
+            // partial pivoting: the largest |B[i, j]|, ties to the smallest i
+            double best = -1.0;
             int p = j;
-            double best = Cx<T>::ab2(B[j + (size_t)j * m]);
-            for (int i = j + 1; i < m; ++i) {
+            for (int i = j + lane; i < m; i += 32) {
                 double a = Cx<T>::ab2(B[i + (size_t)j * m]);
                 if (a > best) { best = a; p = i; }
             }
-            p_s = p;
-            piv[j] = p;
-            if (p != j) {
-                for (int c = 0; c < m; ++c) {
-                    T t = B[j + (size_t)c * m];
-                    B[j + (size_t)c * m] = B[p + (size_t)c * m];
-                    B[p + (size_t)c * m] = t;
-                }
-                T t = f[j]; f[j] = f[p]; f[p] = t;
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_down_sync(0xffffffffu, best, o);
+                int op = __shfl_down_sync(0xffffffffu, p, o);
+                if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
             }
+            if (lane == 0) { p_s = p; piv[j] = p; }
+        }
+        __syncthreads();
+        const int p = p_s;
+        if (p != j) {
+            for (int c = threadIdx.x; c < m; c += blockDim.x) {
+                T t = B[j + (size_t)c * m];
+                B[j + (size_t)c * m] = B[p + (size_t)c * m];
+                B[p + (size_t)c * m] = t;
+            }
+            if (threadIdx.x == 0) { T t = f[j]; f[j] = f[p]; f[p] = t; }
         }
         __syncthreads();
         const T pivv = B[j + (size_t)j * m];
         const bool ok = Cx<T>::ab2(pivv) > 0;
+        const T ipiv = ok ? Cx<T>::div(Cx<T>::one(), pivv) : Cx<T>::zero();
         for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
             if (!ok) break;
-            T l = Cx<T>::div(B[i + (size_t)j * m], pivv);
+            T l = Cx<T>::mul(B[i + (size_t)j * m], ipiv);
             for (int c = j + 1; c < m; ++c) B[i + (size_t)c * m] = subt(B[i + (size_t)c * m], Cx<T>::mul(l, B[j + (size_t)c * m]));
             f[i] = subt(f[i], Cx<T>::mul(l, f[j]));
             B[i + (size_t)j * m] = Cx<T>::zero();
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        for (int i = m - 1; i >= 0; --i) {
-            T s = f[i];
-            for (int c = i + 1; c < m; ++c) s = subt(s, Cx<T>::mul(B[i + (size_t)c * m], f[c]));
+    // back substitution U f = f, column oriented
+    __shared__ T fi_s;
+    for (int i = m - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) {
             T bii = B[i + (size_t)i * m];
-            f[i] = Cx<T>::ab2(bii) > 0 ? Cx<T>::div(s, bii) : Cx<T>::zero();
+            fi_s = Cx<T>::ab2(bii) > 0 ? Cx<T>::div(f[i], bii) : Cx<T>::zero();
+            f[i] = fi_s;
         }
+        __syncthreads();
+        const T fi = fi_s;
+        for (int r = threadIdx.x; r < i; r += blockDim.x) f[r] = subt(f[r], Cx<T>::mul(B[r + (size_t)i * m], fi));
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // ----------------------------------------------------------------------------- Hessenberg form
 // A (m x m, ld m) <- Q^H A Q upper Hessenberg; Z <- Q (Z must hold I on entry).
 template <class T>
 __device__ void hessenberg(T *A, int m, T *Z, T *v) {
-    __shared__ T tau_s;
     for (int j = 0; j + 2 < m; ++j) {
         const int len = m - j - 1;
-        if (threadIdx.x == 0) {
-            T beta;
-            tau_s = house<T>(A + (j + 1) + (size_t)j * m, 1, len, v, &beta);
-        }
-        __syncthreads();
-        const T tau = tau_s;
-        if (Cx<T>::ab2(tau) == 0.0) { __syncthreads(); continue; }
+        T beta;
+        const T tau = house_par<T>(A + (j + 1) + (size_t)j * m, len, v, &beta);
+        if (Cx<T>::ab2(tau) == 0.0) continue;
         // left: rows j+1..m-1, columns j..m-1: A <- H A = A - tau v (v^H A)
         for (int c = j + threadIdx.x; c < m; c += blockDim.x) {
             T *col = A + (size_t)c * m + j + 1;
@@ -230,25 +277,35 @@ __device__ int real_schur(double *H, int m, double *Z) {
     int its = 0, total = 0;
     while (true) {
         // thread 0 finds the active block and decides what to do
-        if (threadIdx.x == 0) {
-            int hi = hi_s;
+        if (threadIdx.x < 32) {
+            // the active block: the largest l <= hi with a negligible H[l, l-1] (0 if none),
+            // found by warp 0 with a ballot over the candidates
+            const int hi = hi_s;
+            __syncwarp();          // every lane has read hi_s before lane 0 may update it
+            int l = 0;
+            if (hi > 0) {
+                for (int base = hi; base > 0 && l == 0; base -= 32) {
+                    const int cand = base - (int)threadIdx.x;
+                    bool neg = false;
+                    if (cand > 0) {
+                        double s = fabs(H[(cand - 1) + (size_t)(cand - 1) * m]) + fabs(H[cand + (size_t)cand * m]);
+                        if (s == 0.0) s = 1.0;
+                        neg = fabs(H[cand + (size_t)(cand - 1) * m]) <= kEps * s;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, neg);
+                    if (bal) l = base - (__ffs(bal) - 1);     // lowest lane = largest index
+                }
+            }
+            if (threadIdx.x == 0 && l > 0) H[l + (size_t)(l - 1) * m] = 0.0;
+            if (threadIdx.x == 0) {
             act_s = 0;
             if (hi < 0) act_s = -1;
             else {
-                int l = hi;
-                while (l > 0) {
-                    double s = fabs(H[(l - 1) + (size_t)(l - 1) * m]) + fabs(H[l + (size_t)l * m]);
-                    if (s == 0.0) s = 1.0;
-                    if (fabs(H[l + (size_t)(l - 1) * m]) <= kEps * s) {
-                        H[l + (size_t)(l - 1) * m] = 0.0;
-                        break;
-                    }
-                    --l;
-                }
                 l_s = l;
                 if (l == hi) { hi_s = hi - 1; act_s = 1; }
                 else if (l == hi - 1) { act_s = 2; }   // 2x2 block: standardise below
                 else act_s = 3;                         // QR sweep on l..hi
+            }
             }
         }
         __syncthreads();
@@ -337,11 +394,21 @@ __device__ int real_schur(double *H, int m, double *Z) {
         for (int kk = l; kk <= hi - 1; ++kk) {
             const int nr = (kk <= hi - 2) ? 3 : 2;
             if (threadIdx.x == 0) {
-                double x[3] = {x_s, y_s, z_s};
-                double beta;
-                double v[3];
-                tau3 = house<double>(x, 1, nr, v, &beta);
-                vv[0] = 1.0; vv[1] = v[1]; vv[2] = nr == 3 ? v[2] : 0.0;
+                // 3 x 3 (or 2 x 2) reflector: beta = -sign(x) ||(x,y,z)||, v = (1, y/v0, z/v0),
+                // tau = -v0/beta with v0 = x - beta; one division: r = 1/(v0 beta)
+                const double x0 = x_s, y0 = y_s, z0 = nr == 3 ? z_s : 0.0;
+                const double sn = y0 * y0 + z0 * z0;
+                if (sn == 0.0) {
+                    tau3 = 0.0;
+                } else {
+                    const double beta = -copysign(sqrt(x0 * x0 + sn), x0);
+                    const double v0 = x0 - beta;
+                    const double r = 1.0 / (v0 * beta);
+                    vv[0] = 1.0;
+                    vv[1] = y0 * beta * r;
+                    vv[2] = z0 * beta * r;
+                    tau3 = -v0 * v0 * r;
+                }
             }
             __syncthreads();
             const double tau = tau3;
@@ -400,24 +467,32 @@ __device__ int complex_schur(cplx *H, int m, cplx *Z) {
     __syncthreads();
     int its = 0, total = 0;
     while (true) {
-        if (threadIdx.x == 0) {
-            int hi = hi_s;
-            act_s = 0;
-            if (hi <= 0) act_s = -1;
-            else {
-                int l = hi;
-                while (l > 0) {
-                    double s = cabs_(H[(l - 1) + (size_t)(l - 1) * m]) + cabs_(H[l + (size_t)l * m]);
-                    if (s == 0.0) s = 1.0;
-                    if (cabs_(H[l + (size_t)(l - 1) * m]) <= kEps * s) {
-                        H[l + (size_t)(l - 1) * m] = {0.0, 0.0};
-                        break;
+        if (threadIdx.x < 32) {
+            const int hi = hi_s;
+            __syncwarp();          // every lane has read hi_s before lane 0 may update it
+            int l = 0;
+            if (hi > 0) {
+                for (int base = hi; base > 0 && l == 0; base -= 32) {
+                    const int cand = base - (int)threadIdx.x;
+                    bool neg = false;
+                    if (cand > 0) {
+                        double s = cabs_(H[(cand - 1) + (size_t)(cand - 1) * m]) + cabs_(H[cand + (size_t)cand * m]);
+                        if (s == 0.0) s = 1.0;
+                        neg = cabs_(H[cand + (size_t)(cand - 1) * m]) <= kEps * s;
                     }
-                    --l;
+                    const unsigned bal = __ballot_sync(0xffffffffu, neg);
+                    if (bal) l = base - (__ffs(bal) - 1);
                 }
-                l_s = l;
-                if (l == hi) { hi_s = hi - 1; act_s = 1; }
-                else act_s = 2;
+            }
+            if (threadIdx.x == 0) {
+                if (l > 0) H[l + (size_t)(l - 1) * m] = {0.0, 0.0};
+                act_s = 0;
+                if (hi <= 0) act_s = -1;
+                else {
+                    l_s = l;
+                    if (l == hi) { hi_s = hi - 1; act_s = 1; }
+                    else act_s = 2;
+                }
             }
         }
         __syncthreads();
@@ -597,9 +672,8 @@ __device__ void complex_schur_vector(const cplx *T, int m, int j, cplx *y, doubl
     }
 }
 
-// order: by |theta|, then Re, then Im >= 0 first (one thread, insertion sort)
-__device__ bool ritz_less(double ar, double ai, double br, double bi) {
-    double ma = hypot(ar, ai), mb = hypot(br, bi);
+// order: by |theta|, then Re, then Im >= 0 first (one thread, insertion sort; moduli given)
+__device__ bool ritz_less_m(double ma, double ar, double ai, double mb, double br, double bi) {
     if (ma != mb) return ma < mb;
     if (ar != br) return ar < br;
     int ka = ai >= 0 ? 0 : 1, kb = bi >= 0 ? 0 : 1;
@@ -725,14 +799,18 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
     // Z: m x m Schur vectors.  Both live in shared memory when the launch provided it
     // (the QR sweeps are a long chain of dependent small steps, so their latency rules).
     extern __shared__ __align__(16) unsigned char gdr_smem[];
-    T *W = a.smem ? reinterpret_cast<T *>(gdr_smem) : a.work;
-    T *Z = W + (size_t)rows * m;
-    T *B = a.work + (size_t)rows * m + (size_t)m * m;   // m x m scratch (LU), global
-    T *vtmp = B + (size_t)m * m;          // 2 (m+1) vectors
+    T *sm = reinterpret_cast<T *>(gdr_smem);
+    T *W = a.smem >= 1 ? sm : a.work;
+    T *Z = a.smem >= 2 ? sm + (size_t)rows * m : a.work + (size_t)rows * m;
+    T *B = a.smem >= 3 ? sm + (size_t)rows * m + (size_t)m * m : a.work + (size_t)rows * m + (size_t)m * m;  // m x m (LU)
+    T *vtmp = a.work + (size_t)rows * m + 2 * (size_t)m * m;   // 2 (m+1) vectors
     T *f = vtmp + 2 * (m + 1);
+    cplx *Ysm = a.smem >= 4 ? reinterpret_cast<cplx *>(sm + (size_t)rows * m + 2 * (size_t)m * m) : a.ywork;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     T *res = a.res;
     __shared__ int piv_s[kMaxM + 1];
 
+    long long t_mark = clock64();
     // ---- 1. least squares: d = argmin ||c - Hbar d||, res = c - Hbar d
     for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
         int i = e % rows, j = e / rows;
@@ -753,6 +831,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
         a.info->rnorm = sqrt(s);
     }
 
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[0] = _t - t_mark; t_mark = _t; }
     // ---- 2. f = H_m^{-H} e_m and the harmonic matrix M = H_m + |h|^2 f e_m^T (in W, ld m)
     solve_adjoint_last<T>(a.H, ldh, m, B, f, piv_s);
     const T hm = a.H[m + (size_t)(m - 1) * ldh];
@@ -768,8 +848,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
     // z = [-|h|^2 f; h] (restart direction), kept in a.z
     for (int i = threadIdx.x; i < rows; i += blockDim.x) a.z[i] = (i < m) ? Cx<T>::sc(-hm2, f[i]) : hm;
 
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[1] = _t - t_mark; t_mark = _t; }
     // ---- 3. eigen-decomposition of M: Hessenberg, Schur, eigenvalues
     hessenberg<T>(W, m, Z, vtmp);
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[2] = _t - t_mark; t_mark = _t; }
     int st;
     double *wr = a.wr, *wi = a.wi;
     if constexpr (sizeof(T) == sizeof(double)) {
@@ -784,26 +868,39 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
         }
         __syncthreads();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[3] = _t - t_mark; t_mark = _t; }
     double tnorm = 0.0;
     {
-        __shared__ double tn_s;
+        __shared__ double tn_s[32];
+        double s2 = 0.0;
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) s2 = fmax(s2, Cx<T>::ab2(W[e]));
+        for (int o = 16; o > 0; o >>= 1) s2 = fmax(s2, __shfl_down_sync(0xffffffffu, s2, o));
+        if (lane == 0) tn_s[warp] = s2;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int e = 0; e < m * m; ++e) s = fmax(s, sqrt(Cx<T>::ab2(W[e])));
-            tn_s = s;
+            double mx = 0.0;
+            for (int w = 0; w < nwarps; ++w) mx = fmax(mx, tn_s[w]);
+            tn_s[0] = sqrt(mx);
         }
         __syncthreads();
-        tnorm = tn_s;
+        tnorm = tn_s[0];
     }
 
     // ---- 4. order and select
     __shared__ int kk_s;
     int *ord = a.order;
+    __shared__ double mod_s[kMaxM];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) mod_s[i] = hypot(wr[i], wi[i]);
+    __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < m; ++i) ord[i] = i;
         for (int i = 1; i < m; ++i) {
             int v = ord[i], j = i - 1;
-            while (j >= 0 && ritz_less(wr[v], wi[v], wr[ord[j]], wi[ord[j]])) { ord[j + 1] = ord[j]; --j; }
+            while (j >= 0 && ritz_less_m(mod_s[v], wr[v], wi[v], mod_s[ord[j]], wr[ord[j]], wi[ord[j]])) {
+                ord[j + 1] = ord[j];
+                --j;
+            }
             ord[j + 1] = v;
         }
         int kk = a.k;
@@ -821,10 +918,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
     __syncthreads();
     const int kk = kk_s;
 
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[4] = _t - t_mark; t_mark = _t; }
     // ---- 5. eigenvectors of the kept pairs: g = Z y (complex), unit norm; residuals
     // a.gwork holds the kept eigenvectors as complex columns (m x kk)
     cplx *G = a.gwork;
-    cplx *Y = a.ywork;
+    cplx *Y = Ysm;
     for (int q = threadIdx.x; q < kk; q += blockDim.x) {
         const int j = ord[q];
         cplx *y = Y + (size_t)q * m;
@@ -848,28 +947,31 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
         G[i + (size_t)q * m] = s;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < kk; q += blockDim.x) {
+    for (int q = warp; q < kk; q += nwarps) {
         cplx *g = G + (size_t)q * m;
         double nr = 0.0;
-        for (int i = 0; i < m; ++i) nr += abs2(g[i]);
-        nr = sqrt(nr);
-        for (int i = 0; i < m; ++i) g[i] = g[i] * (1.0 / nr);
+        for (int i = lane; i < m; i += 32) nr += abs2(g[i]);
+        nr = sqrt(warp_sum(nr));
+        nr = __shfl_sync(0xffffffffu, nr, 0);
+        for (int i = lane; i < m; i += 32) g[i] = g[i] * (1.0 / nr);
+        __syncwarp();
         // residual ||Hbar g - theta [g; 0]||
         const cplx th = mkc(a.theta[2 * q], a.theta[2 * q + 1]);
         double r2 = 0.0;
-        for (int i = 0; i < rows; ++i) {
-            cplx s = {0.0, 0.0};
+        for (int i = lane; i < rows; i += 32) {
+            cplx sacc = {0.0, 0.0};
             for (int j = 0; j < m; ++j) {
                 T hij = a.H[i + (size_t)j * ldh];
                 cplx hc;
                 if constexpr (sizeof(T) == sizeof(double)) hc = mkc(*reinterpret_cast<const double *>(&hij), 0.0);
                 else hc = *reinterpret_cast<const cplx *>(&hij);
-                s = s + hc * g[j];
+                sacc = sacc + hc * g[j];
             }
-            if (i < m) s = s - th * g[i];
-            r2 += abs2(s);
+            if (i < m) sacc = sacc - th * g[i];
+            r2 += abs2(sacc);
         }
-        a.eres[q] = sqrt(r2);
+        r2 = warp_sum(r2);
+        if (lane == 0) a.eres[q] = sqrt(r2);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -880,73 +982,99 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
         a.info->kk = kk;
     }
 
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[5] = _t - t_mark; t_mark = _t; }
     // ---- 6. P_k: orthonormal basis of the kept span (real: Re/Im of pairs), m x kk
     //          then P_{k+1} = orth([[P_k; 0], z]), stored (m+1) x (kk+1) with ld m+1.
     T *P = a.P;
     __shared__ int ncol_s;
+    __shared__ int colof_s[kMaxM + 1];
     if (threadIdx.x == 0) {
         int col = 0;
         for (int q = 0; q < kk; ++q) {
-            const cplx *g = G + (size_t)q * m;
             const double im = a.theta[2 * q + 1];
-            if constexpr (sizeof(T) == sizeof(double)) {
-                double *Pd = reinterpret_cast<double *>(P);
-                if (im == 0.0) {
-                    // a real eigenvector computed in complex arithmetic has a common phase;
-                    // rotate it onto the real axis via its largest entry
-                    int imax = 0;
-                    double best = -1.0;
-                    for (int i = 0; i < m; ++i) if (abs2(g[i]) > best) { best = abs2(g[i]); imax = i; }
-                    cplx ph = conj(g[imax]) * (1.0 / sqrt(best));
-                    for (int i = 0; i < m; ++i) Pd[i + (size_t)col * rows] = (g[i] * ph).re;
-                    Pd[m + (size_t)col * rows] = 0.0;
-                    ++col;
-                } else if (im > 0.0) {
-                    for (int i = 0; i < m; ++i) {
-                        Pd[i + (size_t)col * rows] = g[i].re;
-                        Pd[i + (size_t)(col + 1) * rows] = g[i].im;
-                    }
-                    Pd[m + (size_t)col * rows] = 0.0;
-                    Pd[m + (size_t)(col + 1) * rows] = 0.0;
-                    col += 2;
-                }
+            if (sizeof(T) == sizeof(double)) {
+                if (im == 0.0) { colof_s[q] = col; col += 1; }
+                else if (im > 0.0) { colof_s[q] = col; col += 2; }
+                else colof_s[q] = -1;      // the partner (Im > 0) supplies both columns
             } else {
-                cplx *Pc = reinterpret_cast<cplx *>(P);
-                for (int i = 0; i < m; ++i) Pc[i + (size_t)col * rows] = g[i];
-                Pc[m + (size_t)col * rows] = {0.0, 0.0};
-                ++col;
+                colof_s[q] = col++;
             }
         }
         ncol_s = col;
+    }
+    __syncthreads();
+    for (int q = warp; q < kk; q += nwarps) {
+        const int c0 = colof_s[q];
+        if (c0 < 0) continue;
+        const cplx *g = G + (size_t)q * m;
+        const double im = a.theta[2 * q + 1];
+        if constexpr (sizeof(T) == sizeof(double)) {
+            double *Pd = reinterpret_cast<double *>(P);
+            if (im == 0.0) {
+                // a real eigenvector computed in complex arithmetic carries a common phase:
+                // rotate it onto the real axis through its largest entry (ties: smallest index)
+                double best = -1.0;
+                int imax = 0;
+                for (int i = lane; i < m; i += 32)
+                    if (abs2(g[i]) > best) { best = abs2(g[i]); imax = i; }
+                for (int o = 16; o > 0; o >>= 1) {
+                    double ob = __shfl_down_sync(0xffffffffu, best, o);
+                    int oi = __shfl_down_sync(0xffffffffu, imax, o);
+                    if (ob > best || (ob == best && oi < imax)) { best = ob; imax = oi; }
+                }
+                imax = __shfl_sync(0xffffffffu, imax, 0);
+                best = __shfl_sync(0xffffffffu, best, 0);
+                const cplx ph = conj(g[imax]) * (1.0 / sqrt(best));
+                for (int i = lane; i < m; i += 32) Pd[i + (size_t)c0 * rows] = (g[i] * ph).re;
+                if (lane == 0) Pd[m + (size_t)c0 * rows] = 0.0;
+            } else {
+                for (int i = lane; i < m; i += 32) {
+                    Pd[i + (size_t)c0 * rows] = g[i].re;
+                    Pd[i + (size_t)(c0 + 1) * rows] = g[i].im;
+                }
+                if (lane == 0) {
+                    Pd[m + (size_t)c0 * rows] = 0.0;
+                    Pd[m + (size_t)(c0 + 1) * rows] = 0.0;
+                }
+            }
+        } else {
+            cplx *Pc = reinterpret_cast<cplx *>(P);
+            for (int i = lane; i < m; i += 32) Pc[i + (size_t)c0 * rows] = g[i];
+            if (lane == 0) Pc[m + (size_t)c0 * rows] = {0.0, 0.0};
+        }
     }
     __syncthreads();
     const int nc = ncol_s;     // == kk
     // append z as column kk
     for (int i = threadIdx.x; i < rows; i += blockDim.x) P[i + (size_t)nc * rows] = a.z[i];
     __syncthreads();
-    // modified Gram-Schmidt, two passes, over the nc + 1 columns (length m+1)
+    // classical Gram-Schmidt applied twice over the nc + 1 columns (length m+1): per column,
+    // the projections on the previous columns in parallel, then the update in parallel
+    __shared__ T proj_s[kMaxM + 2];
     __shared__ double nrm_s;
-    __shared__ T proj_s;
     for (int c = 0; c <= nc; ++c) {
         T *pc = P + (size_t)c * rows;
         for (int pass = 0; pass < 2; ++pass) {
-            for (int q = 0; q < c; ++q) {
+            for (int q = threadIdx.x; q < c; q += blockDim.x) {
                 const T *pq = P + (size_t)q * rows;
-                if (threadIdx.x == 0) {
-                    T s = Cx<T>::zero();
-                    for (int i = 0; i < rows; ++i) s = add(s, Cx<T>::mul(Cx<T>::cj(pq[i]), pc[i]));
-                    proj_s = s;
-                }
-                __syncthreads();
-                const T s = proj_s;
-                for (int i = threadIdx.x; i < rows; i += blockDim.x) pc[i] = subt(pc[i], Cx<T>::mul(s, pq[i]));
-                __syncthreads();
+                T sacc = Cx<T>::zero();
+                for (int i = 0; i < rows; ++i) sacc = add(sacc, Cx<T>::mul(Cx<T>::cj(pq[i]), pc[i]));
+                proj_s[q] = sacc;
             }
+            __syncthreads();
+            for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+                T acc = pc[i];
+                for (int q = 0; q < c; ++q) acc = subt(acc, Cx<T>::mul(proj_s[q], P[i + (size_t)q * rows]));
+                pc[i] = acc;
+            }
+            __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < rows; ++i) s += Cx<T>::ab2(pc[i]);
-            nrm_s = sqrt(s);
+        if (warp == 0) {
+            double sq2 = 0.0;
+            for (int i = lane; i < rows; i += 32) sq2 += Cx<T>::ab2(pc[i]);
+            sq2 = warp_sum(sq2);
+            if (lane == 0) nrm_s = sqrt(sq2);
         }
         __syncthreads();
         const double inv = nrm_s > 0 ? 1.0 / nrm_s : 0.0;
@@ -954,6 +1082,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
         __syncthreads();
     }
 
+    __syncthreads();
+    if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[6] = _t - t_mark; t_mark = _t; }
     // ---- 7. Hnew = P_{k+1}^H Hbar P_k  ((kk+1) x kk, ld m+1 into a.Hnew), cnew = P_{k+1}^H res
     // T1 = Hbar P_k ((m+1) x kk) into W
     for (int e = threadIdx.x; e < rows * nc; e += blockDim.x) {
@@ -975,6 +1105,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a)
         a.cnew[i] = s;
     }
     __syncthreads();
+    if (threadIdx.x == 0) a.info->phase[7] = clock64() - t_mark;
 }
 
 // ----------------------------------------------------------------------------- GMRES(m) Givens step
@@ -1039,9 +1170,16 @@ void launch_small_gemv(const D *M, int k, const D *c, D *out, cudaStream_t s) {
 template <class T>
 void launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
     GdrArgs<T> a = a_in;
-    const size_t need = ((size_t)(a.m + 1) * a.m + (size_t)a.m * a.m) * sizeof(T);
-    a.smem = need <= kGdrSmemMax ? 1 : 0;
-    const size_t smem = a.smem ? need : 0;
+    // W, Z, B (T) and the eigenvector work Y (complex, m x m) go to shared memory in that
+    // order while they fit
+    const size_t m = a.m;
+    const size_t parts[4] = {(m + 1) * m * sizeof(T), m * m * sizeof(T), m * m * sizeof(T), m * m * sizeof(cplx)};
+    size_t smem = 0;
+    a.smem = 0;
+    for (int q = 0; q < 4 && smem + parts[q] <= kGdrSmemMax; ++q) {
+        smem += parts[q];
+        a.smem = q + 1;
+    }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute((const void *)k_gmresdr_restart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gmresdr_restart<T><<<1, kGdrThreads, smem, s>>>(a);

@@ -15,6 +15,8 @@ struct GdrInfo {
     int nconv;      // kept pairs (first nev) with residual <= rtolev |theta|
     int kk;         // kept pairs (k or k+1)
     int status;     // 0, or 1 if the QR iteration did not converge
+    int pad;
+    long long phase[8];   // SM cycles spent in each phase (instrumentation)
 };
 
 // Arguments of the GMRES-DR restart kernel (all pointers device memory).
