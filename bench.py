@@ -221,6 +221,7 @@ def run_tg(args, wl, rank, world):
         ir_ok = all(s == tg.TG_OK and st["relres"] <= wl["rtol"] for s, st, _ in infos_ir)
 
     status, st, cst = infos[-1]
+    phases = prof.pop("gmresdr_restart_phase_cycles", None)
     peaks, peak_src = measured_peaks()
     # roofline of the dominant kernel class (largest share of device time in the timed region)
     dom_name, dom = max(((k, v) for k, v in prof.items() if k != "bicg_noop"), key=lambda kv: kv[1]["ms"])
@@ -264,6 +265,8 @@ def run_tg(args, wl, rank, world):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "kernels": kernels,
+        "gmresdr_restart_phase_us": None if not phases else
+            [round(p / max(1, cst["cycles"] * args.steps) / 2070.0, 1) for p in phases],
         "clocks": clocks.summary(),
     }
     return line, {"coarse_cycles": cst["cycles"], "fine_mvps": st["mvps"], "fine_cycles": st["cycles"],

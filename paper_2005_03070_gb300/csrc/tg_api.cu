@@ -1002,9 +1002,8 @@ template <class T>
 static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int n, int j, T *H, int ldh,
                         cudaStream_t s) {
     using D = typename ST<T>::D;
-    // w = A v_j; classical Gram-Schmidt with selective re-orthogonalisation (the second
-    // pass runs only when the first cancelled more than half of ||w||^2; decided on the
-    // device, so the host never waits)
+    // w = A v_j, then two classical Gram-Schmidt passes, each a tall-skinny V^H w and a
+    // fused update + norm
     T *w = V + (size_t)(j + 1) * ldv;
     TG_CHECK(launch_apply<T>(A, A32, V + (size_t)j * ldv, w, s));
     TG_CHECK(red_ready(op, 0));
@@ -1028,13 +1027,14 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
             k_sum_part<D><<<(ncol + 1 + 7) / 8, 256, 0, s>>>(part, gb, ncol + 1, h1, 0));
     TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
             k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h1, w, n, nullptr, part, tk, nrm, h1 + ncol, flag, 0.5));
-    // pass 2 (only when flagged)
-    // (the device decides; these launches return at once when not needed, so they are
-    // timed in their own class without algorithmic bytes)
-    TG_PROF(P_REORTH, 0.0, 0.0, k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, part, flag));
-    TG_PROF(P_REORTH, 0.0, 0.0, k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gb, ncol, h2, 0, flag));
-    TG_PROF(P_REORTH, 0.0, 0.0,
-            k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h2, w, n, flag, part, tk, nrm, nullptr, nullptr, 0.0));
+    // pass 2 (classical Gram-Schmidt twice: on this operator the selective criterion of
+    // Daniel, Gragg, Kaufman and Stewart asked for the second pass on nearly every step)
+    TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
+            k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, part));
+    TG_PROF(P_SUM_PART, (double)gb * ncol * sizeof(D), (double)gb * ncol,
+            k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gb, ncol, h2, 0));
+    TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
+            k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h2, w, n, nullptr, part, tk, nrm, nullptr, nullptr, 0.0));
     TG_PROF(P_SMALL, 0, j, k_arnoldi_finish2<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, inv));
     TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, inv));
     TG_LAUNCH_CHECK();
