@@ -204,6 +204,22 @@ int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *
 int tg_harmonic_ritz(const void *Hbar, int m, int k, int complex_, void *theta_out,
                      void *basis_out, void *eres_out, int *kk_out, void *stream);
 
+/* The same step as tg_harmonic_ritz (same arguments, same results), for callers that
+ * cannot allocate device memory: callers that own all device memory through their own
+ * allocator or a fixed pre-reserved pool (a cudaMalloc inside the library would bypass
+ * the pool, or fail once it holds the memory), and latency-critical loops that cannot take
+ * the device-wide synchronisation cudaMalloc / cudaFree may cause.  The paper has no
+ * counterpart; this is a deployment variant.
+ * No device memory is allocated or freed: all scratch lives in one fixed 2 MiB device
+ * array of the library, reserved on every GPU that loads it and held until the process
+ * exits.  Limit: m <= 128 (TG_BAD_ARG with a message beyond it).  The first call on a
+ * device (with that device current) looks up the array's device address; make that first
+ * call before any stream capture.  Every call uses the same array: two calls whose work
+ * overlaps on the GPU (different streams, or several host threads) race and corrupt each
+ * other's results; serialise them.  Synchronises `stream`.                             */
+int tg_harmonic_ritz_noalloc(const void *Hbar, int m, int k, int complex_, void *theta_out,
+                             void *basis_out, void *eres_out, int *kk_out, void *stream);
+
 /* ------------------------------------------------------------------ instrumentation
  * Not part of the method: measurement hooks for benchmarks.
  * tg_profile_enable(1) starts recording a CUDA event pair around every kernel the

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtg.so")
 
-SOURCES = ["tg_api.cu", "tg_setup.cu", "tg_small.cu"]
+SOURCES = ["tg_api.cu", "tg_setup.cu", "tg_small.cu", "tg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
          "-diag-suppress", "177"]

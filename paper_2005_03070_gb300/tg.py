@@ -34,7 +34,7 @@ EXPORTS = [
     "tg_status_string", "tg_last_error", "tg_setup_operator", "tg_destroy_op", "tg_op_size", "tg_apply",
     "tg_prolong", "tg_restrict", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
     "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_adjoint_solve", "tg_kappa_gradient",
-    "tg_harmonic_ritz", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
+    "tg_harmonic_ritz", "tg_harmonic_ritz_noalloc", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
 ]
 
 
@@ -88,6 +88,7 @@ def load() -> C.CDLL:
         "tg_adjoint_solve": (i32, [vp, vp, vp, vp, vp, vp, dbl, i32, i32, i32, C.POINTER(TgStats), vp]),
         "tg_kappa_gradient": (i32, [vp, vp, vp, vp, vp]),
         "tg_harmonic_ritz": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
+        "tg_harmonic_ritz_noalloc": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
         "tg_profile_enable": (i32, [i32]),
         "tg_profile_read": (i32, [C.c_char_p, i32]),
         "tg_launch_count": (i64, []),
