@@ -47,9 +47,11 @@ WORKLOADS = {
 }
 L2_BYTES = 129 * 1024 * 1024
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz
-# DRAM bytes per launch of the dominant kernel from an ncu capture (see profiles/), per
-# workload and kernel class; None when the kernel changed after the capture.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch over algorithmic bytes per launch, per kernel class,
+# from an ncu capture of a smaller case of the same kernel (profiles/gemv_t_cd3d191.md);
+# the traffic of a full-size launch is this ratio times its algorithmic bytes (the traffic
+# grows in proportion to rows x columns).  Remove an entry when its kernel changes.
+NCU_TRAFFIC_RATIO = {"gemv_t": 1.024}
 
 
 def measured_peaks():
@@ -229,7 +231,8 @@ def run_tg(args, wl, rank, world):
     per_launch_ms = dom["ms"] / dom["launches"]
     gbs = dom["bytes"] / (dom["ms"] * 1e-3) / 1e9
     tflops = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC.get(args.workload, {}).get(dom_name)
+    ratio = NCU_TRAFFIC_RATIO.get(dom_name)
+    traffic = None if ratio is None else ratio * dom["bytes"] / dom["launches"]
     roofline = {"kernel": dom_name, "bound": "alu", "achieved": round(tflops, 4),
                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz",
