@@ -323,27 +323,33 @@ def cpu_sample(wl, counts):
         a_ = t1 / k1 - c * k1
         t_proj = max(a_ * k + c * k * k, t2 * k / k2)
         proj_note = f"MinRes projections with {k1} and {k2} vectors (extrapolated to {k} as a k + c k^2)"
-    # coarse Arnoldi step at the mean basis size of a restarted cycle, and one small eig
-    jm = (m + k) // 2
-    V = np.zeros((nc, jm + 2))
-    H = np.zeros((jm + 2, jm + 1))
-    V[:, :jm] = np.linalg.qr(gi.random_dense((nc, jm), 3))[0]
-    t_step = _timeit(lambda: arnoldi_extend(opc.apply, V, H, jm - 1, jm))
-    del V
-    Hs = gi.random_hessenberg(m, 4) + 3 * np.vstack([np.eye(m), np.zeros((1, m))])
-    t_eig = _timeit(lambda: harmonic_ritz(Hs))
-    est = (counts["coarse_steps"] * t_step + counts["coarse_cycles"] * t_eig + k * t_mvp
+    # coarse GMRES-DR: one and two full cycles of the oracle on the restricted right-hand
+    # side (the second cycle's cost stands for every later cycle)
+    from oracle import gmresdr as ogd
+    from oracle import transfer as otr
+    bc = otr.restrict(b, wl["N"], 2 if wl["kind"] == "cd2d" else 3)
+    t3 = time.perf_counter()
+    ogd.gmresdr(opc.apply, bc, m, k, nev=wl["nev"], rtolev=wl["rtolev"], rtol=wl["rtol_c"], max_cycles=1)
+    t_c1 = time.perf_counter() - t3
+    t3 = time.perf_counter()
+    ogd.gmresdr(opc.apply, bc, m, k, nev=wl["nev"], rtolev=wl["rtolev"], rtol=wl["rtol_c"], max_cycles=2)
+    t_c2 = time.perf_counter() - t3
+    t_cycle = max(t_c2 - t_c1, 0.0)
+    est = (t_c1 + (counts["coarse_cycles"] - 1) * t_cycle + k * t_mvp
            + counts["fine_mvps"] / 2 * t_iter + counts["fine_cycles"] * (t_proj + t_mvp))
-    info = {"kind": "oracle", "cores": 1,
-            "sample": (f"oracle (numpy float64, 1 thread for the stencil and vector work) timed on one fine "
-                       f"BiCGStab iteration, one fine product, {proj_note}, one coarse "
-                       f"Arnoldi step at j={jm} and one {m}x{m} harmonic-Ritz eig, each after a warm-up call; "
-                       f"scaled to one solve with {counts['coarse_steps']} coarse steps, {counts['coarse_cycles']} "
-                       f"coarse cycles, {k} A Y products, {counts['fine_mvps']} fine products and "
-                       f"{counts['fine_cycles']} fine cycles"),
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([p.get("num_threads", 1) for p in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    info = {"kind": "oracle", "cores": cores,
+            "sample": (f"oracle (numpy float64: stencils single-threaded, BLAS calls on {cores} threads) timed on "
+                       f"one fine BiCGStab iteration, one fine product, {proj_note}, and coarse GMRES-DR runs of one "
+                       f"and of two cycles; scaled to one solve with {counts['coarse_cycles']} coarse cycles, "
+                       f"{k} A Y products, {counts['fine_mvps']} fine products and {counts['fine_cycles']} fine cycles"),
             "sample_seconds": round(time.perf_counter() - t0, 2), "est_seconds_per_solve": round(est, 3),
-            "pieces_s": {"fine_iter": t_iter, "fine_mvp": t_mvp, "projection": t_proj, "coarse_step": t_step,
-                         "eig": t_eig}}
+            "pieces_s": {"fine_iter": t_iter, "fine_mvp": t_mvp, "projection": t_proj, "coarse_cycle1": t_c1,
+                         "coarse_cycle": t_cycle}}
     return 1.0 / est, info
 
 

@@ -304,13 +304,46 @@ static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Ou
 }
 
 // h = V^H w (ncol entries, device D array)
+// Whether the pipelined float64 V^H w kernel applies: 16-byte aligned columns and room for
+// whole 64-row chunks below the leading dimension.
+template <class T>
+static bool pipe_ok(const T *V, size_t ldv, const T *w, int n, int ncol) {
+    if (sizeof(T) != 8) return false;
+    if (ldv % 2 || ldv < (size_t)((n + kPipeRows - 1) / kPipeRows) * kPipeRows) return false;
+    if (((uintptr_t)V | (uintptr_t)w) & 15) return false;
+    return ncol + 1 <= 136 && n >= kPipeRows;
+}
+
+// partials of V^H w into part (gb blocks); returns gb
+template <class T>
+static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int n, typename ST<T>::D *part,
+                              cudaStream_t s, bool *used_pipe) {
+    if (pipe_ok<T>(V, ldv, w, n, ncol)) {
+        const size_t smem = (size_t)kPipeStages * (ncol + 1) * kPipeRows * sizeof(double);
+        cudaFuncSetAttribute((const void *)k_gemv_t_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+        const int nchunks = (n + kPipeRows - 1) / kPipeRows;
+        const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
+        k_gemv_t_pipe<<<gb, kThreads, smem, s>>>(reinterpret_cast<const double *>(V), ldv, ncol,
+                                                 reinterpret_cast<const double *>(w), n,
+                                                 reinterpret_cast<double *>(part));
+        *used_pipe = true;
+        return gb;
+    }
+    const int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
+    k_gemv_t_part<T><<<std::max(gb, 1), kThreads, 0, s>>>(V, ldv, ncol, w, n, part);
+    *used_pipe = false;
+    return std::max(gb, 1);
+}
+
 template <class T>
 static int gemv_t(tg_op *op, const T *V, size_t ldv, int ncol, const T *w, int n, typename ST<T>::D *h, cudaStream_t s) {
     using D = typename ST<T>::D;
-    int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
-    if (gb < 1) gb = 1;
-    TG_CHECK(red_ready(op, (size_t)gb * ncol * sizeof(D)));
-    TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1), k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, wsp<D>(op, S_PART)));
+    TG_CHECK(red_ready(op, (size_t)num_sms() * 8 * (ncol + 1) * sizeof(D)));
+    bool piped = false;
+    int gb = 1;
+    TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
+            gb = gemv_t_part_launch<T>(V, ldv, ncol, w, n, wsp<D>(op, S_PART), s, &piped));
     TG_LAUNCH_CHECK();
     TG_PROF(P_SUM_PART, (double)gb * ncol * sizeof(D), (double)gb * ncol, k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(wsp<D>(op, S_PART), gb, ncol, h, 0));
     TG_LAUNCH_CHECK();
@@ -1021,18 +1054,20 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     TG_CHECK(red_ready(op, (size_t)gb * (ncol + 1) * sizeof(D)));
     part = wsp<D>(op, S_PART);
     // pass 1: h1 = [V_j, w]^H w
+    bool piped = false;
+    int gbt = gb;
     TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * (ncol + 1) * n * (sizeof(T) == 16 ? 4 : 1),
-            k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol + 1, w, n, part));
-    TG_PROF(P_SUM_PART, (double)gb * (ncol + 1) * sizeof(D), (double)gb * (ncol + 1),
-            k_sum_part<D><<<(ncol + 1 + 7) / 8, 256, 0, s>>>(part, gb, ncol + 1, h1, 0));
+            gbt = gemv_t_part_launch<T>(V, ldv, ncol + 1, w, n, part, s, &piped));
+    TG_PROF(P_SUM_PART, (double)gbt * (ncol + 1) * sizeof(D), (double)gbt * (ncol + 1),
+            k_sum_part<D><<<(ncol + 1 + 7) / 8, 256, 0, s>>>(part, gbt, ncol + 1, h1, 0));
     TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
             k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h1, w, n, nullptr, part, tk, nrm, h1 + ncol, flag, 0.5));
     // pass 2 (classical Gram-Schmidt twice: on this operator the selective criterion of
     // Daniel, Gragg, Kaufman and Stewart asked for the second pass on nearly every step)
     TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
-            k_gemv_t_part<T><<<gb, kThreads, 0, s>>>(V, ldv, ncol, w, n, part));
-    TG_PROF(P_SUM_PART, (double)gb * ncol * sizeof(D), (double)gb * ncol,
-            k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gb, ncol, h2, 0));
+            gbt = gemv_t_part_launch<T>(V, ldv, ncol, w, n, part, s, &piped));
+    TG_PROF(P_SUM_PART, (double)gbt * ncol * sizeof(D), (double)gbt * ncol,
+            k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gbt, ncol, h2, 0));
     TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
             k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h2, w, n, nullptr, part, tk, nrm, nullptr, nullptr, 0.0));
     TG_PROF(P_SMALL, 0, j, k_arnoldi_finish2<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, inv));
@@ -1183,8 +1218,11 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     const int nc = op->nc;
     const int ldh = m + 1;
     const size_t es = sizeof(T);
-    TG_CHECK(wsx(op, S_GV, (size_t)nc * (m + 1) * es));
-    TG_CHECK(wsx(op, S_GV2, (size_t)nc * (m + 1) * es));
+    // basis leading dimension rounded up to 64 rows: every column starts 16-byte aligned
+    // and whole 64-row chunks stay inside the allocation (pipelined V^H w)
+    const size_t ldv = ((size_t)nc + 63) / 64 * 64;
+    TG_CHECK(wsx(op, S_GV, ldv * (m + 1) * es));
+    TG_CHECK(wsx(op, S_GV2, ldv * (m + 1) * es));
     TG_CHECK(wsx(op, S_GH, (size_t)ldh * m * es));
     TG_CHECK(wsx(op, S_GH2, (size_t)ldh * m * es));
     TG_CHECK(wsx(op, S_GC, (size_t)(m + 1) * es));
@@ -1233,7 +1271,7 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     bool converged = false;
     while (true) {
         ++cycles;
-        for (int j = j0; j < m; ++j) TG_CHECK(arnoldi_step<T>(op, A, A32, V, nc, nc, j, H, ldh, s));
+        for (int j = j0; j < m; ++j) TG_CHECK(arnoldi_step<T>(op, A, A32, V, ldv, nc, j, H, ldh, s));
         cmvps += m - j0;
         TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * es, s));
         GdrArgs<T> a;
@@ -1246,7 +1284,7 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
         TG_LAUNCH_CHECK();
         // x_c += V_m d
-        TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, m, a.d, 1.0, xc, nc));
+        TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, ldv, m, a.d, 1.0, xc, nc));
         TG_LAUNCH_CHECK();
         TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
         memcpy(&info, op->pin.p, sizeof(info));
@@ -1261,7 +1299,7 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         converged = info.rnorm <= rtol * nbc && info.nconv >= (nev < kk ? nev : kk);
         if (converged || cycles >= max_cycles) break;
         // restart: V_{k+1} = V_{m+1} P_{k+1}; Hbar = Hnew; c = cnew
-        TG_CHECK(tsm<T>(V, nc, m + 1, a.P, m + 1, kk + 1, V2, nc, nc, s));
+        TG_CHECK(tsm<T>(V, ldv, m + 1, a.P, m + 1, kk + 1, V2, ldv, nc, s));
         std::swap(V, V2);
         std::swap(H, H2);
         TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * es, s));
@@ -1269,11 +1307,11 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         // re-orthogonalise v_{k+1} against V_k and normalise
         {
             using DD = typename ST<T>::D;
-            T *w = V + (size_t)kk * nc;
+            T *w = V + (size_t)kk * ldv;
             DD *h1 = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384);
             DD *nrm = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
-            TG_CHECK(gemv_t<T>(op, V, nc, kk, w, nc, h1, s));
-            TG_PROF(P_GEMV_N, (kk + 2.0) * nc * sizeof(T), 2.0 * kk * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, kk, h1, -1.0, w, nc));
+            TG_CHECK(gemv_t<T>(op, V, ldv, kk, w, nc, h1, s));
+            TG_PROF(P_GEMV_N, (kk + 2.0) * nc * sizeof(T), 2.0 * kk * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, ldv, kk, h1, -1.0, w, nc));
             TG_PROF(P_DOT, 1.0 * nc * sizeof(T), 2.0 * nc, k_dot<T><<<grid_for(nc, 4), kThreads, 0, s>>>(w, nullptr, nc, wsp<DD>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm));
             TG_PROF(P_SMALL, 0, 1, launch_inv_sqrt(s, reinterpret_cast<const double *>(nrm), reinterpret_cast<double *>(nrm) + 4));
             TG_PROF(P_SCALE, 2.0 * nc * sizeof(T), nc, k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(w, nc, reinterpret_cast<double *>(nrm) + 4));
@@ -1294,7 +1332,7 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     if (defl_out) {
         DBuf Yc;
         TG_CHECK(Yc.ensure((size_t)nc * kk * es));
-        TG_CHECK(tsm<T>(V, nc, m, wsp<T>(op, S_GP), m + 1, kk, Yc.as<T>(), nc, nc, s));
+        TG_CHECK(tsm<T>(V, ldv, m, wsp<T>(op, S_GP), m + 1, kk, Yc.as<T>(), nc, nc, s));
         tg_defl *d;
         TG_CHECK(defl_create(op, transpose, kk, proj, precision, &d));
         int rc = prolong_impl(op, Yc.p, d->Y.p, kk, s);

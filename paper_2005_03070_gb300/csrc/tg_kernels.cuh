@@ -382,6 +382,82 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
     }
 }
 
+// h = V^H w partials for float64 V with 16-byte aligned columns (ldv even, V and w 16-byte
+// aligned, ldv >= the rows rounded up to 64): the rows are walked in 64-row chunks staged
+// in shared memory by a 3-deep cp.async pipeline, so that loads of the next chunks are in
+// flight while the FP64 pipe works on the current one.  Block b takes chunks b, b + G, ...
+// Warp w owns columns w, w + 8, ...; lane l rows l and l + 32 of a chunk.  Shared memory:
+// 3 x (ncol + 1) x 64 doubles (w is the extra column).
+constexpr int kPipeRows = 64;
+constexpr int kPipeStages = 3;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__global__ void __launch_bounds__(kThreads) k_gemv_t_pipe(const double *__restrict__ V, size_t ldv, int ncol,
+                                                           const double *__restrict__ w, int n, double *part) {
+    constexpr int kMaxPerWarp = 17;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *buf = reinterpret_cast<double *>(smem_raw);
+    const int cols = ncol + 1;                      // w staged as column ncol
+    const size_t stage_elems = (size_t)cols * kPipeRows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nchunks = (n + kPipeRows - 1) / kPipeRows;
+    const int G = gridDim.x;
+    const int mine = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / G + 1 : 0;
+    auto issue = [&](int it) {
+        if (it < mine) {
+            const size_t row0 = (size_t)(blockIdx.x + (size_t)it * G) * kPipeRows;
+            double *dst = buf + (size_t)(it % kPipeStages) * stage_elems;
+            // (cols x 64 rows) as 16-byte pieces: piece e -> column e / 32, rows 2 (e % 32) ..
+            for (int e = threadIdx.x; e < cols * (kPipeRows / 2); e += blockDim.x) {
+                const int c = e / (kPipeRows / 2), rp = e % (kPipeRows / 2);
+                const double *src = (c < ncol ? V + (size_t)c * ldv : w) + row0 + 2 * rp;
+                cp_async16(dst + (size_t)c * kPipeRows + 2 * rp, src);
+            }
+        }
+        cp_async_commit();
+    };
+    double acc[kMaxPerWarp];
+#pragma unroll
+    for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = 0.0;
+#pragma unroll
+    for (int s = 0; s < kPipeStages - 1; ++s) issue(s);
+    for (int it = 0; it < mine; ++it) {
+        cp_async_wait<kPipeStages - 2>();
+        __syncthreads();
+        issue(it + kPipeStages - 1);              // the buffer of iteration it - 1, read by everyone already
+        const double *st = buf + (size_t)(it % kPipeStages) * stage_elems;
+        const int row0 = (blockIdx.x + it * G) * kPipeRows;
+        const bool r0ok = row0 + lane < n, r1ok = row0 + lane + 32 < n;
+        const double w0 = r0ok ? st[(size_t)ncol * kPipeRows + lane] : 0.0;
+        const double w1 = r1ok ? st[(size_t)ncol * kPipeRows + lane + 32] : 0.0;
+#pragma unroll
+        for (int q = 0; q < kMaxPerWarp; ++q) {
+            const int c = warp + 8 * q;
+            if (c < ncol) {
+                const double *sc = st + (size_t)c * kPipeRows;
+                const double v0 = r0ok ? sc[lane] : 0.0;
+                const double v1 = r1ok ? sc[lane + 32] : 0.0;
+                acc[q] = fma(v1, w1, fma(v0, w0, acc[q]));
+            }
+        }
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int q = 0; q < kMaxPerWarp; ++q) {
+        const int c = warp + 8 * q;
+        if (c < ncol) {
+            const double s = warp_sum(acc[q]);
+            if (lane == 0) part[(size_t)blockIdx.x * ncol + c] = s;
+        }
+    }
+}
+
 // out[e] (mode 0: =, mode 1: +=) sum_b part[b * nent + e].  One warp per entry: lane l
 // adds blocks l, l + 32, ... in order, then the fixed shuffle tree (deterministic).
 template <class D>
