@@ -56,6 +56,7 @@ enum { TG_FINE = 0, TG_COARSE = 1 };                               /* grid level
 
 typedef struct tg_op tg_op;       /* fine + coarse operator, grid maps, workspaces       */
 typedef struct tg_defl tg_defl;   /* deflation basis Y, A Y factored, projection data     */
+typedef struct tg_batch tg_batch; /* many instances x 8 right-hand sides (added form)    */
 
 /* Per-solve statistics (host memory, filled by the solvers). */
 typedef struct tg_stats {
@@ -190,6 +191,31 @@ int tg_adjoint_solve(tg_op *op, const tg_defl *defl_left, const void *g, void *l
 /* dkappa from given x and lambda (the contraction step alone). */
 int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *dkappa,
                       void *stream);
+
+/* ------------------------------------------------------------------ batched form (added)
+ * Not in the paper: many independent 2D convection-diffusion instances (TG_CD2D, sizes Ns[i]
+ * odd, convection betas[i]), each with nrhs = 8 right-hand sides sharing one deflation
+ * basis (the paper reuses the basis across right-hand sides, Section 4.1, Example 2).
+ * Right-hand sides and solutions are float64, concatenated by instance, each instance's
+ * n_i x 8 block point-major: element (point j, column q) of instance i at
+ * offset_i + j * 8 + q (tg_batch_layout gives offset_i and n_i).
+ * tg_batch_setup: per instance, coarse GMRES-DR(m,k) on the restriction of its column 0,
+ *   prolongation, A Y and CholQR2 with float32 copies (1 <= k <= 32); stats: count entries.
+ * tg_batch_solve: per instance, float32-inner / float64-refinement BiCGStab(ncyc)-Proj(k)
+ *   on the 8 columns together (one read of the basis serves all 8), each column with its
+ *   own cycle tolerance and stopping test; the iteration batch is a CUDA graph replayed
+ *   until every column of the cycle has finished.  x holds the initial guesses.
+ *   Instances run concurrently on `threads` host threads, one stream each; both calls
+ *   wait for `stream` first and return when all work is done.  stats: count * 8 entries.
+ * Returns TG_OK when every column converged, else the first failing status.           */
+int tg_batch_create(tg_batch **out, int count, const int64_t *Ns, const double *betas, int nrhs,
+                    void *stream);
+int tg_batch_layout(const tg_batch *b, int i, int64_t *offset, int64_t *n);
+int tg_batch_setup(tg_batch *b, const void *rhs, int m, int k, int nev, double rtolev, double rtol,
+                   int max_cycles, int proj, int threads, tg_stats *stats, void *stream);
+int tg_batch_solve(tg_batch *b, const void *rhs, void *x, double rtol, int ncyc, int restart_mvps,
+                   int64_t max_mvps, int threads, tg_stats *stats, void *stream);
+int tg_destroy_batch(tg_batch *b);
 
 /* ------------------------------------------------------------------ small dense step
  * The single-CTA float64 kernel of GMRES-DR's restart (Section 2.1), exposed for tests:

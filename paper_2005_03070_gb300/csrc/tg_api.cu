@@ -3,7 +3,11 @@
 // tg_kernels.cuh, tg_small.cu and tg_setup.cu; the host only launches them, reads a few
 // scalars per cycle and takes the restart decisions of the algorithms.
 #include <algorithm>
+#include <atomic>
 #include <climits>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,6 +16,7 @@
 #include <vector>
 
 #include "tg_kernels.cuh"
+#include "tg_mrhs.cuh"
 #include "tg_setup.cuh"
 #include "tg_small.cuh"
 
@@ -93,9 +98,15 @@ struct Prof {
 };
 static Prof g_prof;
 
+static std::mutex g_prof_mu;
+
 static int prof_begin(cudaStream_t s) {
+    if (!g_prof.on) {
+        __atomic_add_fetch(&g_prof.launches, 1, __ATOMIC_RELAXED);
+        return -1;
+    }
+    std::lock_guard<std::mutex> lock(g_prof_mu);
     g_prof.launches += 1;
-    if (!g_prof.on) return -1;
     if (g_prof.next + 2 > g_prof.events.size()) {
         size_t add = g_prof.events.size() < 4096 ? 4096 : g_prof.events.size();
         for (size_t i = 0; i < add; ++i) {
@@ -111,6 +122,7 @@ static int prof_begin(cudaStream_t s) {
 }
 static void prof_end(int ev, int cls, double bytes, double flops, cudaStream_t s) {
     if (ev < 0) return;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
     cudaEventRecord(g_prof.events[ev + 1], s);
     g_prof.recs.push_back(ProfRec{cls, ev, bytes, flops});
 }
@@ -186,6 +198,7 @@ enum Slot {
     S_GV, S_GV2, S_GH, S_GH2, S_GC, S_GX, S_GD, S_GRES, S_GZ, S_GP, S_GCN, S_GTHETA, S_GWR, S_GWI,
     S_GORD, S_GERES, S_GWORK, S_GY, S_GG, S_GINFO, S_GTMP, S_GB, S_GH1, S_GHV,
     S_FV, S_FH, S_FCS, S_FSN, S_FG, S_FY, S_FSTATE, S_BC,
+    S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC,
     S_COUNT
 };
 
@@ -232,11 +245,13 @@ template <class U> static U *wsp(tg_op *op, Slot s) { return op->ws[s].as<U>(); 
 static int wsx(tg_op *op, Slot s, size_t bytes) { return op->ws[s].ensure(bytes); }
 
 // reduction scratch: partials (sized generously), a ticket, a small result area
-static int red_ready(tg_op *op, size_t part_bytes) {
+// The ticket is zeroed on the stream that will use it (a plain cudaMemset runs on the
+// legacy stream, which streams created non-blocking do not wait for).
+static int red_ready(tg_op *op, size_t part_bytes, cudaStream_t s) {
     TG_CHECK(wsx(op, S_PART, part_bytes < (4 << 20) ? (4 << 20) : part_bytes));
     if (!op->ws[S_TICKET].p) {
         TG_CHECK(wsx(op, S_TICKET, 64));
-        TG_CHECK_CUDA(cudaMemset(op->ws[S_TICKET].p, 0, 64));
+        TG_CHECK_CUDA(cudaMemsetAsync(op->ws[S_TICKET].p, 0, 64, s));
     }
     TG_CHECK(wsx(op, S_SMALL, 1 << 16));
     TG_CHECK(op->pin.ensure(1 << 16));
@@ -256,7 +271,7 @@ static double dnorm2(cplx v) { return v.re; }
 template <class T>
 static int dot_host(tg_op *op, const T *a, const T *b, int n, double *aa, typename ST<T>::D *ab, cudaStream_t s) {
     using D = typename ST<T>::D;
-    TG_CHECK(red_ready(op, 0));
+    TG_CHECK(red_ready(op, 0, s));
     int g = grid_for(n, 4);
     D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 1024);
     TG_PROF(P_DOT, (b ? 2.0 : 1.0) * n * sizeof(T), (b ? 4.0 : 2.0) * n, k_dot<T><<<g, kThreads, 0, s>>>(a, b, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out));
@@ -287,9 +302,25 @@ static int launch_apply(const DevOp &A, const DevOp32 &A32, const T *x, T *y, cu
 }
 
 // ----------------------------------------------------------------------------- tall-skinny helpers
+// Allows a kernel the device's full dynamic shared memory.  Always the same value, so
+// concurrent host threads setting it cannot lower it under each other's launches.
+static int max_dyn_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) v = 48 * 1024;
+    return v;
+}
+
 template <class T>
 static int set_smem(const void *fn, size_t bytes) {
-    if (bytes > 48 * 1024) TG_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (bytes > 48 * 1024) {
+        const int mx = max_dyn_smem();
+        if ((int)bytes > mx) {
+            set_error("a launch needs %zu bytes of shared memory, more than the %d available", bytes, mx);
+            return TG_BAD_ARG;
+        }
+        TG_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    }
     return TG_OK;
 }
 
@@ -320,7 +351,7 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
                               cudaStream_t s, bool *used_pipe) {
     if (pipe_ok<T>(V, ldv, w, n, ncol)) {
         const size_t smem = (size_t)kPipeStages * (ncol + 1) * kPipeRows * sizeof(double);
-        cudaFuncSetAttribute((const void *)k_gemv_t_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute((const void *)k_gemv_t_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem());
         const int per_sm = smem <= 100 * 1024 ? 2 : 1;
         const int nchunks = (n + kPipeRows - 1) / kPipeRows;
         const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
@@ -339,7 +370,7 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
 template <class T>
 static int gemv_t(tg_op *op, const T *V, size_t ldv, int ncol, const T *w, int n, typename ST<T>::D *h, cudaStream_t s) {
     using D = typename ST<T>::D;
-    TG_CHECK(red_ready(op, (size_t)num_sms() * 8 * (ncol + 1) * sizeof(D)));
+    TG_CHECK(red_ready(op, (size_t)num_sms() * 8 * (ncol + 1) * sizeof(D), s));
     bool piped = false;
     int gb = 1;
     TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
@@ -356,7 +387,7 @@ static int gram_ept(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, 
                     cudaStream_t s) {
     using D = typename ST<T>::D;
     int gb = tiles_grid(n, 1);
-    TG_CHECK(red_ready(op, (size_t)gb * k * k * sizeof(D)));
+    TG_CHECK(red_ready(op, (size_t)gb * k * k * sizeof(D), s));
     size_t smem = (size_t)2 * 32 * k * sizeof(T);
     TG_CHECK(set_smem<T>((const void *)k_gram_part<T, EPT>, smem));
     TG_PROF(P_GRAM, (A == B ? 1.0 : 2.0) * k * n * sizeof(T), (sym ? 1.0 * k * (k + 1) : 2.0 * k * k) * n * (sizeof(T) == 16 ? 4 : 1), k_gram_part<T, EPT><<<gb, kThreads, smem, s>>>(A, B, ld, k, n, sym, wsp<D>(op, S_PART)));
@@ -376,13 +407,15 @@ static int gram(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int 
 // CholQR2: A (n x k) = Q R.  Writes Q (n x k), R and Rinv (k x k, device D).
 template <class T>
 static int cholqr2(tg_op *op, const T *A, int k, int n, T *Q, T *R, T *Rinv, int *info_dev, cudaStream_t s) {
-    DBuf G, R1, R1i, R2, R2i;
+    // k x k scratch from the operator's workspace (no allocation after the first call)
     size_t kb = (size_t)k * k * sizeof(T);
-    TG_CHECK(G.ensure(kb));
-    TG_CHECK(R1.ensure(kb));
-    TG_CHECK(R1i.ensure(kb));
-    TG_CHECK(R2.ensure(kb));
-    TG_CHECK(R2i.ensure(kb));
+    TG_CHECK(wsx(op, S_CQ_G, kb));
+    TG_CHECK(wsx(op, S_CQ_R1, kb));
+    TG_CHECK(wsx(op, S_CQ_R1I, kb));
+    TG_CHECK(wsx(op, S_CQ_R2, kb));
+    TG_CHECK(wsx(op, S_CQ_R2I, kb));
+    DBuf &G = op->ws[S_CQ_G], &R1 = op->ws[S_CQ_R1], &R1i = op->ws[S_CQ_R1I], &R2 = op->ws[S_CQ_R2],
+         &R2i = op->ws[S_CQ_R2I];
     TG_CHECK(gram<T>(op, A, A, n, k, n, 1, G.as<T>(), s));
     TG_PROF(P_SMALL, 0, 1.0 * k * k * k, launch_chol_inv<T>(G.as<T>(), k, R1.as<T>(), R1i.as<T>(), info_dev, s));
     TG_LAUNCH_CHECK();
@@ -393,7 +426,6 @@ static int cholqr2(tg_op *op, const T *A, int k, int n, T *Q, T *R, T *Rinv, int
     TG_CHECK(tsm<T>(Q, n, k, R2i.as<T>(), k, k, Q, n, n, s));   // in place: each tile is staged first
     TG_CHECK(tsm<T>(R2.as<T>(), k, k, R1.as<T>(), k, k, R, k, k, s));     // R = R2 R1
     TG_CHECK(tsm<T>(R1i.as<T>(), k, k, R2i.as<T>(), k, k, Rinv, k, k, s));  // R^-1 = R1^-1 R2^-1
-    TG_CHECK_CUDA(cudaStreamSynchronize(s));   // the local buffers are freed on return
     return TG_OK;
 }
 
@@ -633,10 +665,10 @@ static int build_defl(tg_op *op, int transpose, tg_defl *d, cudaStream_t s) {
         TG_CHECK(cholqr2<T>(op, AY, kk, n, d->Q.as<T>(), d->R.as<T>(), d->M.as<T>(), info, s));
     } else {
         // V = orth(Y) (in Q), A V = A Y Ry^{-1} (in AV), H = V^H A V (in R), M = H^{-1}
-        DBuf Ry, Ryi, W;
-        TG_CHECK(Ry.ensure(kb));
-        TG_CHECK(Ryi.ensure(kb));
-        TG_CHECK(W.ensure(2 * kb));
+        TG_CHECK(wsx(op, S_GAL_RY, kb));
+        TG_CHECK(wsx(op, S_GAL_RYI, kb));
+        TG_CHECK(wsx(op, S_GAL_W, 2 * kb));
+        DBuf &Ry = op->ws[S_GAL_RY], &Ryi = op->ws[S_GAL_RYI], &W = op->ws[S_GAL_W];
         TG_CHECK(d->AV.ensure(nb));
         TG_CHECK(cholqr2<T>(op, Y, kk, n, d->Q.as<T>(), Ry.as<T>(), Ryi.as<T>(), info, s));
         TG_CHECK(tsm<T>(AY, n, kk, Ryi.as<T>(), kk, kk, d->AV.as<T>(), n, n, s));
@@ -673,7 +705,7 @@ static int project_impl(tg_op *op, const tg_defl *df, const T *W, const T *B1, c
                         cudaStream_t s) {
     using D = typename ST<T>::D;
     const int kk = df->kk;
-    TG_CHECK(red_ready(op, 0));
+    TG_CHECK(red_ready(op, 0, s));
     D *cvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192);
     D *dvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192 + 4096);
     TG_CHECK(gemv_t<T>(op, W, n, kk, r, n, cvec, s));
@@ -805,7 +837,7 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     BiVecs<T> w;
     TG_CHECK(bicg_vecs<T>(op, n, &w));
     const int g = grid_for(n, 8);
-    TG_CHECK(red_ready(op, (size_t)g * 4 * sizeof(D)));
+    TG_CHECK(red_ready(op, (size_t)g * 4 * sizeof(D), s));
     D *part = wsp<D>(op, S_PART);
     unsigned *tk = wsp<unsigned>(op, S_TICKET);
     BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL));
@@ -903,7 +935,7 @@ static int true_residual(tg_op *op, const DevOp &A, const T *b, const T *x, T *r
     using D = typename ST<T>::D;
     const int n = A.n;
     const int g = grid_for(n, 8);
-    TG_CHECK(red_ready(op, (size_t)g * 2 * sizeof(D)));
+    TG_CHECK(red_ready(op, (size_t)g * 2 * sizeof(D), s));
     D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 2048);
     double xb, fl;
     op_cost(A, &xb, &fl);
@@ -934,14 +966,14 @@ static int solve_bicg64(tg_op *op, int transpose, const tg_defl *df, const T *b,
     else if (nb == 0.0 || nr <= cfg.rtol * nb) status = TG_OK;
     while (status == TG_NOT_CONVERGED) {
         ++cyc;
-        if (cfg.ncyc && cyc > cfg.ncyc) break;
+        const bool sched = cfg.ncyc && cyc <= cfg.ncyc;   // beyond ncyc: finish with rtol ||b|| / ||r||
         if (df && df->kk > 0) {                                    // step a
             TG_CHECK(project64<T>(op, df, x, r, s));
             double rr;
             TG_CHECK(dot_host<T>(op, r, nullptr, n, &rr, nullptr, s));
             nr = sqrt(rr);
         }
-        double rt = cfg.ncyc ? cycle_tol(cfg.rtol, nb, nr, cyc, cfg.ncyc) : cfg.rtol * nb / nr;   // step b
+        double rt = sched ? cycle_tol(cfg.rtol, nb, nr, cyc, cfg.ncyc) : cfg.rtol * nb / nr;   // step b
         hist_push(st, nr / nb, rt, mvps);
         int64_t cap64 = cfg.max_mvps - mvps;
         if (cfg.restart_mvps > 0 && cap64 > cfg.restart_mvps) cap64 = cfg.restart_mvps;
@@ -987,7 +1019,7 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
     const int g = grid_for(n, 8);
     while (status == TG_NOT_CONVERGED) {
         ++cyc;
-        if (cfg.ncyc && cyc > cfg.ncyc) break;
+        const bool sched = cfg.ncyc && cyc <= cfg.ncyc;   // beyond ncyc: finish with rtol ||b|| / ||r||
         // correction equation A e = r, scaled so that ||r32|| = 1
         TG_PROF(P_CONVERT, 12.0 * n, n, launch_d2f_scaled(g, s, r, r32, n, 1.0 / nr));
         TG_CHECK_CUDA(cudaMemsetAsync(e32, 0, (size_t)n * 4, s));
@@ -1001,7 +1033,7 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
             nrel = sqrt(rr);
         }
         const double nrp = nrel * scale;    // residual norm after the projection
-        double rt = cfg.ncyc ? cycle_tol(cfg.rtol, nb, nrp, cyc, cfg.ncyc) : cfg.rtol * nb / nrp;
+        double rt = sched ? cycle_tol(cfg.rtol, nb, nrp, cyc, cfg.ncyc) : cfg.rtol * nb / nrp;
         if (rt < 1e-6) rt = 1e-6;   // a float32 cycle cannot resolve more; refinement continues
         hist_push(st, nrp / nb, rt, mvps);
         int64_t cap64 = cfg.max_mvps - mvps;
@@ -1039,7 +1071,7 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     // fused update + norm
     T *w = V + (size_t)(j + 1) * ldv;
     TG_CHECK(launch_apply<T>(A, A32, V + (size_t)j * ldv, w, s));
-    TG_CHECK(red_ready(op, 0));
+    TG_CHECK(red_ready(op, 0, s));
     char *sm = wsp<char>(op, S_SMALL);
     D *h1 = reinterpret_cast<D *>(sm + 16384);           // j+2 entries: V_j^H w and ||w||^2
     D *h2 = reinterpret_cast<D *>(sm + 16384 + 4096);
@@ -1051,7 +1083,7 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     const int ncol = j + 1;
     D *part = wsp<D>(op, S_PART);
     unsigned *tk = wsp<unsigned>(op, S_TICKET);
-    TG_CHECK(red_ready(op, (size_t)gb * (ncol + 1) * sizeof(D)));
+    TG_CHECK(red_ready(op, (size_t)gb * (ncol + 1) * sizeof(D), s));
     part = wsp<D>(op, S_PART);
     // pass 1: h1 = [V_j, w]^H w
     bool piped = false;
@@ -1211,7 +1243,7 @@ namespace tg {
 template <class T>
 static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int k, int nev, double rtolev,
                         double rtol, int max_cycles, void *xc_out, tg_defl **defl_out, int proj, int precision,
-                        tg_stats *stats, cudaStream_t s) {
+                        tg_stats *stats, cudaStream_t s, tg_defl *reuse = nullptr) {
     using D = T;
     const DevOp &A = pick(op, TG_COARSE, transpose);
     const DevOp32 &A32 = pick32(op, TG_COARSE, transpose);
@@ -1330,15 +1362,22 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     }
     if (xc_out) TG_CHECK_CUDA(cudaMemcpyAsync(xc_out, xc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
     if (defl_out) {
-        DBuf Yc;
-        TG_CHECK(Yc.ensure((size_t)nc * kk * es));
+        TG_CHECK(wsx(op, S_GYC, (size_t)nc * kk * es));
+        DBuf &Yc = op->ws[S_GYC];
         TG_CHECK(tsm<T>(V, ldv, m, wsp<T>(op, S_GP), m + 1, kk, Yc.as<T>(), nc, nc, s));
-        tg_defl *d;
-        TG_CHECK(defl_create(op, transpose, kk, proj, precision, &d));
+        tg_defl *d = reuse;
+        if (d) {
+            // rebuild in the caller's handle: its buffers grow only when needed
+            d->kk = kk; d->n = op->n; d->proj = proj; d->precision = precision; d->cplx_ = op->cplx_;
+            d->transposed = transpose != 0;
+            TG_CHECK(d->Y.ensure((size_t)op->n * kk * es));
+        } else {
+            TG_CHECK(defl_create(op, transpose, kk, proj, precision, &d));
+        }
         int rc = prolong_impl(op, Yc.p, d->Y.p, kk, s);
         if (!rc) rc = build_defl<T>(op, transpose, d, s);
         if (rc) {
-            delete d;
+            if (!reuse) delete d;
             return rc;
         }
         *defl_out = d;
@@ -1497,3 +1536,372 @@ extern "C" int tg_profile_read(char *json, int cap) {
 }
 
 extern "C" int64_t tg_launch_count(void) { return g_prof.launches; }
+
+// ============================================================================= batched solver
+// Many independent instances (each its own operator, coarse grid and deflation basis),
+// each with R right-hand sides stored point-major (element (j, q) of instance i at
+// offset_i + j * R + q).  Set-up runs coarse GMRES-DR per instance; the solve runs the
+// float32-inner / float64-refinement BiCGStab(ncyc)-Proj(k) on the R columns of an
+// instance together (one read of the basis and of the stencil neighbourhood serves all R),
+// with the iteration batch captured once as a CUDA graph and replayed; instances are
+// processed concurrently by a pool of host threads, one CUDA stream per instance.
+namespace tg {
+
+constexpr int kBatchR = 8;
+constexpr int kGraphIters = 8;
+
+struct BatchInst {
+    DBuf rh, p, v, s, t, r32, e32, r64, part, small, tmp;
+    PinBuf pin;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    ~BatchInst() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+}  // namespace tg
+
+struct tg_batch {
+    int count = 0;
+    int R = tg::kBatchR;
+    std::vector<tg_op *> ops;
+    std::vector<tg_defl *> defls;
+    std::vector<int64_t> off;
+    int64_t total = 0;
+    int device = 0;
+    std::vector<std::unique_ptr<tg::BatchInst>> inst;
+    ~tg_batch() {
+        for (auto *d : defls) delete d;
+        for (auto *o : ops) delete o;
+    }
+};
+
+namespace tg {
+
+// Runs f(i) for i in [0, count) on up to `threads` host threads (each bound to `device`).
+template <class F>
+static int parallel_for(int count, int threads, int device, F f) {
+    std::atomic<int> next{0};
+    std::atomic<int> first_err{TG_OK};
+    std::mutex err_mu;
+    std::string err_text;
+    auto worker = [&]() {
+        cudaSetDevice(device);
+        while (true) {
+            const int i = next.fetch_add(1);
+            if (i >= count || first_err.load() != TG_OK) break;
+            const int rc = f(i);
+            if (rc != TG_OK) {
+                int expected = TG_OK;
+                if (first_err.compare_exchange_strong(expected, rc)) {
+                    std::lock_guard<std::mutex> lock(err_mu);
+                    err_text = g_err;
+                }
+            }
+        }
+    };
+    threads = std::max(1, std::min(threads, count));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+    if (first_err.load() != TG_OK) g_err = err_text;
+    return first_err.load();
+}
+
+// small-area layout of one instance (bytes)
+struct MrSmall {
+    static constexpr size_t st = 0;              // BiState<double>[R]
+    static constexpr size_t ctl = 2048;          // MrCtl
+    static constexpr size_t ticket = 2304;       // unsigned
+    static constexpr size_t target2 = 2560;      // double[R]
+    static constexpr size_t inv = 2816;          // double[R]
+    static constexpr size_t scale = 3072;        // double[R]
+    static constexpr size_t norms = 3328;        // double[2R] (residual) / [R] (projection)
+    static constexpr size_t cvec = 4096;         // double[k R]
+    static constexpr size_t dvec = 8192;         // double[k R]
+    static constexpr size_t bytes = 12288;
+};
+
+static int batch_inst_ready(tg_batch *b, int i) {
+    BatchInst &I = *b->inst[i];
+    const int n = b->ops[i]->n;
+    const size_t fb = (size_t)n * kBatchR * 4, db = (size_t)n * kBatchR * 8;
+    TG_CHECK(I.rh.ensure(fb));
+    TG_CHECK(I.p.ensure(fb));
+    TG_CHECK(I.v.ensure(fb));
+    TG_CHECK(I.s.ensure(fb));
+    TG_CHECK(I.t.ensure(fb));
+    TG_CHECK(I.r32.ensure(fb));
+    TG_CHECK(I.e32.ensure(fb));
+    TG_CHECK(I.r64.ensure(db));
+    TG_CHECK(I.part.ensure((size_t)4 << 20));
+    if (!I.stream) TG_CHECK_CUDA(cudaStreamCreateWithFlags(&I.stream, cudaStreamNonBlocking));
+    if (!I.small.p) {
+        TG_CHECK(I.small.ensure(MrSmall::bytes));
+        TG_CHECK_CUDA(cudaMemsetAsync(I.small.p, 0, MrSmall::bytes, I.stream));
+    }
+    TG_CHECK(I.pin.ensure(4096));
+    return TG_OK;
+}
+
+static void batch_iters(const DevOp &A, const DevOp32 &A32, BatchInst &I, int n, int g, int iters) {
+    char *sm = I.small.as<char>();
+    BiState<double> *st = reinterpret_cast<BiState<double> *>(sm + MrSmall::st);
+    MrCtl *ctl = reinterpret_cast<MrCtl *>(sm + MrSmall::ctl);
+    unsigned *tk = reinterpret_cast<unsigned *>(sm + MrSmall::ticket);
+    double *part = I.part.as<double>();
+    float *rh = I.rh.as<float>(), *p = I.p.as<float>(), *v = I.v.as<float>(), *s = I.s.as<float>(),
+          *t = I.t.as<float>(), *r = I.r32.as<float>(), *x = I.e32.as<float>();
+    for (int it = 0; it < iters; ++it) {
+        k_mr_bi_v<kBatchR><<<g, kThreads, 0, I.stream>>>(A, A32, p, rh, v, part, tk, st, ctl);
+        k_mr_bi_s<kBatchR><<<g, kThreads, 0, I.stream>>>(r, v, s, n, part, tk, st, ctl);
+        k_mr_bi_t<kBatchR><<<g, kThreads, 0, I.stream>>>(A, A32, s, rh, t, part, tk, st, ctl);
+        k_mr_bi_x<kBatchR><<<g, kThreads, 0, I.stream>>>(x, r, p, s, t, v, n, part, tk, st, ctl);
+    }
+}
+
+static int batch_solve_one(tg_batch *b, int i, const double *B, double *X, const SolveCfg &cfg, tg_stats *stats) {
+    constexpr int R = kBatchR;
+    tg_op *op = b->ops[i];
+    const tg_defl *df = b->defls.empty() ? nullptr : b->defls[i];
+    TG_CHECK(batch_inst_ready(b, i));
+    BatchInst &I = *b->inst[i];
+    cudaStream_t s = I.stream;
+    const DevOp &A = op->fine.A;
+    const DevOp32 &A32 = op->fine.A32;
+    const int n = op->n;
+    const int g = grid_for(n, 8);
+    char *sm = I.small.as<char>();
+    double *part = I.part.as<double>();
+    unsigned *tk = reinterpret_cast<unsigned *>(sm + MrSmall::ticket);
+    double *d_norms = reinterpret_cast<double *>(sm + MrSmall::norms);
+    double *d_t2 = reinterpret_cast<double *>(sm + MrSmall::target2);
+    double *d_inv = reinterpret_cast<double *>(sm + MrSmall::inv);
+    double *d_scale = reinterpret_cast<double *>(sm + MrSmall::scale);
+    double *cvec = reinterpret_cast<double *>(sm + MrSmall::cvec);
+    double *dvec = reinterpret_cast<double *>(sm + MrSmall::dvec);
+    BiState<double> *st = reinterpret_cast<BiState<double> *>(sm + MrSmall::st);
+    MrCtl *ctl = reinterpret_cast<MrCtl *>(sm + MrSmall::ctl);
+    double *hp = reinterpret_cast<double *>(I.pin.p);
+    const int kk = df ? df->kk : 0;
+    if (kk > 32) {
+        set_error("batched projection supports k <= 32 (got %d)", kk);
+        return TG_BAD_ARG;
+    }
+    if (!I.graph) {
+        // the iteration batch as one CUDA graph (captured once per instance)
+        cudaGraph_t graph;
+        TG_CHECK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        batch_iters(A, A32, I, n, g, kGraphIters);
+        TG_CHECK_CUDA(cudaStreamEndCapture(s, &graph));
+        cudaError_t e = cudaGraphInstantiate(&I.graph, graph, 0);
+        cudaGraphDestroy(graph);
+        TG_CHECK_CUDA(e);
+    }
+    auto residual = [&](double *nr, double *nb) -> int {
+        TG_PROF(P_RESIDUAL, (3.0 * 8 * R) * n, 12.0 * R * n,
+                k_mr_residual<R><<<g, kThreads, 0, s>>>(A, B, X, I.r64.as<double>(), part, tk, d_norms));
+        TG_CHECK_CUDA(cudaMemcpyAsync(hp, d_norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TG_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int q = 0; q < R; ++q) {
+            nr[q] = sqrt(hp[q]);
+            nb[q] = sqrt(hp[R + q]);
+        }
+        return TG_OK;
+    };
+    double nr[R], nb[R];
+    int64_t mv[R] = {0};
+    int status[R];
+    TG_CHECK(residual(nr, nb));
+    for (int q = 0; q < R; ++q) status[q] = (nb[q] == 0.0 || nr[q] <= cfg.rtol * nb[q]) ? TG_OK : TG_NOT_CONVERGED;
+    int cyc = 0;
+    while (true) {
+        bool any = false;
+        for (int q = 0; q < R; ++q) any |= status[q] == TG_NOT_CONVERGED;
+        if (!any) break;
+        ++cyc;
+        const bool sched = cfg.ncyc && cyc <= cfg.ncyc;   // beyond ncyc: finish with rtol ||b|| / ||r||
+        // correction equations A e_q = r_q / ||r_q|| in float32
+        for (int q = 0; q < R; ++q) {
+            const bool on = status[q] == TG_NOT_CONVERGED;
+            hp[q] = on ? 1.0 / nr[q] : 0.0;
+            hp[R + q] = on ? nr[q] : 0.0;
+        }
+        TG_CHECK_CUDA(cudaMemcpyAsync(d_inv, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(d_scale, hp + R, R * sizeof(double), cudaMemcpyHostToDevice, s));
+        TG_PROF(P_CONVERT, 16.0 * R * n, R * n,
+                k_mr_scale<R><<<grid_for((int64_t)n * R, 8), kThreads, 0, s>>>(I.r64.as<double>(), I.r32.as<float>(),
+                                                                                 I.e32.as<float>(), n, d_inv));
+        double nrel[R];
+        for (int q = 0; q < R; ++q) nrel[q] = 1.0;
+        if (kk > 0) {
+            const float *W = df->W32.as<float>(), *B1 = df->B1_32.as<float>(), *B2 = df->B2_32.as<float>();
+            const int gp = std::max(1, std::min((n + 127) / 128, num_sms() * 8));
+            const size_t smem = ((size_t)kk * 128 + 128 * R) * sizeof(float);
+            TG_PROF(P_GEMV_T, (double)(kk + R) * n * 4, 2.0 * kk * R * n,
+                    k_mr_proj_dots<R><<<gp, kThreads, smem, s>>>(W, kk, I.r32.as<float>(), n, part));
+            TG_PROF(P_SUM_PART, (double)gp * kk * R * 8, (double)gp * kk * R,
+                    k_sum_part<double><<<(kk * R + 7) / 8, 256, 0, s>>>(part, gp, kk * R, cvec, 0));
+            TG_PROF(P_SMALL, 0, 2.0 * kk * kk * R, k_mr_small<R><<<1, 256, 0, s>>>(df->M.as<double>(), kk, cvec, dvec));
+            const double *ee = df->proj == TG_PROJ_MINRES ? cvec : dvec;
+            TG_PROF(P_PROJ, (2.0 * kk + 4.0 * R) * n * 4, 4.0 * kk * R * n,
+                    k_mr_proj_update<R><<<g, kThreads, 0, s>>>(B1, B2, kk, dvec, ee, I.e32.as<float>(),
+                                                              I.r32.as<float>(), n, part, tk, d_norms));
+            TG_CHECK_CUDA(cudaMemcpyAsync(hp, d_norms, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+            TG_CHECK_CUDA(cudaStreamSynchronize(s));
+            for (int q = 0; q < R; ++q) nrel[q] = sqrt(hp[q]);
+        }
+        int64_t cap64 = cfg.max_mvps;
+        for (int q = 0; q < R; ++q) {
+            const bool on = status[q] == TG_NOT_CONVERGED;
+            double t2 = -1.0;
+            if (on) {
+                const double nrp = nrel[q] * nr[q];
+                double rt = sched ? cycle_tol(cfg.rtol, nb[q], nrp, cyc, cfg.ncyc) : cfg.rtol * nb[q] / nrp;
+                if (rt < 1e-6) rt = 1e-6;
+                t2 = (rt * nrel[q]) * (rt * nrel[q]);
+                cap64 = std::min<int64_t>(cap64, cfg.max_mvps - mv[q]);
+            }
+            hp[q] = t2;
+        }
+        if (cfg.restart_mvps > 0) cap64 = std::min<int64_t>(cap64, cfg.restart_mvps);
+        cap64 = std::max<int64_t>(1, std::min<int64_t>(cap64, INT_MAX / 2));
+        TG_CHECK_CUDA(cudaMemcpyAsync(d_t2, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
+        TG_PROF(P_BI_INIT, 12.0 * R * n, 2.0 * R * n,
+                k_mr_bi_init<R><<<g, kThreads, 0, s>>>(I.r32.as<float>(), I.rh.as<float>(), I.p.as<float>(), n, d_t2,
+                                                       (int)cap64, part, tk, st, ctl));
+        int graphs = 0;
+        while (true) {
+            TG_CHECK_CUDA(cudaGraphLaunch(I.graph, s));
+            __atomic_add_fetch(&g_prof.launches, 4 * kGraphIters, __ATOMIC_RELAXED);
+            ++graphs;
+            MrCtl hc;
+            TG_CHECK_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(MrCtl), cudaMemcpyDeviceToHost, s));
+            TG_CHECK_CUDA(cudaStreamSynchronize(s));
+            if (hc.active == 0) break;
+            if ((int64_t)graphs * kGraphIters > cap64 + 8) {
+                set_error("batched BiCGStab cycle exceeded its product cap");
+                return TG_SYNC_TIMEOUT;
+            }
+        }
+        BiState<double> hs[R];
+        TG_CHECK_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        TG_PROF(P_CONVERT, 12.0 * R * n, 2.0 * R * n,
+                k_mr_add<R><<<grid_for((int64_t)n * R, 8), kThreads, 0, s>>>(X, I.e32.as<float>(), n, d_scale));
+        TG_CHECK_CUDA(cudaStreamSynchronize(s));
+        TG_CHECK(residual(nr, nb));
+        bool stuck = true;
+        for (int q = 0; q < R; ++q) {
+            if (status[q] != TG_NOT_CONVERGED) continue;
+            mv[q] += hs[q].mvps;
+            if (hs[q].mvps > 0) stuck = false;
+            if (!std::isfinite(nr[q]) || hs[q].status == 4) status[q] = TG_NAN;
+            else if (nr[q] <= cfg.rtol * nb[q]) status[q] = TG_OK;
+            else if (mv[q] >= cfg.max_mvps) status[q] = TG_NOT_CONVERGED + 100;   // out of budget
+        }
+        if (stuck) break;
+    }
+    for (int q = 0; q < R; ++q) {
+        if (status[q] == TG_NOT_CONVERGED + 100) status[q] = TG_NOT_CONVERGED;
+        if (stats) {
+            tg_stats &o = stats[(size_t)i * R + q];
+            o.mvps = mv[q];
+            o.cycles = cyc;
+            o.relres = nb[q] > 0 ? nr[q] / nb[q] : 0.0;
+            o.status = status[q];
+            o.vops = mv[q] * 7;
+        }
+    }
+    for (int q = 0; q < R; ++q)
+        if (status[q] != TG_OK) return status[q] == TG_NOT_CONVERGED ? TG_NOT_CONVERGED : status[q];
+    return TG_OK;
+}
+
+}  // namespace tg
+
+extern "C" int tg_batch_create(tg_batch **out, int count, const int64_t *Ns, const double *betas, int nrhs,
+                               void *stream) {
+    TG_ARG(out && Ns && betas && count >= 1, "bad argument");
+    TG_ARG(nrhs == kBatchR, "the batched solver takes %d right-hand sides per instance (got %d)", kBatchR, nrhs);
+    *out = nullptr;
+    tg_batch *b = new tg_batch();
+    b->count = count;
+    cudaGetDevice(&b->device);
+    for (int i = 0; i < count; ++i) {
+        tg_op *op = nullptr;
+        const double beta3[3] = {betas[i], 0.0, 0.0};
+        int rc = tg_setup_operator(&op, TG_CD2D, Ns + i, 1, beta3, nullptr, nullptr, 2, stream);
+        if (rc != TG_OK) {
+            delete b;
+            return rc;
+        }
+        b->ops.push_back(op);
+        b->off.push_back(b->total);
+        b->total += (int64_t)op->n * kBatchR;
+        b->inst.emplace_back(new BatchInst());
+    }
+    *out = b;
+    return TG_OK;
+}
+
+extern "C" int tg_destroy_batch(tg_batch *b) {
+    delete b;
+    return TG_OK;
+}
+
+extern "C" int tg_batch_layout(const tg_batch *b, int i, int64_t *offset, int64_t *n) {
+    TG_ARG(b && i >= 0 && i < b->count, "bad instance index");
+    if (offset) *offset = b->off[i];
+    if (n) *n = b->ops[i]->n;
+    return TG_OK;
+}
+
+extern "C" int tg_batch_setup(tg_batch *b, const void *rhs, int m, int k, int nev, double rtolev, double rtol,
+                              int max_cycles, int proj, int threads, tg_stats *stats, void *stream) {
+    TG_ARG(b && rhs, "NULL argument");
+    TG_ARG(k >= 1 && k <= 32, "the batched projection takes 1 <= k <= 32 (got %d)", k);
+    TG_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if ((int)b->defls.size() != b->count) b->defls.assign(b->count, nullptr);   // handles are rebuilt in place
+    const double *R0 = static_cast<const double *>(rhs);
+    return parallel_for(b->count, threads, b->device, [&](int i) -> int {
+        TG_CHECK(batch_inst_ready(b, i));
+        BatchInst &I = *b->inst[i];
+        tg_op *op = b->ops[i];
+        TG_CHECK(I.tmp.ensure((size_t)op->n * 8));
+        k_mr_extract<kBatchR><<<grid_for(op->n, 8), kThreads, 0, I.stream>>>(R0 + b->off[i], 0, op->n, I.tmp.as<double>());
+        TG_LAUNCH_CHECK();
+        tg_stats st{};
+        tg_defl *d = nullptr;
+        TG_ARG(m >= 2 && m <= kMaxM && k < m - 1 && m < op->nc && nev >= 0 && nev <= k, "bad GMRES-DR sizes");
+        int rc = gmresdr_impl<double>(op, 0, I.tmp.p, m, k, nev, rtolev, rtol, max_cycles, nullptr, &d, proj,
+                                      TG_F32_IR, &st, I.stream, b->defls[i]);
+        if (stats) stats[i] = st;
+        if (rc != TG_OK && rc != TG_NOT_CONVERGED) return rc;
+        b->defls[i] = d;
+        return TG_OK;
+    });
+}
+
+extern "C" int tg_batch_solve(tg_batch *b, const void *rhs, void *x, double rtol, int ncyc, int restart_mvps,
+                              int64_t max_mvps, int threads, tg_stats *stats, void *stream) {
+    TG_ARG(b && rhs && x, "NULL argument");
+    TG_ARG(rtol > 0 && rtol < 1, "rtol must be in (0, 1)");
+    TG_ARG(ncyc > 0 || restart_mvps > 0, "fixed-length restarting needs restart_mvps > 0");
+    TG_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    SolveCfg cfg{rtol, ncyc, restart_mvps, 0, max_mvps};
+    const double *B = static_cast<const double *>(rhs);
+    double *X = static_cast<double *>(x);
+    std::vector<int> rcs(b->count, TG_OK);
+    int rc = parallel_for(b->count, threads, b->device, [&](int i) -> int {
+        int r = batch_solve_one(b, i, B + b->off[i], X + b->off[i], cfg, stats);
+        rcs[i] = r;
+        return (r == TG_NOT_CONVERGED || r == TG_BREAKDOWN) ? TG_OK : r;   // keep going on numerical failures
+    });
+    if (rc != TG_OK) return rc;
+    for (int r : rcs)
+        if (r != TG_OK) return r;
+    return TG_OK;
+}

@@ -1180,8 +1180,9 @@ void launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
         smem += parts[q];
         a.smem = q + 1;
     }
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute((const void *)k_gmresdr_restart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024)   // one fixed value: concurrent callers cannot lower it under each other
+        cudaFuncSetAttribute((const void *)k_gmresdr_restart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGdrSmemMax);
     k_gmresdr_restart<T><<<1, kGdrThreads, smem, s>>>(a);
 }
 template <class D>

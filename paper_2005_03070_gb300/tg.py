@@ -35,6 +35,7 @@ EXPORTS = [
     "tg_prolong", "tg_restrict", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
     "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_adjoint_solve", "tg_kappa_gradient",
     "tg_harmonic_ritz", "tg_harmonic_ritz_noalloc", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
+    "tg_batch_create", "tg_batch_layout", "tg_batch_setup", "tg_batch_solve", "tg_destroy_batch",
 ]
 
 
@@ -89,6 +90,11 @@ def load() -> C.CDLL:
         "tg_kappa_gradient": (i32, [vp, vp, vp, vp, vp]),
         "tg_harmonic_ritz": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
         "tg_harmonic_ritz_noalloc": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
+        "tg_batch_create": (i32, [C.POINTER(vp), i32, C.POINTER(i64), C.POINTER(dbl), i32, vp]),
+        "tg_batch_layout": (i32, [vp, i32, C.POINTER(i64), C.POINTER(i64)]),
+        "tg_batch_setup": (i32, [vp, vp, i32, i32, i32, dbl, dbl, i32, i32, i32, C.POINTER(TgStats), vp]),
+        "tg_batch_solve": (i32, [vp, vp, vp, dbl, i32, i32, i64, i32, C.POINTER(TgStats), vp]),
+        "tg_destroy_batch": (i32, [vp]),
         "tg_profile_enable": (i32, [i32]),
         "tg_profile_read": (i32, [C.c_char_p, i32]),
         "tg_launch_count": (i64, []),
@@ -302,3 +308,47 @@ def tg_profile_read() -> dict:
 
 def tg_launch_count() -> int:
     return int(load().tg_launch_count())
+
+
+class Batch:
+    """tg_batch_*: independent 2D convection-diffusion instances, 8 right-hand sides each,
+    sharing one deflation basis per instance (float32 inner / float64 refinement)."""
+    R = 8
+
+    def __init__(self, Ns, betas, stream=None):
+        lib = load()
+        self.count = len(Ns)
+        h = C.c_void_p()
+        ns = (C.c_int64 * self.count)(*[int(v) for v in Ns])
+        bs = (C.c_double * self.count)(*[float(v) for v in betas])
+        _check(lib.tg_batch_create(C.byref(h), self.count, ns, bs, self.R, _stream(stream)), "tg_batch_create")
+        self._h = h
+        self.offsets, self.sizes = [], []
+        for i in range(self.count):
+            o, n = C.c_int64(), C.c_int64()
+            _check(lib.tg_batch_layout(h, i, C.byref(o), C.byref(n)), "tg_batch_layout")
+            self.offsets.append(o.value)
+            self.sizes.append(n.value)
+        self.total = self.offsets[-1] + self.sizes[-1] * self.R
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.tg_destroy_batch(self._h)
+            self._h = None
+
+    def setup(self, rhs, m=40, k=20, nev=None, rtolev=1e-2, rtol=1e-8, max_cycles=300, proj="minres", threads=16,
+              stream=None):
+        nev = k if nev is None else nev
+        stats = (TgStats * self.count)()
+        st = _lib.tg_batch_setup(self._h, _ptr(rhs), m, k, nev, rtolev, rtol, max_cycles, PROJ[proj], threads, stats,
+                                 _stream(stream))
+        _check(st, "tg_batch_setup")
+        return [s.as_dict() for s in stats]
+
+    def solve(self, rhs, x, rtol=1e-8, ncyc=20, restart_mvps=0, max_mvps=10 ** 6, threads=16, stream=None):
+        stats = (TgStats * (self.count * self.R))()
+        st = _lib.tg_batch_solve(self._h, _ptr(rhs), _ptr(x), rtol, ncyc, restart_mvps, max_mvps, threads, stats,
+                                 _stream(stream))
+        if st in (TG_BAD_ARG, TG_OOM, TG_CUDA_ERROR, TG_SYNC_TIMEOUT):
+            _check(st, "tg_batch_solve")
+        return st, [s.as_dict() for s in stats]

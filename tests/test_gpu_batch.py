@@ -1,0 +1,78 @@
+"""Batched form (many instances x 8 right-hand sides, float32 inner / float64 refinement)
+against the oracle's direct solves, and against the per-instance float64 path.
+
+Bars: every column reaches ||b - A x|| / ||b|| <= rtol (recomputed here by the oracle's
+float64 operator) and ||x - x*|| / ||x*|| <= 1e-6 with x* = A^{-1} b (sparse LU), at
+rtol = 1e-10 (see tests/test_gpu_solve.py for why parity runs use 1e-10)."""
+import numpy as np
+import pytest
+
+import tg_inputs as gi
+from oracle.operators import CD2D, Operator as OOp
+from oracle.twogrid import exact_solution
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_03070_gb300 import build
+    build.build()
+    from paper_2005_03070_gb300 import tg as mod
+    mod.load()
+    return mod
+
+
+def _batch_inputs(Ns, seed=0):
+    blocks = []
+    for i, N in enumerate(Ns):
+        B = gi.rhs(N * N, seed=100 + i, nrhs=8)          # (8, n)
+        blocks.append(np.ascontiguousarray(B.T).reshape(-1))   # point-major n x 8
+    return blocks
+
+
+@pytest.mark.parametrize("ncyc,restart", [(20, 0), (0, 60)])
+def test_batch_matches_direct_solves(tg, ncyc, restart):
+    Ns = [31, 15, 63, 47, 17, 33]
+    Ns, betas = Ns, [0.7, 3.5, 1.0, 2.2, 0.5, 4.0]
+    batch = tg.Batch(Ns, betas)
+    blocks = _batch_inputs(Ns)
+    rhs = torch.from_numpy(np.concatenate(blocks)).cuda()
+    assert rhs.numel() == batch.total
+    cst = batch.setup(rhs, m=20, k=8, rtolev=1e-2, threads=4)
+    assert all(s["kk"] >= 8 for s in cst)
+    x = torch.zeros_like(rhs)
+    status, stats = batch.solve(rhs, x, rtol=1e-10, ncyc=ncyc, restart_mvps=restart, threads=4)
+    assert status == tg.TG_OK, [s["status"] for s in stats]
+    xh = x.cpu().numpy()
+    for i, N in enumerate(Ns):
+        op = OOp(CD2D, N, (betas[i],))
+        o, n = batch.offsets[i], batch.sizes[i]
+        B = blocks[i].reshape(n, 8)
+        X = xh[o:o + n * 8].reshape(n, 8)
+        for q in range(8):
+            b = B[:, q]
+            xq = X[:, q]
+            assert np.linalg.norm(b - op.apply(xq)) / np.linalg.norm(b) <= 1e-10
+            xs = exact_solution(op, b)
+            assert np.linalg.norm(xq - xs) / np.linalg.norm(xs) <= 1e-6
+            assert stats[i * 8 + q]["relres"] <= 1e-10
+
+
+def test_batch_per_instance_fp64_path(tg):
+    # the same instances solved one column at a time in float64 with the set-up's bases
+    Ns, betas = [31, 15], [0.7, 3.5]
+    ops = [tg.Operator("cd2d", N, (b,)) for N, b in zip(Ns, betas)]
+    for i, (op, N) in enumerate(zip(ops, Ns)):
+        B = gi.rhs(N * N, seed=100 + i, nrhs=8)
+        xc, defl, _, _ = op.coarse_gmresdr(torch.from_numpy(B[0]).cuda(), 20, 8, rtolev=1e-2)
+        for q in range(8):
+            b = torch.from_numpy(B[q]).cuda()
+            x = torch.zeros_like(b)
+            st, s = op.solve(b, x, defl, rtol=1e-10, ncyc=20, restart_mvps=0)
+            assert st == tg.TG_OK
+            xs = exact_solution(OOp(CD2D, N, (betas[i],)), B[q])
+            assert np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs) <= 1e-6
