@@ -41,6 +41,9 @@ WORKLOADS = {
     "cd3d_191": dict(kind="cd3d", N=191, beta=(2.0, 1.0, 0.5), m=60, k=30, nev=30, rtolev=1e-2, rtol_c=1e-8,
                      max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20,
                      restart_mvps=0, m3=20),
+    # 32^4 U(1) lattice, complex128, mass tuned to lambda_min = 1e-3, coarse 16^4 Galerkin, k = 40
+    "u1_32": dict(kind="u1_4d", N=32, m=80, k=40, nev=40, rtolev=1e-2, rtol_c=1e-8, max_cycles=300,
+                  method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20, restart_mvps=0, m3=20),
     # 128 independent 2D problems, N_i odd ~ U{255..1023}, beta_i ~ U(0.5, 4), 8 right-hand
     # sides each sharing one 20-vector basis; float32 inner BiCGStab, float64 refinement
     "batch128": dict(kind="batch", count=128, m=40, k=20, nev=20, rtolev=1e-2, rtol_c=1e-8, max_cycles=300,
@@ -123,6 +126,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+# ----------------------------------------------------------------------------- lattice input
+def lattice_operator(tg, L, seed=0, lam_min=1e-3, iters=200):
+    """The lattice workload's operator: links from the seeded generator and the mass that
+    puts the smallest eigenvalue at lam_min.  lambda_max of the hopping term D comes from
+    plain Lanczos whose products are the library's own operator (mass -8 gives -D);
+    input preparation, outside any timed region."""
+    import numpy as np
+    import torch
+
+    import tg_inputs as gi
+    links = torch.from_numpy(gi.u1_links(L, seed)).cuda()
+    op0 = tg.Operator("u1_4d", L, links=links, mass=-8.0)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    V = L ** 4
+    q = torch.complex(torch.randn(V, generator=g, dtype=torch.float64),
+                      torch.randn(V, generator=g, dtype=torch.float64)).cuda()
+    q /= torch.linalg.vector_norm(q)
+    qprev = torch.zeros_like(q)
+    alpha, betas, b = [], [], 0.0
+    for _ in range(iters):
+        w = -op0.apply(q)
+        a = torch.vdot(q, w).real.item()
+        w = w - a * q - b * qprev
+        alpha.append(a)
+        b = torch.linalg.vector_norm(w).item()
+        betas.append(b)
+        qprev, q = q, w / b
+    T = np.diag(alpha) + np.diag(betas[:-1], 1) + np.diag(betas[:-1], -1)
+    mass = float(np.linalg.eigvalsh(T)[-1] - 8.0 + lam_min)
+    return tg.Operator("u1_4d", L, links=links, mass=mass), mass
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_tg(args, wl, rank, world):
     import numpy as np
@@ -134,9 +169,14 @@ def run_tg(args, wl, rank, world):
     from paper_2005_03070_gb300 import tg
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    op = tg.Operator(wl["kind"], wl["N"], wl["beta"])
+    if wl["kind"] == "u1_4d":
+        op, mass = lattice_operator(tg, wl["N"], seed=rank)
+        wl = dict(wl, mass=mass)
+        b_host = torch.from_numpy(gi.rhs(op.n, seed=rank).astype(np.complex128)).pin_memory()
+    else:
+        op = tg.Operator(wl["kind"], wl["N"], wl["beta"])
+        b_host = torch.from_numpy(gi.rhs(op.n, seed=rank)).pin_memory()
     n = op.n
-    b_host = torch.from_numpy(gi.rhs(n, seed=rank)).pin_memory()
     b = b_host.to(dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if n * 8 < L2_BYTES else None
 
@@ -155,7 +195,7 @@ def run_tg(args, wl, rank, world):
         stream = torch.cuda.current_stream()
         total_ms = 0.0
         infos = []
-        x_host = torch.empty(n, dtype=torch.float64).pin_memory() if host_io else None
+        x_host = torch.empty(n, dtype=op.dtype).pin_memory() if host_io else None
         if profile:
             tg.tg_profile_enable(True)
         l0 = tg.tg_launch_count()
@@ -256,17 +296,18 @@ def run_tg(args, wl, rank, world):
         "metric": "fine-grid solves/sec to rel. residual 1e-8 (FP64 vs batched FP32+IR) and HBM GB/s",
         "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded N(0,1) right-hand side)",
+        "vs_baseline": None, "dtype": "c128" if wl["kind"] == "u1_4d" else "f64",
+        "data": "synthetic (seeded N(0,1) right-hand side)",
         "config": {"workload": args.workload, **{k: (list(v) if isinstance(v, tuple) else v) for k, v in wl.items()},
                    "n": n, "n_coarse": op.nc,
-                   "l2": "inputs larger than L2 (133 MB per fine vector)" if flush is None else "L2 flushed between steps",
+                   "l2": "inputs larger than L2" if flush is None else "L2 flushed between steps",
                    "parallelism": f"replicas x{world}"},
         "solves_converged": ok,
         "step_breakdown": {"coarse_cycles": cst["cycles"], "coarse_mvps": cst["coarse_mvps"],
                            "eig_converged": cst["eig_converged"], "fine_mvps": st["mvps"],
                            "fine_cycles": st["cycles"], "relres": st["relres"]},
-        "e2e": {"value": round(world * 1000.0 / ms_e2e, 5), "unit": "solves/s", "h2d_bytes_per_step": n * 8,
-                "d2h_bytes_per_step": n * 8},
+        "e2e": {"value": round(world * 1000.0 / ms_e2e, 5), "unit": "solves/s",
+                "h2d_bytes_per_step": n * b_host.element_size(), "d2h_bytes_per_step": n * b_host.element_size()},
         "fp32_ir": None if ms_ir is None else {"value": round(world * 1000.0 / ms_ir, 5), "unit": "solves/s",
                                                "ms_per_step": round(ms_ir, 3), "converged": ir_ok,
                                                "speedup_vs_f64": round(ms / ms_ir, 3)},
@@ -366,7 +407,7 @@ def oracle_counts(workload):
 
 
 def run_batch(args, wl, rank, world):
-    """configs[3]: the batched float32+refinement form against the per-instance float64 path."""
+    """128 cd2d instances x 8 right-hand sides: the batched float32+refinement form against the per-instance float64 path."""
     import numpy as np
     import torch
 
@@ -536,7 +577,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
     line, counts = run_tg(args, wl, rank, world)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ("cd2d", "cd3d"):
         v, info = cpu_sample(wl, counts)
         line["cpu_baseline"] = {**info, "value": v, "unit": "solves/s"}
     if rank == 0:

@@ -73,6 +73,9 @@ typedef struct tg_stats {
                             /* (||r||/||b|| after the projection, rticyc, mvps so far)   */
     int32_t history_cap;
     int32_t history_len;    /* entries written                                           */
+    int32_t fp64_cycles;    /* TG_F32_IR: cycles finished in float64 after a float32      */
+                            /* correction failed to lower the float64 residual            */
+    int32_t reserved;
 } tg_stats;
 
 /* Human-readable text of a status code, and of the last error on this thread. */
@@ -166,7 +169,11 @@ int tg_project(const tg_op *op, const tg_defl *defl, void *x, void *r, void *str
  * most restart_mvps products (Example 2).  method TG_GMRES: GMRES(m3)-Proj(k), Section
  * 2.2.  The true residual b - A x is recomputed in float64 at every restart.
  * precision TG_F32_IR: each cycle solves the correction equation in float32 (projection
- * included) and adds the correction to the float64 x (iterative refinement).
+ * included) and adds the correction to the float64 x (iterative refinement).  A cycle
+ * whose correction does not lower the float64 residual (float32 rounding times the
+ * condition number near 1) is undone and the solve finishes in float64 cycles
+ * (stats.fp64_cycles counts them).  A BiCGStab cycle also stops when its residual
+ * has grown 1e4-fold (divergence).
  * b, x: device, n x nrhs column-major (x: in x0, out solution).  Each right-hand side
  * is solved in turn; stats (host, may be NULL) must hold nrhs entries.
  * Returns TG_OK if every right-hand side converged, else the first failure status.

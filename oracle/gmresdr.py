@@ -16,7 +16,7 @@ published GMRES-DR (the method the paper cites):
            Hbar_k <- P_{k+1}^H Hbar_m P_k; c <- P_{k+1}^H (c - Hbar_m d); then Arnoldi
            extends V to m + 1 columns and the least-squares problem is solved again.
 
-Readings taken (also in the design doc):
+Readings taken:
   * Order of the harmonic Ritz values: by |theta|, then Re theta, then Im theta >= 0 first.
     If the k-th value splits a complex-conjugate pair, k + 1 are kept for that cycle.
   * Real problems keep a real basis: Re g and Im g of each kept complex pair.

@@ -11,7 +11,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   bicgstab_proj                       BiCGStab(ncyc)-Proj(k), Section 4.1.
   gmres_cycle / gmres_proj            GMRES(m)-Proj(k), Section 2.2.
 
-Readings taken where the paper is silent (each also listed in the design doc):
+Readings taken where the paper is silent:
   * ||r0|| in the cycle tolerance is ||b||, so "relative residual" is ||b - Ax|| / ||b||.
   * ||r|| in step 3b is the residual after step 3a's projection.
   * Each BiCGStab cycle starts with shadow vector r_hat = r, p = v = 0; it stops when

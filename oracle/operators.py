@@ -301,33 +301,32 @@ def free_lattice_eigenvalues(L: int, mass: float) -> np.ndarray:
 
 
 def lattice_tuned_mass(links: np.ndarray, L: int, lam_min: float = 1e-3,
-                       iters: int = 300, seed: int = 0) -> float:
+                       iters: int = 200, seed: int = 0) -> float:
     """Mass m such that the smallest eigenvalue of u1_4d is lam_min.
 
     A = (m + 8) I - D with D the Hermitian hopping term, so lambda_min(A) = m + 8 -
-    lambda_max(D).  lambda_max(D) is found by plain Lanczos (full reorthogonalisation)
-    on D, then m = lambda_max(D) - 8 + lam_min.
+    lambda_max(D).  lambda_max(D) is the top Ritz value of plain Lanczos on D (the
+    extreme Ritz value converges without reorthogonalisation; loss of orthogonality only
+    adds copies of it), then m = lambda_max(D) - 8 + lam_min.
     """
     op0 = Operator(U1_4D, L, links=links, mass=-8.0)    # apply = -D
     rng = np.random.default_rng(seed)
     V = L ** 4
     q = rng.standard_normal(V) + 1j * rng.standard_normal(V)
     q /= np.linalg.norm(q)
-    Q = [q]
+    qprev = np.zeros_like(q)
     alpha, betas = [], []
     b = 0.0
-    qprev = np.zeros_like(q)
     for _ in range(iters):
         w = -op0.apply(q)
         a = np.vdot(q, w).real
         w = w - a * q - b * qprev
-        for qq in Q:
-            w -= np.vdot(qq, w) * qq
         alpha.append(a)
         b = np.linalg.norm(w)
         betas.append(b)
+        if b == 0.0:
+            break
         qprev, q = q, w / b
-        Q.append(q)
-    T = np.diag(alpha) + np.diag(betas[:-1], 1) + np.diag(betas[:-1], -1)
+    T = np.diag(alpha) + np.diag(betas[:len(alpha) - 1], 1) + np.diag(betas[:len(alpha) - 1], -1)
     lam_max = np.linalg.eigvalsh(T)[-1]
     return float(lam_max - 8.0 + lam_min)

@@ -198,7 +198,7 @@ enum Slot {
     S_GV, S_GV2, S_GH, S_GH2, S_GC, S_GX, S_GD, S_GRES, S_GZ, S_GP, S_GCN, S_GTHETA, S_GWR, S_GWI,
     S_GORD, S_GERES, S_GWORK, S_GY, S_GG, S_GINFO, S_GTMP, S_GB, S_GH1, S_GHV,
     S_FV, S_FH, S_FCS, S_FSN, S_FG, S_FY, S_FSTATE, S_BC,
-    S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC,
+    S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC, S_XBAK,
     S_COUNT
 };
 
@@ -999,6 +999,7 @@ static int solve_bicg64(tg_op *op, int transpose, const tg_defl *df, const T *b,
 }
 
 // float32 inner cycles with float64 refinement (real operators only).
+constexpr int64_t kIrCycleCap = 2000;
 static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const double *b, double *x, const SolveCfg &cfg,
                          tg_stats *st, cudaStream_t s) {
     const DevOp &A = pick(op, TG_FINE, transpose);
@@ -1007,6 +1008,9 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
     TG_CHECK(wsx(op, S_R64, (size_t)n * 8));
     TG_CHECK(wsx(op, S_R32, (size_t)n * 4));
     TG_CHECK(wsx(op, S_E32, (size_t)n * 4));
+    TG_CHECK(wsx(op, S_XBAK, (size_t)n * 8));
+    double *xbak = wsp<double>(op, S_XBAK);
+    int fp64_cycles = 0;
     double *r = wsp<double>(op, S_R64);
     float *r32 = wsp<float>(op, S_R32), *e32 = wsp<float>(op, S_E32);
     double nr, nb;
@@ -1037,16 +1041,38 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
         if (rt < 1e-6) rt = 1e-6;   // a float32 cycle cannot resolve more; refinement continues
         hist_push(st, nrp / nb, rt, mvps);
         int64_t cap64 = cfg.max_mvps - mvps;
-        if (cfg.restart_mvps > 0 && cap64 > cfg.restart_mvps) cap64 = cfg.restart_mvps;
+        // a float32 cycle that stagnates above its target ends after kIrCycleCap products
+        const int64_t cyc_cap = cfg.restart_mvps > 0 ? cfg.restart_mvps : kIrCycleCap;
+        if (cap64 > cyc_cap) cap64 = cyc_cap;
         if (cap64 > INT_MAX / 2) cap64 = INT_MAX / 2;
         CycleOut co;
         TG_CHECK(bicg_cycle<float>(op, A, A32, e32, r32, n, (rt * nrel) * (rt * nrel), (int)cap64, &co, s));
         mvps += co.mvps;
+        // keep x: a float32 correction that does not lower the float64 residual is undone
+        TG_CHECK_CUDA(cudaMemcpyAsync(xbak, x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        const double nr_before = nr;
         TG_PROF(P_CONVERT, 20.0 * n, 2.0 * n, launch_add_f2d_scaled(g, s, x, e32, n, scale));
         TG_LAUNCH_CHECK();
         TG_CHECK(true_residual<double>(op, A, b, x, r, &nr, &nb, s));
-        if (!std::isfinite(nr)) { status = TG_NAN; break; }
-        if (nr <= cfg.rtol * nb) { status = TG_OK; break; }
+        if (std::isfinite(nr) && nr <= cfg.rtol * nb) { status = TG_OK; break; }
+        if (!std::isfinite(nr) || nr >= nr_before || co.status == 4 || co.status == 5) {
+            // float32 cannot resolve this system (its rounding times the condition number is
+            // too large): restore x and finish with float64 cycles on the GPU
+            TG_CHECK_CUDA(cudaMemcpyAsync(x, xbak, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+            SolveCfg c64 = cfg;
+            c64.max_mvps = std::max<int64_t>(1, cfg.max_mvps - mvps);
+            c64.ncyc = 0;
+            if (c64.restart_mvps <= 0) c64.restart_mvps = 1000;
+            tg_stats s64{};
+            s64.history = nullptr;
+            const int rc64 = solve_bicg64<double>(op, transpose, df, b, x, c64, &s64, s);
+            mvps += s64.mvps;
+            cyc += s64.cycles;
+            fp64_cycles = s64.cycles;
+            nr = s64.relres * nb;
+            status = rc64;
+            break;
+        }
         if (mvps >= cfg.max_mvps) break;
         if (co.mvps == 0) { status = TG_BREAKDOWN; break; }
     }
@@ -1056,6 +1082,7 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
         st->relres = nb > 0 ? nr / nb : 0.0;
         st->status = status;
         st->vops = mvps * 7;
+        st->fp64_cycles = fp64_cycles;
     }
     return status;
 }
@@ -1767,7 +1794,7 @@ static int batch_solve_one(tg_batch *b, int i, const double *B, double *X, const
             }
             hp[q] = t2;
         }
-        if (cfg.restart_mvps > 0) cap64 = std::min<int64_t>(cap64, cfg.restart_mvps);
+        cap64 = std::min<int64_t>(cap64, cfg.restart_mvps > 0 ? cfg.restart_mvps : kIrCycleCap);
         cap64 = std::max<int64_t>(1, std::min<int64_t>(cap64, INT_MAX / 2));
         TG_CHECK_CUDA(cudaMemcpyAsync(d_t2, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
         TG_PROF(P_BI_INIT, 12.0 * R * n, 2.0 * R * n,
@@ -1789,6 +1816,14 @@ static int batch_solve_one(tg_batch *b, int i, const double *B, double *X, const
         }
         BiState<double> hs[R];
         TG_CHECK_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        TG_CHECK_CUDA(cudaStreamSynchronize(s));
+        bool reject = false;
+        for (int q = 0; q < R; ++q) {   // a diverged or NaN float32 correction is not added
+            const bool bad = status[q] == TG_NOT_CONVERGED && (hs[q].status == 4 || hs[q].status == 5);
+            hp[q] = (status[q] == TG_NOT_CONVERGED && !bad) ? nr[q] : 0.0;
+            reject |= bad;
+        }
+        if (reject) TG_CHECK_CUDA(cudaMemcpyAsync(d_scale, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
         TG_PROF(P_CONVERT, 12.0 * R * n, 2.0 * R * n,
                 k_mr_add<R><<<grid_for((int64_t)n * R, 8), kThreads, 0, s>>>(X, I.e32.as<float>(), n, d_scale));
         TG_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -1798,7 +1833,7 @@ static int batch_solve_one(tg_batch *b, int i, const double *B, double *X, const
             if (status[q] != TG_NOT_CONVERGED) continue;
             mv[q] += hs[q].mvps;
             if (hs[q].mvps > 0) stuck = false;
-            if (!std::isfinite(nr[q]) || hs[q].status == 4) status[q] = TG_NAN;
+            if (!std::isfinite(nr[q]) || hs[q].status == 4 || hs[q].status == 5) status[q] = TG_NAN;
             else if (nr[q] <= cfg.rtol * nb[q]) status[q] = TG_OK;
             else if (mv[q] >= cfg.max_mvps) status[q] = TG_NOT_CONVERGED + 100;   // out of budget
         }

@@ -120,10 +120,11 @@ struct BiState {
     double rr;      // ||r||^2 (last full step)
     double ss;      // ||s||^2 (last half step)
     double target2; // (rticyc ||r_cycle_start||)^2
+    double div2;    // divergence bound: the cycle stops (status 5) once ||r||^2 exceeds it
     int mvps;       // operator applications in this cycle
     int cap;        // at most this many (INT_MAX: no cap)
     int iters;
-    int status;     // 0 running, 1 converged, 2 breakdown, 3 capped, 4 NaN
+    int status;     // 0 running, 1 converged, 2 breakdown, 3 capped, 4 NaN, 5 diverged
     int half;       // a half-step exit is pending: the t-kernel skips, the x-kernel applies omega = 0
     int pending;    // status to take when the pending half step is applied
 };
@@ -156,6 +157,8 @@ __global__ void __launch_bounds__(kThreads) k_bi_init(const T *__restrict__ r, T
             st->rr = dreal(rho);
             st->ss = 0.0;
             st->target2 = target2;
+            // float32 cycles stop once ||r|| has grown 1e4-fold (divergence); float64 cycles never
+            st->div2 = sizeof(T) == 4 ? 1e8 * dreal(rho) : 1.7e308;
             st->mvps = 0;
             st->cap = cap;
             st->iters = 0;
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_bi_s(const T *__restrict__ r, cons
             st->ss = ss;
             if (!isfinite(ss)) st->status = 4;
             else if (ss <= st->target2) { st->half = 1; st->pending = 1; }
+            else if (ss > st->div2) st->status = 5;
             else if (st->mvps >= st->cap) { st->half = 1; st->pending = 3; }
         }
     }
@@ -328,6 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restr
             st->rho = st->rho_next;
             if (!isfinite(rr)) st->status = 4;
             else if (rr <= st->target2) st->status = 1;
+            else if (rr > st->div2) st->status = 5;
             else if (dabs(st->omega) < kTiny) st->status = 2;
             else if (dabs(st->rho_next) < kTiny) st->status = 2;
             else if (st->mvps >= st->cap) st->status = 3;

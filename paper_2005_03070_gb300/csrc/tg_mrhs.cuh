@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_mr_bi_init(const float *__restrict
             for (int q = 0; q < R; ++q) {
                 BiState<double> &s = st[q];
                 const double rho = tot[q];
-                s.rho = rho; s.rr = rho; s.ss = 0.0; s.target2 = target2[q];
+                s.rho = rho; s.rr = rho; s.ss = 0.0; s.target2 = target2[q]; s.div2 = 1e8 * rho;
                 s.mvps = 0; s.cap = cap; s.iters = 0; s.half = 0; s.pending = 0;
                 s.alpha = s.omega = s.beta = s.rho_next = 1.0;
                 if (target2[q] < 0.0) s.status = 1;            // not in this cycle
@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_mr_bi_s(const float *__restrict__ 
                 b.ss = ss;
                 if (!isfinite(ss)) b.status = 4;
                 else if (ss <= b.target2) { b.half = 1; b.pending = 1; }
+                else if (ss > b.div2) b.status = 5;
                 else if (b.mvps >= b.cap) { b.half = 1; b.pending = 3; }
             }
         }
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_mr_bi_x(float *__restrict__ x, flo
                     b.rho = b.rho_next;
                     if (!isfinite(rr)) b.status = 4;
                     else if (rr <= b.target2) b.status = 1;
+                    else if (rr > b.div2) b.status = 5;
                     else if (fabs(b.omega) < kTiny) b.status = 2;
                     else if (fabs(b.rho_next) < kTiny) b.status = 2;
                     else if (b.mvps >= b.cap) b.status = 3;

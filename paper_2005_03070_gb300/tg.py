@@ -45,10 +45,11 @@ class TgStats(C.Structure):
         ("cycles", C.c_int32), ("status", C.c_int32), ("relres", C.c_double),
         ("coarse_relres", C.c_double), ("kk", C.c_int32), ("eig_converged", C.c_int32),
         ("history", C.POINTER(C.c_double)), ("history_cap", C.c_int32), ("history_len", C.c_int32),
+        ("fp64_cycles", C.c_int32), ("reserved", C.c_int32),
     ]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "history"}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f not in ("history", "reserved")}
 
 
 class TgError(RuntimeError):

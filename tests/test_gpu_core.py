@@ -151,6 +151,31 @@ def test_projection_parity(tg, proj, kind, N, beta):
     assert np.max(np.abs(host(defl.copy(2)).T - AY)) <= 1e-13 * np.max(np.abs(AY))
 
 
+@pytest.mark.parametrize("proj", ["minres", "galerkin"])
+def test_projection_parity_complex(tg, proj):
+    """Complex projection (lattice operator, 6^4 sites): the same bars with conjugate
+    transposes."""
+    top, oop = make_pair(tg, "u1_4d", 6, None, seed=3)
+    k = 10
+    Y = gi.random_dense((oop.n, k), 8) + 1j * gi.random_dense((oop.n, k), 18)
+    defl = top.defl_from_basis(cu(Y.T.copy().reshape(-1)), k, proj=proj)
+    odefl = krylov.make_deflation(oop.apply, Y, proj)
+    b = gi.rhs(oop.n, 9) + 1j * gi.rhs(oop.n, 19)
+    x0 = gi.random_dense(oop.n, 10) + 1j * gi.random_dense(oop.n, 20)
+    r0 = b - oop.apply(x0)
+    xo, ro = krylov.project(odefl, x0, r0)
+    xt, rt = cu(x0), cu(r0)
+    defl.project(xt, rt)
+    xg, rg = host(xt), host(rt)
+    assert rel(xg, xo) <= 1e-11
+    assert rel(rg, ro) <= 1e-11
+    AY = odefl.AY
+    W = AY if proj == "minres" else np.linalg.qr(Y)[0]
+    assert np.max(np.abs(W.conj().T @ rg)) <= 1e-12 * np.linalg.norm(W) * np.linalg.norm(r0)
+    Q = host(defl.copy(1)).T
+    assert np.max(np.abs(Q.conj().T @ Q - np.eye(k))) <= 1e-13
+
+
 def _span_gap(A, B):
     """sin of the largest principal angle between span(A) and span(B) (columns)."""
     Qa = np.linalg.qr(A)[0]
