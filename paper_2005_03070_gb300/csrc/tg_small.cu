@@ -265,19 +265,94 @@ __device__ void hessenberg(T *A, int m, T *Z, T *v) {
     __syncthreads();
 }
 
+// ----------------------------------------------------------------------------- Schur form: shared pieces
+// Cost model of the QR sweeps on this GPU: every float64 warp instruction occupies its SM
+// sub-partition's float64 unit for tens of cycles whatever the number of active lanes, and
+// sqrt / division / hypot are long sequences of them.  So a bulge-chasing step is organised
+// as two phases between two barriers: (1) all warps apply the current transform to the rows
+// it touches (and to part of the Schur vector rows), (2) warp 0 updates the few entries that
+// define the next transform and computes it with one rsqrt (and, real case, one reciprocal),
+// lanes in parallel, while warps 1.. apply the column transform to the remaining rows and
+// Schur vector rows.  Bulge entries that the next transform annihilates are stored as exact
+// zeros, so no clean-up pass is needed.
+constexpr unsigned kFull = 0xffffffffu;
+
+// Complex Givens rotation G = [conj(a) conj(b); -b a] with G [x; y] = [r; 0], r = ||(x, y)||:
+// a = x / r, b = y / r.  Warp-wide call; lanes 0..3 hold x.re, x.im, y.re, y.im in v and
+// write a.re, a.im, b.re, b.im to rs[0..3].  (x, y) = 0 gives the identity.
+__device__ __forceinline__ void givens_warp(double v, double *rs) {
+    const int lane = threadIdx.x & 31;
+    double s2 = v * v;
+    s2 += __shfl_xor_sync(kFull, s2, 1);
+    s2 += __shfl_xor_sync(kFull, s2, 2);
+    s2 = __shfl_sync(kFull, s2, 0);
+    double out;
+    if (s2 == 0.0) {
+        out = lane == 0 ? 1.0 : 0.0;
+    } else if (s2 > 1e-280 && s2 < 1e280) {
+        out = v * rsqrt(s2);
+    } else {
+        // scale by the largest component first (no overflow or underflow in the squares)
+        double mx = fabs(v);
+        mx = fmax(mx, __shfl_xor_sync(kFull, mx, 1));
+        mx = fmax(mx, __shfl_xor_sync(kFull, mx, 2));
+        mx = __shfl_sync(kFull, mx, 0);
+        const double w = v * (1.0 / mx);
+        double t2 = w * w;
+        t2 += __shfl_xor_sync(kFull, t2, 1);
+        t2 += __shfl_xor_sync(kFull, t2, 2);
+        t2 = __shfl_sync(kFull, t2, 0);
+        out = w * rsqrt(t2);
+    }
+    if (lane < 4) rs[lane] = out;
+}
+
+// Householder reflector (I - tau u u^T), u = (1, u1, u2), mapping (x, y, z) to (beta, 0, 0),
+// beta = -sign(x) ||(x, y, z)||: tau = (beta - x) / beta, u_i = (y, z) / (x - beta).
+// Warp-wide call; lanes 0..2 hold x, y, z in v (z = 0 for a 2-vector); writes tau, u1, u2
+// to hs[0..2].  y = z = 0 gives tau = 0 (the identity).
+__device__ __forceinline__ void house3_warp(double v, double *hs) {
+    const int lane = threadIdx.x & 31;
+    const double x = __shfl_sync(kFull, v, 0), y = __shfl_sync(kFull, v, 1), z = __shfl_sync(kFull, v, 2);
+    const double sn = y * y + z * z;
+    if (lane == 0) {
+        double tau = 0.0, u1 = 0.0, u2 = 0.0;
+        if (sn != 0.0) {
+            double n2 = x * x + sn;
+            double xs = x, ys = y, zs = z;
+            if (!(n2 > 1e-280 && n2 < 1e280)) {      // rescale (the reflector is scale invariant)
+                const double mx = fmax(fabs(x), fmax(fabs(y), fabs(z)));
+                const double r = 1.0 / mx;
+                xs = x * r; ys = y * r; zs = z * r;
+                n2 = xs * xs + (ys * ys + zs * zs);
+            }
+            const double inv = rsqrt(n2);                  // 1 / ||(x, y, z)||
+            const double beta = -copysign(n2 * inv, xs);
+            const double u0 = xs - beta;
+            const double ru0 = 1.0 / u0;
+            tau = u0 * copysign(inv, xs);                  // -u0 / beta
+            u1 = ys * ru0;
+            u2 = zs * ru0;
+        }
+        hs[0] = tau;
+        hs[1] = u1;
+        hs[2] = u2;
+    }
+}
+
 // ----------------------------------------------------------------------------- real Schur form
 // Francis double-shift QR on the real upper Hessenberg H (m x m, ld m), accumulating Z.
 // Returns 0 on success, 1 if an eigenvalue failed to converge in 40 m sweeps.
 __device__ int real_schur(double *H, int m, double *Z) {
     __shared__ int hi_s, l_s, status_s, act_s;
-    __shared__ double vv[3], tau3;
+    __shared__ double hs_s[3];
     __shared__ double x_s, y_s, z_s;
-    if (threadIdx.x == 0) { hi_s = m - 1; status_s = 0; }
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) { hi_s = m - 1; status_s = 0; }
     __syncthreads();
     int its = 0, total = 0;
     while (true) {
-        // thread 0 finds the active block and decides what to do
-        if (threadIdx.x < 32) {
+        if (tid < 32) {
             // the active block: the largest l <= hi with a negligible H[l, l-1] (0 if none),
             // found by warp 0 with a ballot over the candidates
             const int hi = hi_s;
@@ -285,27 +360,27 @@ __device__ int real_schur(double *H, int m, double *Z) {
             int l = 0;
             if (hi > 0) {
                 for (int base = hi; base > 0 && l == 0; base -= 32) {
-                    const int cand = base - (int)threadIdx.x;
+                    const int cand = base - lane;
                     bool neg = false;
                     if (cand > 0) {
                         double s = fabs(H[(cand - 1) + (size_t)(cand - 1) * m]) + fabs(H[cand + (size_t)cand * m]);
                         if (s == 0.0) s = 1.0;
                         neg = fabs(H[cand + (size_t)(cand - 1) * m]) <= kEps * s;
                     }
-                    const unsigned bal = __ballot_sync(0xffffffffu, neg);
+                    const unsigned bal = __ballot_sync(kFull, neg);
                     if (bal) l = base - (__ffs(bal) - 1);     // lowest lane = largest index
                 }
             }
-            if (threadIdx.x == 0 && l > 0) H[l + (size_t)(l - 1) * m] = 0.0;
-            if (threadIdx.x == 0) {
-            act_s = 0;
-            if (hi < 0) act_s = -1;
-            else {
-                l_s = l;
-                if (l == hi) { hi_s = hi - 1; act_s = 1; }
-                else if (l == hi - 1) { act_s = 2; }   // 2x2 block: standardise below
-                else act_s = 3;                         // QR sweep on l..hi
-            }
+            if (lane == 0) {
+                if (l > 0) H[l + (size_t)(l - 1) * m] = 0.0;
+                act_s = 0;
+                if (hi < 0) act_s = -1;
+                else {
+                    l_s = l;
+                    if (l == hi) { hi_s = hi - 1; act_s = 1; }
+                    else if (l == hi - 1) { act_s = 2; }   // 2x2 block: standardise below
+                    else act_s = 3;                         // QR sweep on l..hi
+                }
             }
         }
         __syncthreads();
@@ -317,7 +392,7 @@ __device__ int real_schur(double *H, int m, double *Z) {
             // 2x2 block [a b; c d] at (hi-1, hi): real eigenvalues -> rotate to triangular form
             __shared__ double cs_s, sn_s;
             __shared__ int rot_s;
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 double a = H[(hi - 1) + (size_t)(hi - 1) * m], b = H[(hi - 1) + (size_t)hi * m];
                 double c = H[hi + (size_t)(hi - 1) * m], d = H[hi + (size_t)hi * m];
                 double p = 0.5 * (a - d);
@@ -340,14 +415,14 @@ __device__ int real_schur(double *H, int m, double *Z) {
             if (rot_s) {
                 const double cs = cs_s, sn = sn_s;
                 // rows hi-1, hi: H <- G^T H for columns hi-1..m-1
-                for (int c = hi - 1 + threadIdx.x; c < m; c += blockDim.x) {
+                for (int c = hi - 1 + tid; c < m; c += nt) {
                     double h1 = H[(hi - 1) + (size_t)c * m], h2 = H[hi + (size_t)c * m];
                     H[(hi - 1) + (size_t)c * m] = cs * h1 + sn * h2;
                     H[hi + (size_t)c * m] = -sn * h1 + cs * h2;
                 }
                 __syncthreads();
                 // columns hi-1, hi: H <- H G for rows 0..hi, Z <- Z G
-                for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
+                for (int rr = tid; rr < 2 * m; rr += nt) {
                     double *M = rr < m ? H : Z;
                     const int r = rr < m ? rr : rr - m;
                     if (M == H && r > hi) continue;
@@ -356,9 +431,9 @@ __device__ int real_schur(double *H, int m, double *Z) {
                     M[r + (size_t)hi * m] = -sn * h1 + cs * h2;
                 }
                 __syncthreads();
-                if (threadIdx.x == 0) H[hi + (size_t)(hi - 1) * m] = 0.0;
+                if (tid == 0) H[hi + (size_t)(hi - 1) * m] = 0.0;
             }
-            if (threadIdx.x == 0) hi_s = hi - 2;
+            if (tid == 0) hi_s = hi - 2;
             __syncthreads();
             its = 0;
             continue;
@@ -367,11 +442,11 @@ __device__ int real_schur(double *H, int m, double *Z) {
         ++its;
         ++total;
         if (total > 40 * m) {
-            if (threadIdx.x == 0) status_s = 1;
+            if (tid == 0) status_s = 1;
             __syncthreads();
             break;
         }
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             double s, t;
             if (its % 10 == 0) {
                 // exceptional shift
@@ -384,6 +459,7 @@ __device__ int real_schur(double *H, int m, double *Z) {
                 s = a + d;
                 t = a * d - b * c;
             }
+            // first column of (H - s1 I)(H - s2 I) = H^2 - s H + t I
             double h00 = H[l + (size_t)l * m], h01 = H[l + (size_t)(l + 1) * m];
             double h10 = H[(l + 1) + (size_t)l * m], h11 = H[(l + 1) + (size_t)(l + 1) * m];
             x_s = h00 * h00 + h01 * h10 - s * h00 + t;
@@ -391,100 +467,106 @@ __device__ int real_schur(double *H, int m, double *Z) {
             z_s = (l + 2 <= hi) ? h10 * H[(l + 2) + (size_t)(l + 1) * m] : 0.0;
         }
         __syncthreads();
+        if (warp == 0) house3_warp(lane == 0 ? x_s : lane == 1 ? y_s : lane == 2 ? z_s : 0.0, hs_s);
+        __syncthreads();
         for (int kk = l; kk <= hi - 1; ++kk) {
             const int nr = (kk <= hi - 2) ? 3 : 2;
-            if (threadIdx.x == 0) {
-                // 3 x 3 (or 2 x 2) reflector: beta = -sign(x) ||(x,y,z)||, v = (1, y/v0, z/v0),
-                // tau = -v0/beta with v0 = x - beta; one division: r = 1/(v0 beta)
-                const double x0 = x_s, y0 = y_s, z0 = nr == 3 ? z_s : 0.0;
-                const double sn = y0 * y0 + z0 * z0;
-                if (sn == 0.0) {
-                    tau3 = 0.0;
-                } else {
-                    const double beta = -copysign(sqrt(x0 * x0 + sn), x0);
-                    const double v0 = x0 - beta;
-                    const double r = 1.0 / (v0 * beta);
-                    vv[0] = 1.0;
-                    vv[1] = y0 * beta * r;
-                    vv[2] = z0 * beta * r;
-                    tau3 = -v0 * v0 * r;
-                }
-            }
-            __syncthreads();
-            const double tau = tau3;
-            if (tau != 0.0) {
-                const double v1 = vv[1], v2 = vv[2];
-                // rows kk..kk+nr-1, columns max(l, kk-1)..m-1
-                const int c0 = kk > l ? kk - 1 : l;
-                for (int c = c0 + threadIdx.x; c < m; c += blockDim.x) {
-                    double h0 = H[kk + (size_t)c * m], h1 = H[kk + 1 + (size_t)c * m];
-                    double h2 = nr == 3 ? H[kk + 2 + (size_t)c * m] : 0.0;
-                    double s = tau * (h0 + v1 * h1 + v2 * h2);
+            const double tau = hs_s[0], v1 = hs_s[1], v2 = nr == 3 ? hs_s[2] : 0.0;
+            // phase 1: rows kk..kk+nr-1 over columns c0..m-1; Schur vector rows [0, zs)
+            const int c0 = kk > l ? kk - 1 : l;
+            const int ncol = m - c0;
+            const int zs = min(m, max(0, nt - ncol));
+            for (int t = tid; t < ncol + zs; t += nt) {
+                if (t < ncol) {
+                    const int c = c0 + t;
+                    const double h0 = H[kk + (size_t)c * m], h1 = H[kk + 1 + (size_t)c * m];
+                    const double h2 = nr == 3 ? H[kk + 2 + (size_t)c * m] : 0.0;
+                    const double s = tau * fma(v2, h2, fma(v1, h1, h0));
+                    const bool bulge = kk > l && c == kk - 1;     // entries the reflector annihilates
                     H[kk + (size_t)c * m] = h0 - s;
-                    H[kk + 1 + (size_t)c * m] = h1 - s * v1;
-                    if (nr == 3) H[kk + 2 + (size_t)c * m] = h2 - s * v2;
+                    H[kk + 1 + (size_t)c * m] = bulge ? 0.0 : fma(-s, v1, h1);
+                    if (nr == 3) H[kk + 2 + (size_t)c * m] = bulge ? 0.0 : fma(-s, v2, h2);
+                } else {
+                    double *zr = Z + (t - ncol);
+                    const double h0 = zr[(size_t)kk * m], h1 = zr[(size_t)(kk + 1) * m];
+                    const double h2 = nr == 3 ? zr[(size_t)(kk + 2) * m] : 0.0;
+                    const double s = tau * fma(v2, h2, fma(v1, h1, h0));
+                    zr[(size_t)kk * m] = h0 - s;
+                    zr[(size_t)(kk + 1) * m] = fma(-s, v1, h1);
+                    if (nr == 3) zr[(size_t)(kk + 2) * m] = fma(-s, v2, h2);
                 }
-                __syncthreads();
-                // columns kk..kk+nr-1: rows 0..min(kk+3, hi) of H, all rows of Z
-                const int rmax = (kk + 3 < hi) ? kk + 3 : hi;
-                for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
-                    double *M = rr < m ? H : Z;
-                    const int r = rr < m ? rr : rr - m;
-                    if (M == H && r > rmax) continue;
-                    double h0 = M[r + (size_t)kk * m], h1 = M[r + (size_t)(kk + 1) * m];
-                    double h2 = nr == 3 ? M[r + (size_t)(kk + 2) * m] : 0.0;
-                    double s = tau * (h0 + h1 * v1 + h2 * v2);
-                    M[r + (size_t)kk * m] = h0 - s;
-                    M[r + (size_t)(kk + 1) * m] = h1 - s * v1;
-                    if (nr == 3) M[r + (size_t)(kk + 2) * m] = h2 - s * v2;
-                }
-                __syncthreads();
             }
-            if (threadIdx.x == 0 && kk < hi - 1) {
-                x_s = H[(kk + 1) + (size_t)kk * m];
-                y_s = H[(kk + 2) + (size_t)kk * m];
-                z_s = (kk + 3 <= hi) ? H[(kk + 3) + (size_t)kk * m] : 0.0;
+            __syncthreads();
+            // phase 2: columns kk..kk+nr-1 of rows 0..rmax and of Schur vector rows [zs, m)
+            const int rmax = (kk + 3 < hi) ? kk + 3 : hi;
+            if (warp == 0) {
+                // rows kk+1..rmax (at most 3, one per lane), then the next reflector from
+                // column kk of those rows
+                const int r = kk + 1 + lane;
+                double xv = 0.0;
+                if (lane < 3 && r <= rmax) {
+                    double *hr = H + r;
+                    const double h0 = hr[(size_t)kk * m], h1 = hr[(size_t)(kk + 1) * m];
+                    const double h2 = nr == 3 ? hr[(size_t)(kk + 2) * m] : 0.0;
+                    const double s = tau * fma(v2, h2, fma(v1, h1, h0));
+                    xv = h0 - s;
+                    hr[(size_t)kk * m] = xv;
+                    hr[(size_t)(kk + 1) * m] = fma(-s, v1, h1);
+                    if (nr == 3) hr[(size_t)(kk + 2) * m] = fma(-s, v2, h2);
+                }
+                __syncwarp();
+                if (kk < hi - 1) house3_warp(xv, hs_s);      // z = 0 when kk + 3 > hi
+            } else {
+                const int nh = kk + 1;            // rows 0..kk
+                const int nz = m - zs;
+                for (int t = tid - 32; t < nh + nz; t += nt - 32) {
+                    double *hr = t < nh ? H + t : Z + zs + (t - nh);
+                    const double h0 = hr[(size_t)kk * m], h1 = hr[(size_t)(kk + 1) * m];
+                    const double h2 = nr == 3 ? hr[(size_t)(kk + 2) * m] : 0.0;
+                    const double s = tau * fma(v2, h2, fma(v1, h1, h0));
+                    hr[(size_t)kk * m] = h0 - s;
+                    hr[(size_t)(kk + 1) * m] = fma(-s, v1, h1);
+                    if (nr == 3) hr[(size_t)(kk + 2) * m] = fma(-s, v2, h2);
+                }
             }
             __syncthreads();
         }
-        // zero the entries below the subdiagonal created by rounding
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = e % m, j = e / m;
-            if (i > j + 1) H[e] = 0.0;
-        }
-        __syncthreads();
     }
     return status_s;
 }
 
 // ----------------------------------------------------------------------------- complex Schur form
-// Wilkinson single-shift QR on the complex upper Hessenberg H, accumulating Z.
+// Wilkinson single-shift QR on the complex upper Hessenberg H, accumulating Z.  The
+// negligibility test uses |re| + |im| (no square roots).
+__device__ __forceinline__ double cabs1(cplx a) { return fabs(a.re) + fabs(a.im); }
+
 __device__ int complex_schur(cplx *H, int m, cplx *Z) {
     __shared__ int hi_s, l_s, act_s, status_s;
-    __shared__ double gc_s;
-    __shared__ cplx gs_s, x_s, y_s;
-    if (threadIdx.x == 0) { hi_s = m - 1; status_s = 0; }
+    __shared__ double rs_s[4];      // a.re, a.im, b.re, b.im of the current rotation
+    __shared__ cplx x_s, y_s;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) { hi_s = m - 1; status_s = 0; }
     __syncthreads();
     int its = 0, total = 0;
     while (true) {
-        if (threadIdx.x < 32) {
+        if (tid < 32) {
             const int hi = hi_s;
             __syncwarp();          // every lane has read hi_s before lane 0 may update it
             int l = 0;
             if (hi > 0) {
                 for (int base = hi; base > 0 && l == 0; base -= 32) {
-                    const int cand = base - (int)threadIdx.x;
+                    const int cand = base - lane;
                     bool neg = false;
                     if (cand > 0) {
-                        double s = cabs_(H[(cand - 1) + (size_t)(cand - 1) * m]) + cabs_(H[cand + (size_t)cand * m]);
+                        double s = cabs1(H[(cand - 1) + (size_t)(cand - 1) * m]) + cabs1(H[cand + (size_t)cand * m]);
                         if (s == 0.0) s = 1.0;
-                        neg = cabs_(H[cand + (size_t)(cand - 1) * m]) <= kEps * s;
+                        neg = cabs1(H[cand + (size_t)(cand - 1) * m]) <= kEps * s;
                     }
-                    const unsigned bal = __ballot_sync(0xffffffffu, neg);
+                    const unsigned bal = __ballot_sync(kFull, neg);
                     if (bal) l = base - (__ffs(bal) - 1);
                 }
             }
-            if (threadIdx.x == 0) {
+            if (lane == 0) {
                 if (l > 0) H[l + (size_t)(l - 1) * m] = {0.0, 0.0};
                 act_s = 0;
                 if (hi <= 0) act_s = -1;
@@ -502,12 +584,12 @@ __device__ int complex_schur(cplx *H, int m, cplx *Z) {
         ++its;
         ++total;
         if (total > 40 * m) {
-            if (threadIdx.x == 0) status_s = 1;
+            if (tid == 0) status_s = 1;
             __syncthreads();
             break;
         }
         const int hi = hi_s, l = l_s;
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             cplx a = H[(hi - 1) + (size_t)(hi - 1) * m], b = H[(hi - 1) + (size_t)hi * m];
             cplx c = H[hi + (size_t)(hi - 1) * m], d = H[hi + (size_t)hi * m];
             cplx mu;
@@ -530,51 +612,61 @@ __device__ int complex_schur(cplx *H, int m, cplx *Z) {
             y_s = H[(l + 1) + (size_t)l * m];
         }
         __syncthreads();
+        if (warp == 0) givens_warp(lane == 0 ? x_s.re : lane == 1 ? x_s.im : lane == 2 ? y_s.re : y_s.im, rs_s);
+        __syncthreads();
         for (int kk = l; kk <= hi - 1; ++kk) {
-            if (threadIdx.x == 0) {
-                cplx x = x_s, y = y_s;
-                double nx = cabs_(x), ny = cabs_(y);
-                double nr = hypot(nx, ny);
-                if (nr == 0.0) { gc_s = 1.0; gs_s = {0.0, 0.0}; }
-                else if (nx == 0.0) { gc_s = 0.0; gs_s = conj(y) * (1.0 / ny); }
-                else {
-                    // G = [c s; -conj(s) c], G [x; y] = [r; 0]: c = |x|/nr, s = (x/|x|) conj(y)/nr
-                    gc_s = nx / nr;
-                    gs_s = (x * (1.0 / nx)) * conj(y) * (1.0 / nr);
+            const cplx a = mkc(rs_s[0], rs_s[1]), b = mkc(rs_s[2], rs_s[3]);
+            // phase 1: rows kk, kk+1 over columns c0..m-1 (H <- G H); Schur vector rows [0, zs)
+            const int c0 = kk > l ? kk - 1 : l;
+            const int ncol = m - c0;
+            const int zs = min(m, max(0, nt - ncol));
+            for (int t = tid; t < ncol + zs; t += nt) {
+                if (t < ncol) {
+                    const int c = c0 + t;
+                    const cplx h1 = H[kk + (size_t)c * m], h2 = H[kk + 1 + (size_t)c * m];
+                    H[kk + (size_t)c * m] = conj(a) * h1 + conj(b) * h2;
+                    // the entry the rotation annihilates (the bulge) is stored as an exact zero
+                    H[kk + 1 + (size_t)c * m] = (kk > l && c == kk - 1) ? mkc(0.0, 0.0) : a * h2 - b * h1;
+                } else {
+                    cplx *zr = Z + (t - ncol);
+                    const cplx h1 = zr[(size_t)kk * m], h2 = zr[(size_t)(kk + 1) * m];
+                    zr[(size_t)kk * m] = h1 * a + h2 * b;
+                    zr[(size_t)(kk + 1) * m] = h2 * conj(a) - h1 * conj(b);
                 }
             }
             __syncthreads();
-            const double gc = gc_s;
-            const cplx gs = gs_s;
-            const int c0 = kk > l ? kk - 1 : l;
-            for (int c = c0 + threadIdx.x; c < m; c += blockDim.x) {
-                cplx h1 = H[kk + (size_t)c * m], h2 = H[kk + 1 + (size_t)c * m];
-                H[kk + (size_t)c * m] = gc * h1 + gs * h2;
-                H[kk + 1 + (size_t)c * m] = gc * h2 - conj(gs) * h1;
-            }
-            __syncthreads();
+            // phase 2: columns kk, kk+1 (M <- M G^H) of rows 0..rmax and Schur vector rows [zs, m)
             const int rmax = (kk + 2 < hi) ? kk + 2 : hi;
-            for (int rr = threadIdx.x; rr < 2 * m; rr += blockDim.x) {
-                cplx *M = rr < m ? H : Z;
-                const int r = rr < m ? rr : rr - m;
-                if (M == H && r > rmax) continue;
-                // M <- M G^H: columns kk, kk+1
-                cplx h1 = M[r + (size_t)kk * m], h2 = M[r + (size_t)(kk + 1) * m];
-                M[r + (size_t)kk * m] = gc * h1 + conj(gs) * h2;
-                M[r + (size_t)(kk + 1) * m] = gc * h2 - gs * h1;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0 && kk < hi - 1) {
-                x_s = H[(kk + 1) + (size_t)kk * m];
-                y_s = H[(kk + 2) + (size_t)kk * m];
+            if (warp == 0) {
+                // rows kk+1..rmax: lane q < 8 computes one real part: column kk + (q >> 2),
+                // row kk + 1 + ((q >> 1) & 1), real (q even) or imaginary part; then the next
+                // rotation from column kk of rows kk+1, kk+2 (lanes 0..3)
+                const int q = lane & 7;
+                const int r = kk + 1 + ((q >> 1) & 1);
+                const int col = kk + (q >> 2);
+                const bool live = lane < 8 && r <= rmax;
+                double val = 0.0;
+                if (live) {
+                    const cplx h1 = H[r + (size_t)kk * m], h2 = H[r + (size_t)(kk + 1) * m];
+                    const cplx o = (q >> 2) == 0 ? h1 * a + h2 * b : h2 * conj(a) - h1 * conj(b);
+                    val = (q & 1) ? o.im : o.re;
+                }
+                __syncwarp();
+                if (live) reinterpret_cast<double *>(H + r + (size_t)col * m)[q & 1] = val;
+                __syncwarp();
+                if (kk < hi - 1) givens_warp(val, rs_s);
+            } else {
+                const int nh = kk + 1;            // rows 0..kk
+                const int nz = m - zs;
+                for (int t = tid - 32; t < nh + nz; t += nt - 32) {
+                    cplx *hr = t < nh ? H + t : Z + zs + (t - nh);
+                    const cplx h1 = hr[(size_t)kk * m], h2 = hr[(size_t)(kk + 1) * m];
+                    hr[(size_t)kk * m] = h1 * a + h2 * b;
+                    hr[(size_t)(kk + 1) * m] = h2 * conj(a) - h1 * conj(b);
+                }
             }
             __syncthreads();
         }
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-            int i = e % m, j = e / m;
-            if (i > j + 1) H[e] = {0.0, 0.0};
-        }
-        __syncthreads();
     }
     return status_s;
 }
@@ -791,7 +883,7 @@ __global__ void k_small_gemv(const D *M, int k, const D *c, D *out) {
 // ----------------------------------------------------------------------------- GMRES-DR restart
 // See tg_small.cuh for the argument layout.
 template <class T>
-__global__ void __launch_bounds__(kSmallThreads) k_gmresdr_restart(GdrArgs<T> a) {
+__global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
     const int m = a.m;
     const int rows = m + 1;
     const int ldh = a.ldh;
