@@ -173,7 +173,7 @@ int tg_project(const tg_op *op, const tg_defl *defl, void *x, void *r, void *str
  * whose correction does not lower the float64 residual (float32 rounding times the
  * condition number near 1) is undone and the solve finishes in float64 cycles
  * (stats.fp64_cycles counts them).  A BiCGStab cycle also stops when its residual
- * has grown 1e4-fold (divergence).
+ * has grown 1e8-fold (divergence).
  * b, x: device, n x nrhs column-major (x: in x0, out solution).  Each right-hand side
  * is solved in turn; stats (host, may be NULL) must hold nrhs entries.
  * Returns TG_OK if every right-hand side converged, else the first failure status.

@@ -211,6 +211,19 @@ struct Level {
     DevOp32 A32, AT32;
 };
 
+namespace tg {
+// One captured coarse GMRES-DR cycle (Arnoldi extension from column j0 to m, the restart
+// kernel and the x_c update), valid while the workspace generation is unchanged.
+struct GdrGraph {
+    const void *V = nullptr, *H = nullptr;
+    int j0 = -1, m = 0, k = 0, nev = 0, transpose = 0;
+    double rtolev = 0;
+    unsigned gen = 0;
+    cudaGraphExec_t exec = nullptr;
+    long long nkern = 0;
+};
+}  // namespace tg
+
 struct tg_op {
     int kind = 0;
     int dim = 2;
@@ -224,6 +237,18 @@ struct tg_op {
     DBuf links, pw, cst;
     DBuf ws[S_COUNT];
     PinBuf pin;
+    unsigned ws_gen = 0;                 // bumped whenever a workspace buffer is (re)allocated
+    std::vector<tg::GdrGraph> graphs;    // captured coarse GMRES-DR cycles
+    cudaStream_t cap_stream = nullptr;   // private stream for captures (the caller's may be
+                                         // the legacy stream, which cannot be captured)
+    tg_op() = default;
+    tg_op(const tg_op &) = delete;
+    tg_op &operator=(const tg_op &) = delete;
+    ~tg_op() {
+        for (auto &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 struct tg_defl {
@@ -242,7 +267,12 @@ namespace tg {
 static int elem_size(const tg_op *op) { return op->cplx_ ? 16 : 8; }
 
 template <class U> static U *wsp(tg_op *op, Slot s) { return op->ws[s].as<U>(); }
-static int wsx(tg_op *op, Slot s, size_t bytes) { return op->ws[s].ensure(bytes); }
+static int wsx(tg_op *op, Slot s, size_t bytes) {
+    const void *p0 = op->ws[s].p;
+    const int rc = op->ws[s].ensure(bytes);
+    if (op->ws[s].p != p0) ++op->ws_gen;
+    return rc;
+}
 
 // reduction scratch: partials (sized generously), a ticket, a small result area
 // The ticket is zeroed on the stream that will use it (a plain cudaMemset runs on the
@@ -319,7 +349,7 @@ static int set_smem(const void *fn, size_t bytes) {
             set_error("a launch needs %zu bytes of shared memory, more than the %d available", bytes, mx);
             return TG_BAD_ARG;
         }
-        TG_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        TG_CHECK_CUDA(smem_attr_once(fn, mx));
     }
     return TG_OK;
 }
@@ -351,7 +381,7 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
                               cudaStream_t s, bool *used_pipe) {
     if (pipe_ok<T>(V, ldv, w, n, ncol)) {
         const size_t smem = (size_t)kPipeStages * (ncol + 1) * kPipeRows * sizeof(double);
-        cudaFuncSetAttribute((const void *)k_gemv_t_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem());
+        smem_attr_once((const void *)k_gemv_t_pipe, max_dyn_smem());
         const int per_sm = smem <= 100 * 1024 ? 2 : 1;
         const int nchunks = (n + kPipeRows - 1) / kPipeRows;
         const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
@@ -1267,6 +1297,95 @@ extern "C" int tg_solve_proj(tg_op *op, const tg_defl *defl, int method, int pre
 // ============================================================================= GMRES-DR
 namespace tg {
 
+// One GMRES-DR cycle after the restart recombination: Arnoldi from column j0 to m, the
+// restart kernel (least squares, harmonic Ritz pairs, P_{k+1}, Hnew, cnew) and x_c += V_m d.
+// With per-launch profiling off, the cycle is captured once as a CUDA graph per (basis
+// buffer, Hessenberg buffer, j0) and replayed: about 10 (m - j0) launches become one.
+template <class T>
+static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int nc, int j0, int m, T *H,
+                     int ldh, T *H2, const GdrArgs<T> &a, T *xc, int transpose, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    const cudaStream_t s_caller = s;
+    // the cycle's launches, queued on stream s (the caller's, or the capture stream)
+    auto body = [&](cudaStream_t s) -> int {
+        for (int j = j0; j < m; ++j) TG_CHECK(arnoldi_step<T>(op, A, A32, V, ldv, nc, j, H, ldh, s));
+        TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * sizeof(T), s));
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
+        TG_LAUNCH_CHECK();
+        // x_c += V_m d
+        TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc,
+                k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, ldv, m, a.d, 1.0, xc, nc));
+        TG_LAUNCH_CHECK();
+        return TG_OK;
+    };
+    if (g_prof.on) return body(s_caller);
+    // the reduction scratch the Arnoldi steps use, at its largest, before any capture: a
+    // capture may not allocate
+    const int gb = (int)std::min<int64_t>((nc + 127) / 128, (int64_t)num_sms() * 8);
+    TG_CHECK(red_ready(op, (size_t)std::max(gb, 1) * (m + 2) * sizeof(D), s));
+    // entries of older workspace generations refer to freed buffers: drop them
+    for (auto &g : op->graphs)
+        if (g.gen != op->ws_gen && g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    op->graphs.erase(std::remove_if(op->graphs.begin(), op->graphs.end(),
+                                    [op](const GdrGraph &g) { return g.gen != op->ws_gen; }),
+                     op->graphs.end());
+    GdrGraph *hit = nullptr;
+    for (auto &g : op->graphs)
+        if (g.V == V && g.H == H && g.j0 == j0 && g.m == m && g.k == a.k && g.nev == a.nev && g.rtolev == a.rtolev &&
+            g.transpose == transpose) {
+            hit = &g;
+            break;
+        }
+    if (!hit) {
+        // first use of this cycle shape: run it directly (this also makes every one-time
+        // driver call, such as shared memory limits, outside any capture); capture on reuse
+        GdrGraph ent;
+        ent.V = V; ent.H = H; ent.j0 = j0; ent.m = m; ent.k = a.k; ent.nev = a.nev; ent.rtolev = a.rtolev;
+        ent.transpose = transpose; ent.gen = op->ws_gen;
+        op->graphs.push_back(ent);
+        return body(s_caller);
+    }
+    if (!hit->exec) {
+        if (!op->cap_stream) TG_CHECK_CUDA(cudaStreamCreateWithFlags(&op->cap_stream, cudaStreamNonBlocking));
+        const unsigned gen0 = op->ws_gen;
+        cudaGraph_t graph = nullptr;
+        TG_CHECK_CUDA(cudaStreamBeginCapture(op->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = body(op->cap_stream);
+        const cudaError_t e = cudaStreamEndCapture(op->cap_stream, &graph);
+        if (rc != TG_OK || e != cudaSuccess || op->ws_gen != gen0) {
+            if (graph) cudaGraphDestroy(graph);
+            if (rc != TG_OK) return rc;
+            if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+            set_error("a workspace buffer was reallocated during a graph capture");
+            return TG_BAD_ARG;
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        long long nkern = 0;
+        if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+            for (size_t q = 0; q < nn; ++q) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++nkern;
+            }
+        const cudaError_t ei = cudaGraphInstantiate(&hit->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            hit->exec = nullptr;
+            return cuda_status(ei, "cudaGraphInstantiate");
+        }
+        hit->nkern = nkern;
+        // the capture counted launches that did not run; the replays count them
+        __atomic_sub_fetch(&g_prof.launches, nkern, __ATOMIC_RELAXED);
+    }
+    TG_CHECK_CUDA(cudaGraphLaunch(hit->exec, s_caller));
+    __atomic_add_fetch(&g_prof.launches, hit->nkern, __ATOMIC_RELAXED);
+    return TG_OK;
+}
+
 template <class T>
 static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int k, int nev, double rtolev,
                         double rtol, int max_cycles, void *xc_out, tg_defl **defl_out, int proj, int precision,
@@ -1330,9 +1449,6 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     bool converged = false;
     while (true) {
         ++cycles;
-        for (int j = j0; j < m; ++j) TG_CHECK(arnoldi_step<T>(op, A, A32, V, ldv, nc, j, H, ldh, s));
-        cmvps += m - j0;
-        TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * es, s));
         GdrArgs<T> a;
         a.H = H; a.ldh = ldh; a.c = c; a.m = m; a.k = k; a.nev = nev; a.rtolev = rtolev;
         a.d = wsp<T>(op, S_GD); a.res = wsp<T>(op, S_GRES); a.z = wsp<T>(op, S_GZ);
@@ -1340,11 +1456,8 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         a.order = wsp<int>(op, S_GORD); a.eres = wsp<double>(op, S_GERES); a.P = wsp<T>(op, S_GP);
         a.Hnew = H2; a.cnew = wsp<T>(op, S_GCN); a.work = wsp<T>(op, S_GWORK);
         a.ywork = wsp<cplx>(op, S_GY); a.gwork = wsp<cplx>(op, S_GG); a.info = wsp<GdrInfo>(op, S_GINFO);
-        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
-        TG_LAUNCH_CHECK();
-        // x_c += V_m d
-        TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, ldv, m, a.d, 1.0, xc, nc));
-        TG_LAUNCH_CHECK();
+        TG_CHECK(gdr_cycle<T>(op, A, A32, V, ldv, nc, j0, m, H, ldh, H2, a, xc, transpose, s));
+        cmvps += m - j0;
         TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
         memcpy(&info, op->pin.p, sizeof(info));
         if (g_prof.on)

@@ -3,10 +3,30 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 #include "tg.h"
 
 namespace tg {
+
+// Raise a kernel's dynamic shared memory limit to `bytes` once per (kernel, device).  The
+// value for a given kernel is always the same, so concurrent callers cannot lower it under
+// each other, and later calls make no driver call (safe inside a stream capture).
+inline cudaError_t smem_attr_once(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first == fn && d.second == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.emplace_back(fn, dev);
+    return e;
+}
 
 // ----------------------------------------------------------------------------- status
 void set_error(const char *fmt, ...);

@@ -157,8 +157,9 @@ __global__ void __launch_bounds__(kThreads) k_bi_init(const T *__restrict__ r, T
             st->rr = dreal(rho);
             st->ss = 0.0;
             st->target2 = target2;
-            // float32 cycles stop once ||r|| has grown 1e4-fold (divergence); float64 cycles never
-            st->div2 = sizeof(T) == 4 ? 1e8 * dreal(rho) : 1.7e308;
+            // float32 cycles stop once ||r|| has grown 1e8-fold (divergence on its way to
+            // overflow; transient BiCGStab peaks stay far below that); float64 cycles never
+            st->div2 = sizeof(T) == 4 ? 1e16 * dreal(rho) : 1.7e308;
             st->mvps = 0;
             st->cap = cap;
             st->iters = 0;

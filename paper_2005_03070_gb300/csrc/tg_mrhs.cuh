@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_mr_bi_init(const float *__restrict
             for (int q = 0; q < R; ++q) {
                 BiState<double> &s = st[q];
                 const double rho = tot[q];
-                s.rho = rho; s.rr = rho; s.ss = 0.0; s.target2 = target2[q]; s.div2 = 1e8 * rho;
+                s.rho = rho; s.rr = rho; s.ss = 0.0; s.target2 = target2[q]; s.div2 = 1e16 * rho;   // 1e8-fold growth
                 s.mvps = 0; s.cap = cap; s.iters = 0; s.half = 0; s.pending = 0;
                 s.alpha = s.omega = s.beta = s.rho_next = 1.0;
                 if (target2[q] < 0.0) s.status = 1;            // not in this cycle

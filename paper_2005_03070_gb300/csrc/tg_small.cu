@@ -102,16 +102,24 @@ __device__ T house_par(const T *x, int len, T *v, T *beta_out) {
             beta_sh = x0;
             inv_sh = Cx<T>::zero();
         } else {
-            double a0 = sqrt(Cx<T>::ab2(x0));
-            double alpha = sqrt(Cx<T>::ab2(x0) + nrm2);
-            T ph = a0 > 0 ? Cx<T>::sc(1.0 / a0, x0) : Cx<T>::one();
-            T beta = Cx<T>::sc(-alpha, ph);
-            T v0 = subt(x0, beta);
-            T iv0 = Cx<T>::div(Cx<T>::one(), v0);
-            beta_sh = beta;
-            inv_sh = iv0;
-            // tau = (beta - x0) / beta = -v0 / beta
-            tau_sh = Cx<T>::div(Cx<T>::sc(-1.0, v0), beta);
+            // beta = -phase(x0) alpha, alpha = ||x||; v0 = x0 - beta = phase(x0) (|x0| + alpha);
+            // tau = -v0 / beta = (|x0| + alpha) / alpha; 1 / v0 = conj(phase) / (|x0| + alpha).
+            // One rsqrt per square root and one reciprocal (long float64 sequences on this GPU).
+            const double ax2 = Cx<T>::ab2(x0);
+            const double n2 = ax2 + nrm2;
+            const double ia = rsqrt(n2);                      // 1 / alpha
+            const double alpha = n2 * ia;
+            double a0 = 0.0;
+            T ph = Cx<T>::one();
+            if (ax2 > 0.0) {
+                const double ia0 = rsqrt(ax2);
+                a0 = ax2 * ia0;
+                ph = Cx<T>::sc(ia0, x0);
+            }
+            const double s = a0 + alpha;
+            beta_sh = Cx<T>::sc(-alpha, ph);
+            inv_sh = Cx<T>::sc(1.0 / s, Cx<T>::cj(ph));
+            tau_sh = Cx<T>::sc(s * ia, Cx<T>::one());
         }
     }
     __syncthreads();
@@ -130,8 +138,28 @@ __device__ T house_par(const T *x, int len, T *v, T *beta_out) {
 // d = R^{-1} (Q^H c)[0..m-1].  All threads participate.
 template <class T>
 __device__ void lsq_solve(T *W, int ldw, int rows, int m, T *rhs, T *d, T *v) {
+    // last row that can be nonzero in column j once columns 0..j-1 are reduced: the running
+    // maximum of each column's last nonzero row (a Hessenberg column j ends at j + 1; the
+    // full leading block left by a GMRES-DR restart ends at k); the reflector of column j
+    // only needs rows j..end_j, which keeps the factorisation exact.
+    __shared__ int end_s[kMaxM + 1];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        int e = 0;
+        for (int i = rows - 1; i > 0; --i) {
+            const T w = W[i + (size_t)c * ldw];
+            const unsigned long long *b = reinterpret_cast<const unsigned long long *>(&w);
+            bool nz = (b[0] << 1) != 0ull;                    // nonzero, sign bit ignored
+            if (sizeof(T) == 16) nz = nz || (b[1] << 1) != 0ull;
+            if (nz) { e = i; break; }
+        }
+        end_s[c] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 1; c < m; ++c) end_s[c] = max(end_s[c], end_s[c - 1]);
+    __syncthreads();
     for (int j = 0; j < m; ++j) {
-        const int len = rows - j;
+        const int len = max(end_s[j], j) - j + 1;
         T beta;
         const T tau = house_par<T>(W + j + (size_t)j * ldw, len, v, &beta);
         // apply H = I - tau v v^H to columns j+1..m-1 and to rhs (column index m)
@@ -1039,6 +1067,15 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
         G[i + (size_t)q * m] = s;
     }
     __syncthreads();
+    __shared__ double znorm_s;
+    if (warp == 0) {
+        double z2 = 0.0;
+        for (int i = lane; i < rows; i += 32) z2 += Cx<T>::ab2(a.z[i]);
+        z2 = warp_sum(z2);
+        if (lane == 0) znorm_s = sqrt(z2);
+    }
+    __syncthreads();
+    const double znorm = znorm_s;
     for (int q = warp; q < kk; q += nwarps) {
         cplx *g = G + (size_t)q * m;
         double nr = 0.0;
@@ -1047,23 +1084,10 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
         nr = __shfl_sync(0xffffffffu, nr, 0);
         for (int i = lane; i < m; i += 32) g[i] = g[i] * (1.0 / nr);
         __syncwarp();
-        // residual ||Hbar g - theta [g; 0]||
-        const cplx th = mkc(a.theta[2 * q], a.theta[2 * q + 1]);
-        double r2 = 0.0;
-        for (int i = lane; i < rows; i += 32) {
-            cplx sacc = {0.0, 0.0};
-            for (int j = 0; j < m; ++j) {
-                T hij = a.H[i + (size_t)j * ldh];
-                cplx hc;
-                if constexpr (sizeof(T) == sizeof(double)) hc = mkc(*reinterpret_cast<const double *>(&hij), 0.0);
-                else hc = *reinterpret_cast<const cplx *>(&hij);
-                sacc = sacc + hc * g[j];
-            }
-            if (i < m) sacc = sacc - th * g[i];
-            r2 += abs2(sacc);
-        }
-        r2 = warp_sum(r2);
-        if (lane == 0) a.eres[q] = sqrt(r2);
+        // residual ||Hbar g - theta [g; 0]|| = |g_m| ||z||: an eigenpair of
+        // H_m + |h|^2 f e_m^T satisfies H_m g - theta g = -|h|^2 f g_m, and the last row of
+        // Hbar g is h g_m, so the residual vector is g_m z with z = [-|h|^2 f; h]
+        if (lane == 0) a.eres[q] = sqrt(abs2(g[m - 1])) * znorm;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1272,9 +1296,7 @@ void launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
         smem += parts[q];
         a.smem = q + 1;
     }
-    if (smem > 48 * 1024)   // one fixed value: concurrent callers cannot lower it under each other
-        cudaFuncSetAttribute((const void *)k_gmresdr_restart<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kGdrSmemMax);
+    if (smem > 48 * 1024) smem_attr_once((const void *)k_gmresdr_restart<T>, (int)kGdrSmemMax);
     k_gmresdr_restart<T><<<1, kGdrThreads, smem, s>>>(a);
 }
 template <class D>

@@ -17,7 +17,7 @@ import pytest
 
 import tg_inputs as gi
 from oracle import krylov, transfer
-from oracle.gmresdr import harmonic_ritz as o_hritz, order_ritz, real_span_basis, select_k
+from oracle.gmresdr import eigen_residuals, harmonic_ritz as o_hritz, order_ritz, real_span_basis, select_k
 from oracle.operators import CD2D, CD3D, U1_4D, VARK2D, Operator as OOp
 
 torch = pytest.importorskip("torch")
@@ -213,6 +213,9 @@ def test_harmonic_ritz_kernel_real(tg, m, k, seed, src):
     ref = real_span_basis(G, theta, sel, True)
     assert _span_gap(ref, basis) <= 1e-8
     assert np.max(np.abs(basis.T @ basis - np.eye(len(sel)))) <= 1e-12
+    # eigen-residuals ||Hbar g - theta [g; 0]|| (the oracle forms them explicitly)
+    ref_res = eigen_residuals(H, theta, G, idx[:len(sel)])
+    assert np.allclose(eres, ref_res, rtol=1e-6, atol=1e-10 * np.linalg.norm(H))
 
 
 @pytest.mark.parametrize("m,k,seed", [(20, 6, 5), (40, 20, 6)])
@@ -226,6 +229,8 @@ def test_harmonic_ritz_kernel_complex(tg, m, k, seed):
     assert np.max(np.abs(th - theta[idx]) / np.abs(theta[idx])) <= 1e-10
     sel = select_k(theta, k, False)
     assert _span_gap(G[:, sel], basis) <= 1e-8
+    ref_res = eigen_residuals(H, theta, G, idx[:len(sel)])
+    assert np.allclose(host(eres), ref_res, rtol=1e-6, atol=1e-10 * np.linalg.norm(H))
 
 
 @pytest.mark.parametrize("kind,N,beta", [("cd2d", 63, (1.0,)), ("u1_4d", 8, None)])

@@ -121,6 +121,31 @@ def test_cfg1_shape_small_3d(tg):
         assert rel(x, xs) <= 1e-6
 
 
+@pytest.mark.parametrize("kind,N,beta", [("cd2d", 127, (1.0,)), ("u1_4d", 8, None)])
+def test_coarse_gmresdr_graph_replay_bitwise(tg, kind, N, beta):
+    """Cycles replayed from captured CUDA graphs (per-launch profiling off; capture on the
+    second use of a cycle shape) give bit-identical results to the eager launches
+    (profiling on), on repeated calls with the same operator."""
+    if kind == "u1_4d":
+        links = gi.u1_links(N, 1)
+        top = tg.Operator(kind, N, links=cu(links), mass=0.2)
+        b = cu(gi.rhs(top.n, 3).astype(np.complex128))
+    else:
+        top = tg.Operator(kind, N, beta)
+        b = cu(gi.rhs(top.n, 3))
+    runs = []
+    for prof in (True, False, False, True):
+        tg.tg_profile_enable(prof)
+        xc, defl, st, status = top.coarse_gmresdr(b, 30, 12, rtolev=1e-6, rtol=1e-10, max_cycles=60)
+        tg.tg_profile_enable(False)
+        runs.append((host(xc), host(defl.copy(0)), st["cycles"], st["kk"]))
+    assert runs[0][2] >= 5                      # enough cycles for captured replays to occur
+    for r in runs[1:]:
+        assert r[2] == runs[0][2] and r[3] == runs[0][3]
+        assert np.array_equal(r[0], runs[0][0])
+        assert np.array_equal(r[1], runs[0][1])
+
+
 def test_coarse_gmresdr_eigenvalues(tg):
     N = 63
     top = tg.Operator("cd2d", N, (1.0,))
