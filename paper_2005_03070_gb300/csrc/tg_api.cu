@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "tg_kernels.cuh"
@@ -216,7 +217,7 @@ namespace tg {
 // kernel and the x_c update), valid while the workspace generation is unchanged.
 struct GdrGraph {
     const void *V = nullptr, *H = nullptr;
-    int j0 = -1, m = 0, k = 0, nev = 0, transpose = 0;
+    int j0 = -1, m = 0, k = 0, nev = 0, transpose = 0, esz = 0;   // esz: basis element size
     double rtolev = 0;
     unsigned gen = 0;
     cudaGraphExec_t exec = nullptr;
@@ -360,6 +361,18 @@ static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Ou
     size_t smem = (size_t)32 * p * sizeof(T);
     TG_CHECK(set_smem<T>((const void *)k_tsm<T>, smem));
     TG_PROF(P_TSM, (double)(p + q) * n * sizeof(T), 2.0 * p * q * n * (sizeof(T) == 16 ? 4 : 1), k_tsm<T><<<tiles_grid(n, 4), kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n));
+    TG_LAUNCH_CHECK();
+    return TG_OK;
+}
+
+// Out (n x q) = In (n x p) S (p x q) for a float32 basis and a float64 S; Out float32 or float64
+template <class TO>
+static int tsm_f(const float *In, size_t ldi, int p, const double *S, int lds, int q, TO *Out, size_t ldo, int n,
+                 cudaStream_t s) {
+    const size_t smem = ((size_t)p * q + (size_t)32 * p) * sizeof(float);
+    TG_CHECK(set_smem<float>((const void *)k_tsm_f<TO>, smem));
+    TG_PROF(P_TSM, (double)p * n * 4 + (double)q * n * sizeof(TO), 2.0 * p * q * n,
+            k_tsm_f<TO><<<tiles_grid(n, 4), kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -1120,8 +1133,8 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
 // ----------------------------------------------------------------------------- Arnoldi (CGS2)
 // Extends V (ld ldv, columns 0..j orthonormal) by column j+1 = A v_j orthogonalised; writes
 // Hbar column j (ld ldh).  Two classical Gram-Schmidt passes as tall-skinny products.
-template <class T>
-static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int n, int j, T *H, int ldh,
+template <class T, class HT = T>
+static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int n, int j, HT *H, int ldh,
                         cudaStream_t s) {
     using D = typename ST<T>::D;
     // w = A v_j, then two classical Gram-Schmidt passes, each a tall-skinny V^H w and a
@@ -1159,7 +1172,7 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
             k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gbt, ncol, h2, 0));
     TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
             k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h2, w, n, nullptr, part, tk, nrm, nullptr, nullptr, 0.0));
-    TG_PROF(P_SMALL, 0, j, k_arnoldi_finish2<T><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, inv));
+    TG_PROF(P_SMALL, 0, j, k_arnoldi_finish2<T, HT><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, inv));
     TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, inv));
     TG_LAUNCH_CHECK();
     return TG_OK;
@@ -1301,16 +1314,16 @@ namespace tg {
 // restart kernel (least squares, harmonic Ritz pairs, P_{k+1}, Hnew, cnew) and x_c += V_m d.
 // With per-launch profiling off, the cycle is captured once as a CUDA graph per (basis
 // buffer, Hessenberg buffer, j0) and replayed: about 10 (m - j0) launches become one.
-template <class T>
-static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int nc, int j0, int m, T *H,
-                     int ldh, T *H2, const GdrArgs<T> &a, T *xc, int transpose, cudaStream_t s) {
+template <class T, class HT = T>
+static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int nc, int j0, int m, HT *H,
+                     int ldh, HT *H2, const GdrArgs<HT> &a, T *xc, int transpose, cudaStream_t s) {
     using D = typename ST<T>::D;
     const cudaStream_t s_caller = s;
     // the cycle's launches, queued on stream s (the caller's, or the capture stream)
     auto body = [&](cudaStream_t s) -> int {
-        for (int j = j0; j < m; ++j) TG_CHECK(arnoldi_step<T>(op, A, A32, V, ldv, nc, j, H, ldh, s));
-        TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * sizeof(T), s));
-        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
+        for (int j = j0; j < m; ++j) TG_CHECK((arnoldi_step<T, HT>(op, A, A32, V, ldv, nc, j, H, ldh, s)));
+        TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * sizeof(HT), s));
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<HT>(a, s));
         TG_LAUNCH_CHECK();
         // x_c += V_m d
         TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc,
@@ -1335,7 +1348,7 @@ static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t
     GdrGraph *hit = nullptr;
     for (auto &g : op->graphs)
         if (g.V == V && g.H == H && g.j0 == j0 && g.m == m && g.k == a.k && g.nev == a.nev && g.rtolev == a.rtolev &&
-            g.transpose == transpose) {
+            g.transpose == transpose && g.esz == (int)sizeof(T)) {
             hit = &g;
             break;
         }
@@ -1344,7 +1357,7 @@ static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t
         // driver call, such as shared memory limits, outside any capture); capture on reuse
         GdrGraph ent;
         ent.V = V; ent.H = H; ent.j0 = j0; ent.m = m; ent.k = a.k; ent.nev = a.nev; ent.rtolev = a.rtolev;
-        ent.transpose = transpose; ent.gen = op->ws_gen;
+        ent.transpose = transpose; ent.esz = (int)sizeof(T); ent.gen = op->ws_gen;
         op->graphs.push_back(ent);
         return body(s_caller);
     }
@@ -1386,61 +1399,71 @@ static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t
     return TG_OK;
 }
 
-template <class T>
+// Coarse GMRES-DR(m, k).  T is the basis type (the Arnoldi vectors, operator products and
+// orthogonalisation), HT the type of the Hessenberg matrix and the small dense restart step
+// (least squares, harmonic Ritz pairs, recombination matrices) and of the outputs: T = HT
+// (float64 or complex128), or T = float, HT = double for the float32 + refinement form.
+template <class T, class HT = T>
 static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int k, int nev, double rtolev,
                         double rtol, int max_cycles, void *xc_out, tg_defl **defl_out, int proj, int precision,
                         tg_stats *stats, cudaStream_t s, tg_defl *reuse = nullptr) {
-    using D = T;
+    constexpr bool kMixed = !std::is_same<T, HT>::value;
     const DevOp &A = pick(op, TG_COARSE, transpose);
     const DevOp32 &A32 = pick32(op, TG_COARSE, transpose);
     const int nc = op->nc;
     const int ldh = m + 1;
-    const size_t es = sizeof(T);
+    const size_t es = sizeof(T), hs = sizeof(HT);
     // basis leading dimension rounded up to 64 rows: every column starts 16-byte aligned
     // and whole 64-row chunks stay inside the allocation (pipelined V^H w)
     const size_t ldv = ((size_t)nc + 63) / 64 * 64;
     TG_CHECK(wsx(op, S_GV, ldv * (m + 1) * es));
     TG_CHECK(wsx(op, S_GV2, ldv * (m + 1) * es));
-    TG_CHECK(wsx(op, S_GH, (size_t)ldh * m * es));
-    TG_CHECK(wsx(op, S_GH2, (size_t)ldh * m * es));
-    TG_CHECK(wsx(op, S_GC, (size_t)(m + 1) * es));
+    TG_CHECK(wsx(op, S_GH, (size_t)ldh * m * hs));
+    TG_CHECK(wsx(op, S_GH2, (size_t)ldh * m * hs));
+    TG_CHECK(wsx(op, S_GC, (size_t)(m + 1) * hs));
     TG_CHECK(wsx(op, S_GX, (size_t)nc * es));
-    TG_CHECK(wsx(op, S_GD, (size_t)(m + 1) * es));
-    TG_CHECK(wsx(op, S_GRES, (size_t)(m + 1) * es));
-    TG_CHECK(wsx(op, S_GZ, (size_t)(m + 1) * es));
-    TG_CHECK(wsx(op, S_GP, (size_t)(m + 1) * (m + 2) * es));
-    TG_CHECK(wsx(op, S_GCN, (size_t)(m + 2) * es));
+    TG_CHECK(wsx(op, S_GD, (size_t)(m + 1) * hs));
+    TG_CHECK(wsx(op, S_GRES, (size_t)(m + 1) * hs));
+    TG_CHECK(wsx(op, S_GZ, (size_t)(m + 1) * hs));
+    TG_CHECK(wsx(op, S_GP, (size_t)(m + 1) * (m + 2) * hs));
+    TG_CHECK(wsx(op, S_GCN, (size_t)(m + 2) * hs));
     TG_CHECK(wsx(op, S_GTHETA, (size_t)2 * m * 8));
     TG_CHECK(wsx(op, S_GWR, (size_t)m * 8));
     TG_CHECK(wsx(op, S_GWI, (size_t)m * 8));
     TG_CHECK(wsx(op, S_GORD, (size_t)m * 4));
     TG_CHECK(wsx(op, S_GERES, (size_t)m * 8));
-    TG_CHECK(wsx(op, S_GWORK, ((size_t)(m + 1) * m + 2 * (size_t)m * m + 3 * (size_t)m + 4) * es));
+    TG_CHECK(wsx(op, S_GWORK, ((size_t)(m + 1) * m + 2 * (size_t)m * m + 3 * (size_t)m + 4) * hs));
     TG_CHECK(wsx(op, S_GY, (size_t)m * m * 16));
     TG_CHECK(wsx(op, S_GG, (size_t)m * m * 16));
     TG_CHECK(wsx(op, S_GINFO, sizeof(GdrInfo)));
-    TG_CHECK(wsx(op, S_GB, (size_t)nc * es));
-    TG_CHECK(wsx(op, S_GTMP, (size_t)(m + 2) * es));
+    TG_CHECK(wsx(op, S_GB, (size_t)nc * hs));
+    TG_CHECK(wsx(op, S_GTMP, (size_t)(m + 2) * hs));
     T *V = wsp<T>(op, S_GV), *V2 = wsp<T>(op, S_GV2);
-    T *H = wsp<T>(op, S_GH), *H2 = wsp<T>(op, S_GH2);
-    T *c = wsp<T>(op, S_GC), *xc = wsp<T>(op, S_GX), *bc = wsp<T>(op, S_GB);
+    HT *H = wsp<HT>(op, S_GH), *H2 = wsp<HT>(op, S_GH2);
+    HT *c = wsp<HT>(op, S_GC), *bc = wsp<HT>(op, S_GB);
+    T *xc = wsp<T>(op, S_GX);
     // b_c = restrict(b); v_0 = b_c / ||b_c||; x_c = 0
     TG_CHECK(restrict_impl(op, b_fine, bc, 1, s));
     double nbc2;
-    TG_CHECK(dot_host<T>(op, bc, nullptr, nc, &nbc2, nullptr, s));
+    TG_CHECK(dot_host<HT>(op, bc, nullptr, nc, &nbc2, nullptr, s));
     const double nbc = sqrt(nbc2);
     TG_ARG(nbc > 0 && std::isfinite(nbc), "restricted right-hand side is zero or not finite");
-    TG_CHECK_CUDA(cudaMemcpyAsync(V, bc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
-    double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
-    double hinv = 1.0 / nbc;
-    TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
-    TG_PROF(P_SCALE, 2.0 * nc * sizeof(T), nc, k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, inv));
+    if constexpr (kMixed) {
+        TG_PROF(P_CONVERT, 12.0 * nc, nc, launch_d2f_scaled(grid_for(nc, 8), s, bc, V, nc, 1.0 / nbc));
+        TG_LAUNCH_CHECK();
+    } else {
+        TG_CHECK_CUDA(cudaMemcpyAsync(V, bc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
+        double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
+        double hinv = 1.0 / nbc;
+        TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
+        TG_PROF(P_SCALE, 2.0 * nc * sizeof(T), nc, k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, inv));
+    }
     TG_CHECK_CUDA(cudaMemsetAsync(xc, 0, (size_t)nc * es, s));
-    TG_CHECK_CUDA(cudaMemsetAsync(H, 0, (size_t)ldh * m * es, s));
-    TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * es, s));
-    T c0{};
+    TG_CHECK_CUDA(cudaMemsetAsync(H, 0, (size_t)ldh * m * hs, s));
+    TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * hs, s));
+    HT c0{};
     memcpy(&c0, &nbc, sizeof(double));
-    TG_CHECK_CUDA(cudaMemcpyAsync(c, &c0, sizeof(T), cudaMemcpyHostToDevice, s));
+    TG_CHECK_CUDA(cudaMemcpyAsync(c, &c0, sizeof(HT), cudaMemcpyHostToDevice, s));
     int j0 = 0;
     int cycles = 0;
     int64_t cmvps = 0;
@@ -1449,14 +1472,14 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     bool converged = false;
     while (true) {
         ++cycles;
-        GdrArgs<T> a;
+        GdrArgs<HT> a;
         a.H = H; a.ldh = ldh; a.c = c; a.m = m; a.k = k; a.nev = nev; a.rtolev = rtolev;
-        a.d = wsp<T>(op, S_GD); a.res = wsp<T>(op, S_GRES); a.z = wsp<T>(op, S_GZ);
+        a.d = wsp<HT>(op, S_GD); a.res = wsp<HT>(op, S_GRES); a.z = wsp<HT>(op, S_GZ);
         a.theta = wsp<double>(op, S_GTHETA); a.wr = wsp<double>(op, S_GWR); a.wi = wsp<double>(op, S_GWI);
-        a.order = wsp<int>(op, S_GORD); a.eres = wsp<double>(op, S_GERES); a.P = wsp<T>(op, S_GP);
-        a.Hnew = H2; a.cnew = wsp<T>(op, S_GCN); a.work = wsp<T>(op, S_GWORK);
+        a.order = wsp<int>(op, S_GORD); a.eres = wsp<double>(op, S_GERES); a.P = wsp<HT>(op, S_GP);
+        a.Hnew = H2; a.cnew = wsp<HT>(op, S_GCN); a.work = wsp<HT>(op, S_GWORK);
         a.ywork = wsp<cplx>(op, S_GY); a.gwork = wsp<cplx>(op, S_GG); a.info = wsp<GdrInfo>(op, S_GINFO);
-        TG_CHECK(gdr_cycle<T>(op, A, A32, V, ldv, nc, j0, m, H, ldh, H2, a, xc, transpose, s));
+        TG_CHECK((gdr_cycle<T, HT>(op, A, A32, V, ldv, nc, j0, m, H, ldh, H2, a, xc, transpose, s)));
         cmvps += m - j0;
         TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
         memcpy(&info, op->pin.p, sizeof(info));
@@ -1471,11 +1494,12 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         converged = info.rnorm <= rtol * nbc && info.nconv >= (nev < kk ? nev : kk);
         if (converged || cycles >= max_cycles) break;
         // restart: V_{k+1} = V_{m+1} P_{k+1}; Hbar = Hnew; c = cnew
-        TG_CHECK(tsm<T>(V, ldv, m + 1, a.P, m + 1, kk + 1, V2, ldv, nc, s));
+        if constexpr (kMixed) TG_CHECK(tsm_f<float>(V, ldv, m + 1, a.P, m + 1, kk + 1, V2, ldv, nc, s));
+        else TG_CHECK(tsm<T>(V, ldv, m + 1, a.P, m + 1, kk + 1, V2, ldv, nc, s));
         std::swap(V, V2);
         std::swap(H, H2);
-        TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * es, s));
-        TG_CHECK_CUDA(cudaMemcpyAsync(c, a.cnew, (size_t)(kk + 1) * es, cudaMemcpyDeviceToDevice, s));
+        TG_CHECK_CUDA(cudaMemsetAsync(c, 0, (size_t)(m + 1) * hs, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(c, a.cnew, (size_t)(kk + 1) * hs, cudaMemcpyDeviceToDevice, s));
         // re-orthogonalise v_{k+1} against V_k and normalise
         {
             using DD = typename ST<T>::D;
@@ -1500,22 +1524,31 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         stats->eig_converged = info.nconv;
         stats->status = converged ? TG_OK : TG_NOT_CONVERGED;
     }
-    if (xc_out) TG_CHECK_CUDA(cudaMemcpyAsync(xc_out, xc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
+    if (xc_out) {
+        if constexpr (kMixed) {
+            TG_CHECK_CUDA(cudaMemsetAsync(xc_out, 0, (size_t)nc * hs, s));
+            TG_PROF(P_CONVERT, 12.0 * nc, nc, launch_add_f2d_scaled(grid_for(nc, 8), s, (double *)xc_out, xc, nc, 1.0));
+            TG_LAUNCH_CHECK();
+        } else {
+            TG_CHECK_CUDA(cudaMemcpyAsync(xc_out, xc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
+        }
+    }
     if (defl_out) {
-        TG_CHECK(wsx(op, S_GYC, (size_t)nc * kk * es));
+        TG_CHECK(wsx(op, S_GYC, (size_t)nc * kk * hs));
         DBuf &Yc = op->ws[S_GYC];
-        TG_CHECK(tsm<T>(V, ldv, m, wsp<T>(op, S_GP), m + 1, kk, Yc.as<T>(), nc, nc, s));
+        if constexpr (kMixed) TG_CHECK(tsm_f<double>(V, ldv, m, wsp<HT>(op, S_GP), m + 1, kk, Yc.as<double>(), nc, nc, s));
+        else TG_CHECK(tsm<T>(V, ldv, m, wsp<T>(op, S_GP), m + 1, kk, Yc.as<T>(), nc, nc, s));
         tg_defl *d = reuse;
         if (d) {
             // rebuild in the caller's handle: its buffers grow only when needed
             d->kk = kk; d->n = op->n; d->proj = proj; d->precision = precision; d->cplx_ = op->cplx_;
             d->transposed = transpose != 0;
-            TG_CHECK(d->Y.ensure((size_t)op->n * kk * es));
+            TG_CHECK(d->Y.ensure((size_t)op->n * kk * hs));
         } else {
             TG_CHECK(defl_create(op, transpose, kk, proj, precision, &d));
         }
         int rc = prolong_impl(op, Yc.p, d->Y.p, kk, s);
-        if (!rc) rc = build_defl<T>(op, transpose, d, s);
+        if (!rc) rc = build_defl<HT>(op, transpose, d, s);
         if (rc) {
             if (!reuse) delete d;
             return rc;
@@ -1544,6 +1577,9 @@ extern "C" int tg_coarse_gmresdr(tg_op *op, int transpose, const void *b_fine, i
     if (op->cplx_)
         return gmresdr_impl<cplx>(op, transpose, b_fine, m, k, nev, rtolev, rtol, max_cycles, xc_out, defl_out, proj,
                                   precision, stats, s);
+    if (precision == TG_F32_IR)
+        return gmresdr_impl<float, double>(op, transpose, b_fine, m, k, nev, rtolev, rtol, max_cycles, xc_out, defl_out,
+                                           proj, precision, stats, s);
     return gmresdr_impl<double>(op, transpose, b_fine, m, k, nev, rtolev, rtol, max_cycles, xc_out, defl_out, proj,
                                 precision, stats, s);
 }

@@ -539,13 +539,14 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n_norm(const T *__restrict__ 
 }
 
 // Hbar column j: H[i] = h1[i] + h2[i] (i <= j), H[j+1] = sqrt(nrm2[0]), inv[0] = 1/H[j+1].
-template <class T>
+// HT is the Hessenberg type: the basis type, or float64 for a float32 basis.
+template <class T, class HT = T>
 __global__ void k_arnoldi_finish2(const typename ST<T>::D *h1, const typename ST<T>::D *h2, const double *nrm2,
-                                  int j, T *Hcol, double *inv) {
+                                  int j, HT *Hcol, double *inv) {
     for (int i = threadIdx.x; i <= j; i += blockDim.x) Hcol[i] = dadd(h1[i], h2[i]);
     if (threadIdx.x == 0) {
         const double nn = sqrt(nrm2[0]);
-        T hv = ST<T>::zero();
+        HT hv = ST<HT>::zero();
         *reinterpret_cast<double *>(&hv) = nn;
         Hcol[j + 1] = hv;
         inv[0] = nn > 0 ? 1.0 / nn : 0.0;
@@ -600,6 +601,39 @@ __global__ void __launch_bounds__(kThreads) k_tsm(const T *__restrict__ In, size
             const T *sc = S + (size_t)c * lds;
             for (int i = 0; i < p; ++i) acc = axpy(sc[i], tile[i * 32 + r], acc);
             if (row < n) Out[(size_t)c * ldo + row] = acc;
+        }
+    }
+}
+
+// Out (n x q) = In (n x p) * S (p x q) for a float32 basis In and a float64 S (column-major,
+// leading dimension lds): S is staged once per block as float32 in shared memory, 32-row
+// tiles of In after it; float32 accumulation; Out is float32 or float64 (converted on store).
+template <class TO>
+__global__ void __launch_bounds__(kThreads) k_tsm_f(const float *__restrict__ In, size_t ldi, int p,
+                                                     const double *__restrict__ S, int lds, int q,
+                                                     TO *__restrict__ Out, size_t ldo, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Ss = reinterpret_cast<float *>(smem_raw);            // p x q
+    float *tile = Ss + (size_t)p * q;                           // [p][32]
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+        const int i = e % p, c = e / p;
+        Ss[e] = (float)S[i + (size_t)c * lds];
+    }
+    for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * p; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;
+            const int row = row0 + r;
+            tile[c * 32 + r] = row < n ? In[(size_t)c * ldi + row] : 0.0f;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < 32 * q; o += blockDim.x) {
+            const int r = o & 31, c = o >> 5;
+            const int row = row0 + r;
+            float acc = 0.0f;
+            const float *sc = Ss + (size_t)c * p;
+            for (int i = 0; i < p; ++i) acc = fmaf(sc[i], tile[i * 32 + r], acc);
+            if (row < n) Out[(size_t)c * ldo + row] = (TO)acc;
         }
     }
 }
