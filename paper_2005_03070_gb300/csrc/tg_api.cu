@@ -369,40 +369,58 @@ static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Ou
 template <class TO>
 static int tsm_f(const float *In, size_t ldi, int p, const double *S, int lds, int q, TO *Out, size_t ldo, int n,
                  cudaStream_t s) {
-    const size_t smem = ((size_t)p * q + (size_t)32 * p) * sizeof(float);
-    TG_CHECK(set_smem<float>((const void *)k_tsm_f<TO>, smem));
-    TG_PROF(P_TSM, (double)p * n * 4 + (double)q * n * sizeof(TO), 2.0 * p * q * n,
-            k_tsm_f<TO><<<tiles_grid(n, 4), kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n));
+    TG_ARG(q >= 1 && q <= 128 && p >= 1, "float32 tall-skinny product: need 1 <= q <= 128 (q=%d)", q);
+    TG_ARG(!((uintptr_t)In & 15) && ldi % 4 == 0 && ldi >= (size_t)(n + 63) / 64 * 64,
+           "float32 tall-skinny product: In needs 16-byte aligned columns and 64-row padding");
+    TG_ARG(((uintptr_t)Out & 15) == 0, "float32 tall-skinny product: Out must be 16-byte aligned");
+    const size_t smem = ((size_t)p * q + (size_t)2 * 64 * p) * sizeof(float);
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 63) / 64, (int64_t)num_sms() * 4));
+    auto go = [&](auto cpt) -> int {
+        constexpr int C = decltype(cpt)::value;
+        TG_CHECK(set_smem<float>((const void *)k_tsm_f<TO, C>, smem));
+        TG_PROF(P_TSM, (double)p * n * 4 + (double)q * n * sizeof(TO), 2.0 * p * q * n,
+                k_tsm_f<TO, C><<<gb, kThreads, smem, s>>>(In, ldi, p, S, lds, q, Out, ldo, n));
+        return TG_OK;
+    };
+    if (q <= 16) TG_CHECK(go(std::integral_constant<int, 1>{}));
+    else if (q <= 32) TG_CHECK(go(std::integral_constant<int, 2>{}));
+    else if (q <= 64) TG_CHECK(go(std::integral_constant<int, 4>{}));
+    else TG_CHECK(go(std::integral_constant<int, 8>{}));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
 
 // h = V^H w (ncol entries, device D array)
-// Whether the pipelined float64 V^H w kernel applies: 16-byte aligned columns and room for
-// whole 64-row chunks below the leading dimension.
+// Whether the pipelined V^H w kernel applies (float64 or float32): 16-byte aligned columns
+// and room for whole chunks below the leading dimension.
 template <class T>
 static bool pipe_ok(const T *V, size_t ldv, const T *w, int n, int ncol) {
-    if (sizeof(T) != 8) return false;
-    if (ldv % 2 || ldv < (size_t)((n + kPipeRows - 1) / kPipeRows) * kPipeRows) return false;
+    if (sizeof(T) != 8 && sizeof(T) != 4) return false;
+    const int R = sizeof(T) == 8 ? PipeRows<double>::value : PipeRows<float>::value;
+    if ((ldv * sizeof(T)) % 16 || ldv < (size_t)((n + R - 1) / R) * R) return false;
     if (((uintptr_t)V | (uintptr_t)w) & 15) return false;
-    return ncol + 1 <= 136 && n >= kPipeRows;
+    return ncol + 1 <= 136 && n >= R;
 }
 
 // partials of V^H w into part (gb blocks); returns gb
 template <class T>
 static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int n, typename ST<T>::D *part,
                               cudaStream_t s, bool *used_pipe) {
-    if (pipe_ok<T>(V, ldv, w, n, ncol)) {
-        const size_t smem = (size_t)kPipeStages * (ncol + 1) * kPipeRows * sizeof(double);
-        smem_attr_once((const void *)k_gemv_t_pipe, max_dyn_smem());
-        const int per_sm = smem <= 100 * 1024 ? 2 : 1;
-        const int nchunks = (n + kPipeRows - 1) / kPipeRows;
-        const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
-        k_gemv_t_pipe<<<gb, kThreads, smem, s>>>(reinterpret_cast<const double *>(V), ldv, ncol,
-                                                 reinterpret_cast<const double *>(w), n,
-                                                 reinterpret_cast<double *>(part));
-        *used_pipe = true;
-        return gb;
+    if constexpr (sizeof(T) == 8 || sizeof(T) == 4) {
+        if (pipe_ok<T>(V, ldv, w, n, ncol)) {
+            using E = typename std::conditional<sizeof(T) == 8, double, float>::type;
+            constexpr int R = PipeRows<E>::value;
+            const size_t smem = (size_t)kPipeStages * (ncol + 1) * R * sizeof(E);
+            smem_attr_once((const void *)k_gemv_t_pipe<E>, max_dyn_smem());
+            const int per_sm = smem <= 100 * 1024 ? 2 : 1;
+            const int nchunks = (n + R - 1) / R;
+            const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
+            k_gemv_t_pipe<E><<<gb, kThreads, smem, s>>>(reinterpret_cast<const E *>(V), ldv, ncol,
+                                                        reinterpret_cast<const E *>(w), n,
+                                                        reinterpret_cast<double *>(part));
+            *used_pipe = true;
+            return gb;
+        }
     }
     const int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
     k_gemv_t_part<T><<<std::max(gb, 1), kThreads, 0, s>>>(V, ldv, ncol, w, n, part);
@@ -1133,6 +1151,21 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
 // ----------------------------------------------------------------------------- Arnoldi (CGS2)
 // Extends V (ld ldv, columns 0..j orthonormal) by column j+1 = A v_j orthogonalised; writes
 // Hbar column j (ld ldh).  Two classical Gram-Schmidt passes as tall-skinny products.
+// w -= V h and ||w||^2 (k_gemv_n_norm), with the float4 kernel for an aligned float32 basis
+// (its rows in groups of 4; no re-orthogonalisation flag, which no caller reads there)
+template <class T>
+static void gemv_n_norm_launch(int g, const T *V, size_t ldv, int ncol, const typename ST<T>::D *h, T *w, int n,
+                               typename ST<T>::D *part, unsigned *tk, double *nrm,
+                               const typename ST<T>::D *nrm_before, int *flag, double eta2, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (ldv % 4 == 0 && !(((uintptr_t)V | (uintptr_t)w) & 15)) {
+            k_gemv_n_norm_f4<<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, part, tk, nrm);
+            return;
+        }
+    }
+    k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, nullptr, part, tk, nrm, nrm_before, flag, eta2);
+}
+
 template <class T, class HT = T>
 static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t ldv, int n, int j, HT *H, int ldh,
                         cudaStream_t s) {
@@ -1163,7 +1196,7 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     TG_PROF(P_SUM_PART, (double)gbt * (ncol + 1) * sizeof(D), (double)gbt * (ncol + 1),
             k_sum_part<D><<<(ncol + 1 + 7) / 8, 256, 0, s>>>(part, gbt, ncol + 1, h1, 0));
     TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
-            k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h1, w, n, nullptr, part, tk, nrm, h1 + ncol, flag, 0.5));
+            gemv_n_norm_launch<T>(g, V, ldv, ncol, h1, w, n, part, tk, nrm, h1 + ncol, flag, 0.5, s));
     // pass 2 (classical Gram-Schmidt twice: on this operator the selective criterion of
     // Daniel, Gragg, Kaufman and Stewart asked for the second pass on nearly every step)
     TG_PROF(P_GEMV_T, (double)(ncol + 1) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
@@ -1171,7 +1204,7 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     TG_PROF(P_SUM_PART, (double)gbt * ncol * sizeof(D), (double)gbt * ncol,
             k_sum_part<D><<<(ncol + 7) / 8, 256, 0, s>>>(part, gbt, ncol, h2, 0));
     TG_PROF(P_GEMV_N, (ncol + 2.0) * n * sizeof(T), 2.0 * ncol * n * (sizeof(T) == 16 ? 4 : 1),
-            k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h2, w, n, nullptr, part, tk, nrm, nullptr, nullptr, 0.0));
+            gemv_n_norm_launch<T>(g, V, ldv, ncol, h2, w, n, part, tk, nrm, nullptr, nullptr, 0.0, s));
     TG_PROF(P_SMALL, 0, j, k_arnoldi_finish2<T, HT><<<1, 128, 0, s>>>(h1, h2, nrm, j, H + (size_t)j * ldh, inv));
     TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, inv));
     TG_LAUNCH_CHECK();
@@ -1413,9 +1446,10 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
     const int nc = op->nc;
     const int ldh = m + 1;
     const size_t es = sizeof(T), hs = sizeof(HT);
-    // basis leading dimension rounded up to 64 rows: every column starts 16-byte aligned
-    // and whole 64-row chunks stay inside the allocation (pipelined V^H w)
-    const size_t ldv = ((size_t)nc + 63) / 64 * 64;
+    // basis leading dimension rounded up to 128 rows: every column starts 16-byte aligned
+    // and whole chunks (64 float64 / 128 float32 rows) stay inside the allocation
+    // (pipelined V^H w)
+    const size_t ldv = ((size_t)nc + 127) / 128 * 128;
     TG_CHECK(wsx(op, S_GV, ldv * (m + 1) * es));
     TG_CHECK(wsx(op, S_GV2, ldv * (m + 1) * es));
     TG_CHECK(wsx(op, S_GH, (size_t)ldh * m * hs));

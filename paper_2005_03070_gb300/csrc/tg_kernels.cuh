@@ -4,6 +4,8 @@
 // cplx (complex128 lattice).
 #pragma once
 
+#include <type_traits>
+
 #include "tg_common.cuh"
 
 namespace tg {
@@ -388,13 +390,18 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
     }
 }
 
-// h = V^H w partials for float64 V with 16-byte aligned columns (ldv even, V and w 16-byte
-// aligned, ldv >= the rows rounded up to 64): the rows are walked in 64-row chunks staged
-// in shared memory by a 3-deep cp.async pipeline, so that loads of the next chunks are in
-// flight while the FP64 pipe works on the current one.  Block b takes chunks b, b + G, ...
-// Warp w owns columns w, w + 8, ...; lane l rows l and l + 32 of a chunk.  Shared memory:
-// 3 x (ncol + 1) x 64 doubles (w is the extra column).
-constexpr int kPipeRows = 64;
+// h = V^H w partials for a float64 or float32 V with 16-byte aligned columns (V and w
+// 16-byte aligned, ldv a multiple of 16 bytes and >= the rows rounded up to whole chunks):
+// the rows are walked in chunks of PipeRows<E> rows (64 float64 / 128 float32 rows, 512
+// bytes per column) staged in shared memory by a 3-deep cp.async pipeline, so that loads of
+// the next chunks are in flight while the arithmetic pipe works on the current one.  Block
+// b takes chunks b, b + G, ...  Warp w owns columns w, w + 8, ...; lane l rows l + 32 u of a
+// chunk.  Accumulation in E; partials written as float64.  Shared memory:
+// 3 x (ncol + 1) x PipeRows<E> elements (w is the extra column).
+template <class E> struct PipeRows;
+template <> struct PipeRows<double> { static constexpr int value = 64; };
+template <> struct PipeRows<float> { static constexpr int value = 128; };
+constexpr int kPipeRows = 64;          // float64 chunk (the float32 chunk holds the same bytes)
 constexpr int kPipeStages = 3;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -404,52 +411,59 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-__global__ void __launch_bounds__(kThreads) k_gemv_t_pipe(const double *__restrict__ V, size_t ldv, int ncol,
-                                                           const double *__restrict__ w, int n, double *part) {
+template <class E>
+__global__ void __launch_bounds__(kThreads) k_gemv_t_pipe(const E *__restrict__ V, size_t ldv, int ncol,
+                                                           const E *__restrict__ w, int n, double *part) {
     constexpr int kMaxPerWarp = 17;
+    constexpr int R = PipeRows<E>::value;
+    constexpr int PE = 16 / sizeof(E);           // elements per 16-byte piece
+    constexpr int U = R / 32;                    // rows per lane per chunk
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *buf = reinterpret_cast<double *>(smem_raw);
+    E *buf = reinterpret_cast<E *>(smem_raw);
     const int cols = ncol + 1;                      // w staged as column ncol
-    const size_t stage_elems = (size_t)cols * kPipeRows;
+    const size_t stage_elems = (size_t)cols * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nchunks = (n + kPipeRows - 1) / kPipeRows;
+    const int nchunks = (n + R - 1) / R;
     const int G = gridDim.x;
     const int mine = blockIdx.x < nchunks ? (nchunks - 1 - blockIdx.x) / G + 1 : 0;
     auto issue = [&](int it) {
         if (it < mine) {
-            const size_t row0 = (size_t)(blockIdx.x + (size_t)it * G) * kPipeRows;
-            double *dst = buf + (size_t)(it % kPipeStages) * stage_elems;
-            // (cols x 64 rows) as 16-byte pieces: piece e -> column e / 32, rows 2 (e % 32) ..
-            for (int e = threadIdx.x; e < cols * (kPipeRows / 2); e += blockDim.x) {
-                const int c = e / (kPipeRows / 2), rp = e % (kPipeRows / 2);
-                const double *src = (c < ncol ? V + (size_t)c * ldv : w) + row0 + 2 * rp;
-                cp_async16(dst + (size_t)c * kPipeRows + 2 * rp, src);
+            const size_t row0 = (size_t)(blockIdx.x + (size_t)it * G) * R;
+            E *dst = buf + (size_t)(it % kPipeStages) * stage_elems;
+            // (cols x R rows) as 16-byte pieces: piece e -> column e / (R / PE), rows PE (e % (R / PE)) ..
+            for (int e = threadIdx.x; e < cols * (R / PE); e += blockDim.x) {
+                const int c = e / (R / PE), rp = e % (R / PE);
+                const E *src = (c < ncol ? V + (size_t)c * ldv : w) + row0 + PE * rp;
+                cp_async16(dst + (size_t)c * R + PE * rp, src);
             }
         }
         cp_async_commit();
     };
-    double acc[kMaxPerWarp];
+    E acc[kMaxPerWarp];
 #pragma unroll
-    for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = 0.0;
+    for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = E(0);
 #pragma unroll
     for (int s = 0; s < kPipeStages - 1; ++s) issue(s);
     for (int it = 0; it < mine; ++it) {
         cp_async_wait<kPipeStages - 2>();
         __syncthreads();
         issue(it + kPipeStages - 1);              // the buffer of iteration it - 1, read by everyone already
-        const double *st = buf + (size_t)(it % kPipeStages) * stage_elems;
-        const int row0 = (blockIdx.x + it * G) * kPipeRows;
-        const bool r0ok = row0 + lane < n, r1ok = row0 + lane + 32 < n;
-        const double w0 = r0ok ? st[(size_t)ncol * kPipeRows + lane] : 0.0;
-        const double w1 = r1ok ? st[(size_t)ncol * kPipeRows + lane + 32] : 0.0;
+        const E *st = buf + (size_t)(it % kPipeStages) * stage_elems;
+        const int row0 = (blockIdx.x + it * G) * R;
+        E wv[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ok[u] = row0 + lane + 32 * u < n;
+            wv[u] = ok[u] ? st[(size_t)ncol * R + lane + 32 * u] : E(0);
+        }
 #pragma unroll
         for (int q = 0; q < kMaxPerWarp; ++q) {
             const int c = warp + 8 * q;
             if (c < ncol) {
-                const double *sc = st + (size_t)c * kPipeRows;
-                const double v0 = r0ok ? sc[lane] : 0.0;
-                const double v1 = r1ok ? sc[lane + 32] : 0.0;
-                acc[q] = fma(v1, w1, fma(v0, w0, acc[q]));
+                const E *sc = st + (size_t)c * R;
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[q] = fma(ok[u] ? sc[lane + 32 * u] : E(0), wv[u], acc[q]);
             }
         }
     }
@@ -458,8 +472,8 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_pipe(const double *__restri
     for (int q = 0; q < kMaxPerWarp; ++q) {
         const int c = warp + 8 * q;
         if (c < ncol) {
-            const double s = warp_sum(acc[q]);
-            if (lane == 0) part[(size_t)blockIdx.x * ncol + c] = s;
+            const E s = warp_sum(acc[q]);
+            if (lane == 0) part[(size_t)blockIdx.x * ncol + c] = (double)s;
         }
     }
 }
@@ -487,13 +501,14 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_gemv_n(const T *__restrict__ V, size_t ldv, int ncol,
                                                       const typename ST<T>::D *__restrict__ h, double sign,
                                                       T *__restrict__ w, int n) {
-    using D = typename ST<T>::D;
-    __shared__ D hs[130];
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = h[c];
+    // coefficients converted to the vector type once per block (a per-element float64 ->
+    // float32 conversion would run on the float64 pipe)
+    __shared__ T hs[130];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = KS<T>::of(h[c]);
     __syncthreads();
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         T acc = ST<T>::zero();
-        for (int c = 0; c < ncol; ++c) acc = axpy(KS<T>::of(hs[c]), V[(size_t)c * ldv + row], acc);
+        for (int c = 0; c < ncol; ++c) acc = axpy(hs[c], V[(size_t)c * ldv + row], acc);
         w[row] = sign > 0 ? dadd(w[row], acc) : sub(w[row], acc);
     }
 }
@@ -514,15 +529,15 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n_norm(const T *__restrict__ 
     using D = typename ST<T>::D;
     using P = typename Part<T>::P;
     if (cond && !*cond) return;
-    __shared__ D hs[130];
+    __shared__ T hs[130];      // coefficients in the vector type, converted once per block
     __shared__ D red[(kThreads / 32)];
     __shared__ D tot[1];
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = h[c];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = KS<T>::of(h[c]);
     __syncthreads();
     P acc[1] = {ST<T>::zero()};
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         T a = ST<T>::zero();
-        for (int c = 0; c < ncol; ++c) a = axpy(KS<T>::of(hs[c]), V[(size_t)c * ldv + row], a);
+        for (int c = 0; c < ncol; ++c) a = axpy(hs[c], V[(size_t)c * ldv + row], a);
         const T wv = sub(w[row], a);
         w[row] = wv;
         acc[0] = ST<T>::fma_cm(wv, wv, acc[0]);
@@ -536,6 +551,124 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n_norm(const T *__restrict__ 
             if (flag_out) flag_out[0] = (nn < eta2 * dreal(nrm2_before[0])) ? 1 : 0;
         }
     }
+}
+
+// k_gemv_n_norm for float32 V with 16-byte aligned columns (ldv a multiple of 4, V and w
+// 16-byte aligned): each thread takes 4 consecutive rows as float4 loads; the rows beyond
+// the last whole group of 4 are taken one by one by the first threads.
+__global__ void __launch_bounds__(kThreads) k_gemv_n_norm_f4(const float *__restrict__ V, size_t ldv, int ncol,
+                                                              const double *__restrict__ h, float *__restrict__ w,
+                                                              int n, double *part, unsigned *ticket,
+                                                              double *nrm2_out) {
+    __shared__ float hs[130];
+    __shared__ double red[(kThreads / 32)];
+    __shared__ double tot[1];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = (float)h[c];
+    __syncthreads();
+    float acc[1] = {0.0f};
+    const int n4 = n >> 2;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += gridDim.x * blockDim.x) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < ncol; ++c) {
+            const float4 v = reinterpret_cast<const float4 *>(V + (size_t)c * ldv)[g];
+            const float hc = hs[c];
+            a.x = fmaf(hc, v.x, a.x); a.y = fmaf(hc, v.y, a.y); a.z = fmaf(hc, v.z, a.z); a.w = fmaf(hc, v.w, a.w);
+        }
+        float4 wv = reinterpret_cast<float4 *>(w)[g];
+        wv.x -= a.x; wv.y -= a.y; wv.z -= a.z; wv.w -= a.w;
+        reinterpret_cast<float4 *>(w)[g] = wv;
+        acc[0] = fmaf(wv.x, wv.x, fmaf(wv.y, wv.y, fmaf(wv.z, wv.z, fmaf(wv.w, wv.w, acc[0]))));
+    }
+    for (int row = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        float a = 0.0f;
+        for (int c = 0; c < ncol; ++c) a = fmaf(hs[c], V[(size_t)c * ldv + row], a);
+        const float wv = w[row] - a;
+        w[row] = wv;
+        acc[0] = fmaf(wv, wv, acc[0]);
+    }
+    block_reduce_store<float, double, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<double, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) nrm2_out[0] = tot[0];
+    }
+}
+
+// Out (n x q) = In (n x p) * S (p x q), float32 In, float64 S (column-major, leading
+// dimension lds, staged once per block as float32), float32 accumulation, Out float32 or
+// float64.  In needs 16-byte aligned columns and ldi >= n rounded up to 64 rows: 64-row
+// tiles of In are copied to shared memory by cp.async, double buffered (rows past n are read
+// from the padding and never stored).  Register tiles: thread (rg, cg), rg, cg < 16,
+// computes rows 4 rg .. 4 rg + 3 and columns cg + 16 j (j < CPT, q <= 16 CPT), reading its 4
+// rows of each In column as one float4 (float32 Out: written as float4 too).
+template <class TO, int CPT>
+__global__ void __launch_bounds__(kThreads) k_tsm_f(const float *__restrict__ In, size_t ldi, int p,
+                                                     const double *__restrict__ S, int lds, int q,
+                                                     TO *__restrict__ Out, size_t ldo, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tiles = reinterpret_cast<float *>(smem_raw);         // 2 x [p][64]
+    float *Ss = tiles + (size_t)2 * p * 64;                     // [q][p]
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+        const int i = e % p, c = e / p;
+        Ss[e] = (float)S[i + (size_t)c * lds];
+    }
+    const int ntiles = (n + 63) / 64;
+    const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto issue = [&](int it) {
+        if (it < mine) {
+            const size_t row0 = (size_t)(blockIdx.x + (size_t)it * gridDim.x) * 64;
+            float *dst = tiles + (size_t)(it & 1) * p * 64;
+            for (int e = threadIdx.x; e < p * 16; e += blockDim.x) {     // 16-byte pieces
+                const int c = e >> 4, rp = e & 15;
+                cp_async16(dst + (size_t)c * 64 + 4 * rp, In + (size_t)c * ldi + row0 + 4 * rp);
+            }
+        }
+        cp_async_commit();
+    };
+    const int rg = threadIdx.x & 15, cg = threadIdx.x >> 4;
+    issue(0);
+    for (int it = 0; it < mine; ++it) {
+        issue(it + 1);                           // the other buffer, released by the barrier below
+        cp_async_wait<1>();
+        __syncthreads();
+        const float *tile = tiles + (size_t)(it & 1) * p * 64;
+        const int row0 = (blockIdx.x + it * gridDim.x) * 64;
+        float acc[CPT][4];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[j][u] = 0.0f;
+        // columns past q read row 0 of S's staging (valid memory) and are never stored
+        int soff[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) soff[j] = (cg + 16 * j < q ? cg + 16 * j : 0) * p;
+        for (int i = 0; i < p; ++i) {
+            const float4 v = reinterpret_cast<const float4 *>(tile + (size_t)i * 64)[rg];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const float sv = Ss[soff[j] + i];
+                acc[j][0] = fmaf(sv, v.x, acc[j][0]);
+                acc[j][1] = fmaf(sv, v.y, acc[j][1]);
+                acc[j][2] = fmaf(sv, v.z, acc[j][2]);
+                acc[j][3] = fmaf(sv, v.w, acc[j][3]);
+            }
+        }
+        const int rowb = row0 + 4 * rg;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const int c = cg + 16 * j;
+            if (c >= q) continue;
+            TO *oc = Out + (size_t)c * ldo;
+            if (std::is_same<TO, float>::value && rowb + 3 < n && ldo % 4 == 0) {
+                *reinterpret_cast<float4 *>(oc + rowb) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (rowb + u < n) oc[rowb + u] = (TO)acc[j][u];
+            }
+        }
+        __syncthreads();                         // everyone is done with this buffer
+    }
+    cp_async_wait<0>();
 }
 
 // Hbar column j: H[i] = h1[i] + h2[i] (i <= j), H[j+1] = sqrt(nrm2[0]), inv[0] = 1/H[j+1].
@@ -560,18 +693,17 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(const T *__restrict__ 
                                                            const typename ST<T>::D *__restrict__ d,
                                                            const typename ST<T>::D *__restrict__ e,
                                                            T *__restrict__ x, T *__restrict__ r, int n) {
-    using D = typename ST<T>::D;
-    __shared__ D ds[130], es[130];
+    __shared__ T ds[130], es[130];      // in the vector type, converted once per block
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        ds[c] = d[c];
-        es[c] = e[c];
+        ds[c] = KS<T>::of(d[c]);
+        es[c] = KS<T>::of(e[c]);
     }
     __syncthreads();
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         T ax = ST<T>::zero(), ar = ST<T>::zero();
         for (int c = 0; c < k; ++c) {
-            ax = axpy(KS<T>::of(ds[c]), B1[(size_t)c * ld + row], ax);
-            ar = axpy(KS<T>::of(es[c]), B2[(size_t)c * ld + row], ar);
+            ax = axpy(ds[c], B1[(size_t)c * ld + row], ax);
+            ar = axpy(es[c], B2[(size_t)c * ld + row], ar);
         }
         x[row] = dadd(x[row], ax);
         r[row] = sub(r[row], ar);
@@ -601,39 +733,6 @@ __global__ void __launch_bounds__(kThreads) k_tsm(const T *__restrict__ In, size
             const T *sc = S + (size_t)c * lds;
             for (int i = 0; i < p; ++i) acc = axpy(sc[i], tile[i * 32 + r], acc);
             if (row < n) Out[(size_t)c * ldo + row] = acc;
-        }
-    }
-}
-
-// Out (n x q) = In (n x p) * S (p x q) for a float32 basis In and a float64 S (column-major,
-// leading dimension lds): S is staged once per block as float32 in shared memory, 32-row
-// tiles of In after it; float32 accumulation; Out is float32 or float64 (converted on store).
-template <class TO>
-__global__ void __launch_bounds__(kThreads) k_tsm_f(const float *__restrict__ In, size_t ldi, int p,
-                                                     const double *__restrict__ S, int lds, int q,
-                                                     TO *__restrict__ Out, size_t ldo, int n) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *Ss = reinterpret_cast<float *>(smem_raw);            // p x q
-    float *tile = Ss + (size_t)p * q;                           // [p][32]
-    for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
-        const int i = e % p, c = e / p;
-        Ss[e] = (float)S[i + (size_t)c * lds];
-    }
-    for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < 32 * p; e += blockDim.x) {
-            const int r = e & 31, c = e >> 5;
-            const int row = row0 + r;
-            tile[c * 32 + r] = row < n ? In[(size_t)c * ldi + row] : 0.0f;
-        }
-        __syncthreads();
-        for (int o = threadIdx.x; o < 32 * q; o += blockDim.x) {
-            const int r = o & 31, c = o >> 5;
-            const int row = row0 + r;
-            float acc = 0.0f;
-            const float *sc = Ss + (size_t)c * p;
-            for (int i = 0; i < p; ++i) acc = fmaf(sc[i], tile[i * 32 + r], acc);
-            if (row < n) Out[(size_t)c * ldo + row] = (TO)acc;
         }
     }
 }
