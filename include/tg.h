@@ -134,6 +134,15 @@ int tg_restrict(const tg_op *op, const void *fine, void *coarse, int ncols, void
  * k harmonic Ritz vectors (k+1 if k would split a complex pair), prolonged to the fine
  * grid, A Y formed on the fine grid (k products) and factored for the projection `proj`
  * (MinRes: CholQR2 of A Y; Galerkin: CholQR2 of Y, H = V^T A V and its LU).
+ * precision TG_F64: the whole coarse phase in float64 (complex128 lattice).  TG_F32_IR
+ * (real operators): the Arnoldi basis, the coarse operator products and the CGS2
+ * orthogonalisation run in float32; the Hessenberg matrix, the restart step (least
+ * squares, harmonic Ritz pairs, recombination matrices), ||b_c|| and the outputs (xc_out,
+ * Y, A Y and its factors) are float64, and the handle also carries float32 copies for
+ * float32 inner cycles.  The coarse solution is then accurate to about float32 rounding
+ * times the coarse condition number (it only serves as the fine initial guess).
+ * Each cycle is captured as a CUDA graph on the second use of its shape and replayed
+ * (not while tg_profile_enable is on); results are identical to direct launches.
  * 1 <= k < m <= 128.  Synchronises `stream`.                                           */
 int tg_coarse_gmresdr(tg_op *op, int transpose, const void *b_fine, int m, int k, int nev,
                       double rtolev, double rtol, int max_cycles, void *xc_out,
