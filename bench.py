@@ -159,6 +159,31 @@ def lattice_operator(tg, L, seed=0, lam_min=1e-3, iters=200):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+# ----------------------------------------------------------------------------- ranks
+def rank_barrier(world, dev):
+    """All ranks meet, then the device is idle (the timed region's bracket)."""
+    import torch
+    if world > 1:
+        torch.distributed.barrier()
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+
+
+def max_over_ranks_of(v, world, dev):
+    """The largest of the ranks' values (the slowest rank's time)."""
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(units_per_rank, ms_max, world):
+    """Whole-job throughput: every rank's units over the slowest rank's time (units/s)."""
+    return world * units_per_rank * 1000.0 / ms_max
+
+
 def run_tg(args, wl, rank, world):
     import numpy as np
     import torch
@@ -230,16 +255,10 @@ def run_tg(args, wl, rank, world):
     split = {}      # precision -> (setup ms, fine-solve ms) per step of the last timed run
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+        rank_barrier(world, dev)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(v, world, dev)
 
     # warm-up (also allocates every workspace)
     for _ in range(args.warmup):
@@ -301,7 +320,7 @@ def run_tg(args, wl, rank, world):
                    "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else 0.0,
                    "tflops": round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4) if v["ms"] > 0 else 0.0}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:10]}
-    value = world * 1000.0 / ms
+    value = weak_scaling_rate(1, ms, world)
     line = {
         "metric": "fine-grid solves/sec to rel. residual 1e-8 (FP64 vs batched FP32+IR) and HBM GB/s",
         "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -478,10 +497,15 @@ def run_batch(args, wl, rank, world):
 
     for _ in range(args.warmup):
         batched_step(rhs, x)
+    rank_barrier(world, dev)
     l0 = tg.tg_launch_count()
     ms, (status, stats) = timed(lambda: batched_step(rhs, x), args.steps)
     launches = (tg.tg_launch_count() - l0) // max(args.steps, 1)
+    rank_barrier(world, dev)
+    ms = max_over_ranks_of(ms, world, dev)
     phase_timed = dict(phase)
+    phase_timed["setup_ms"] = max_over_ranks_of(phase_timed["setup_ms"], world, dev)
+    phase_timed["solve_ms"] = max_over_ranks_of(phase_timed["solve_ms"], world, dev)
     ok = status == tg.TG_OK and all(s["relres"] <= wl["rtol"] for s in stats)
 
     def e2e_step():
@@ -490,7 +514,10 @@ def run_batch(args, wl, rank, world):
         out = batched_step(bd, xd)
         xd.cpu()
         return out
+    rank_barrier(world, dev)
     ms_e2e, _ = timed(e2e_step, 1)
+    rank_barrier(world, dev)
+    ms_e2e = max_over_ranks_of(ms_e2e, world, dev)
 
     # the plain float64 path: per instance, coarse GMRES-DR then its 8 columns one by one
     ops = [tg.Operator("cd2d", N, (b,)) for N, b in zip(Ns, betas)]
@@ -524,8 +551,12 @@ def run_batch(args, wl, rank, world):
             split64["solve"] += 1e3 * (time.perf_counter() - t1)
         return good, mv
     fp64_step()       # warm-up (allocates every workspace)
+    rank_barrier(world, dev)
     ms64, (ok64, mv64) = timed(fp64_step, 1)
-    value = world * nsolves * 1000.0 / ms
+    rank_barrier(world, dev)
+    ms64 = max_over_ranks_of(ms64, world, dev)
+    split64["solve"] = max_over_ranks_of(split64["solve"], world, dev)
+    value = weak_scaling_rate(nsolves, ms, world)
     n_tot = int(sum(batch.sizes))
     line = {
         "metric": "fine-grid solves/sec to rel. residual 1e-8 (FP64 vs batched FP32+IR) and HBM GB/s",
