@@ -412,7 +412,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 template <class E>
-__global__ void __launch_bounds__(kThreads) k_gemv_t_pipe(const E *__restrict__ V, size_t ldv, int ncol,
+__global__ void __launch_bounds__(kThreads, 2) k_gemv_t_pipe(const E *__restrict__ V, size_t ldv, int ncol,
                                                            const E *__restrict__ w, int n, double *part) {
     constexpr int kMaxPerWarp = 17;
     constexpr int R = PipeRows<E>::value;
