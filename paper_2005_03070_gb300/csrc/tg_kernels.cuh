@@ -1,7 +1,8 @@
 // Templated device kernels of the tg library: stencil products, the BiCGStab iteration,
 // residuals, tall-skinny products and reductions.  T is the vector element type:
-// double (float64 path), float (inner iteration of the float32 + refinement path) or
-// cplx (complex128 lattice).
+// double (float64 path), float (inner iteration and coarse Arnoldi basis of the float32 +
+// refinement path) or cplx (complex128 lattice).  Reductions of float vectors accumulate
+// per thread in float and across threads and blocks in double.
 #pragma once
 
 #include <type_traits>

@@ -11,8 +11,13 @@
 // Sections 7.4-7.6): Householder reduction to Hessenberg form, Francis double-shift QR
 // (real matrices, real Schur form with 2 x 2 blocks for complex pairs) or Wilkinson
 // single-shift QR (complex matrices), with accumulated Schur vectors, and eigenvectors
-// by back substitution on the (quasi-)triangular factor.  One thread block of
-// kSmallThreads threads; every matrix lives in a global scratch area (L1/L2 resident).
+// by back substitution on the (quasi-)triangular factor.  The restart kernel is one block
+// of kGdrThreads threads whose work matrices sit in shared memory while they fit (global
+// scratch otherwise); the other kernels are one block of kSmallThreads threads on global
+// scratch.  On this GPU every float64 warp instruction holds its sub-partition's float64
+// unit for tens of cycles whatever the active lanes, and sqrt, division and hypot are
+// long sequences of them: the serial chains (QR sweeps, reflectors) are written to keep
+// few float64 instructions on the critical path (see the Schur form section).
 #include <cfloat>
 #include <cmath>
 #include "tg_small.cuh"

@@ -241,3 +241,57 @@ def test_adjoint_gradient_vs_finite_differences():
     p = np.array([0 * (N + 2) + 5])
     fdb = adjoint.finite_difference(op, b, xstar, p)
     assert abs(grad[p][0] - fdb[0]) <= 1e-5 * max(abs(fdb[0]), 1e-3 * np.abs(fd).max())
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_harmonic_residual_identity(complex_):
+    """The residual of every harmonic Ritz pair is a multiple of one vector: for an eigenpair
+    (theta, g) of H_m + |h|^2 f e_m^T with H_m^H f = e_m, Hbar g - theta [g; 0] = g_m z with
+    z = [-|h|^2 f; h].  The GPU restart kernel evaluates ||.|| this way; here the identity is
+    checked against the explicit residual (oracle) on random and Arnoldi Hessenberg matrices."""
+    m = 24
+    H = gi.random_hessenberg(m, 3)
+    if complex_:
+        H = H + 1j * gi.random_hessenberg(m, 4)
+    H = H + 3.0 * np.vstack([np.eye(m), np.zeros((1, m))])
+    theta, G = harmonic_ritz(H)
+    h = H[m, m - 1]
+    f = np.linalg.solve(H[:m, :m].conj().T, np.eye(m)[:, -1])
+    z = np.concatenate([-abs(h) ** 2 * f, [h]])
+    idx = np.arange(m)
+    explicit = eigen_residuals(H, theta, G, idx)
+    for i in idx:
+        g = G[:, i] / np.linalg.norm(G[:, i])
+        gz = np.concatenate([g, [0.0]])
+        r = H @ g - theta[i] * gz
+        assert np.linalg.norm(r - g[-1] * z) <= 1e-10 * np.linalg.norm(H) * max(1.0, np.linalg.norm(z))
+    assert np.allclose(explicit, np.abs(G[-1, :] / np.linalg.norm(G, axis=0)) * np.linalg.norm(z),
+                       rtol=1e-8, atol=1e-12 * np.linalg.norm(H))
+
+
+def test_finite_difference_equals_plain_subtraction_when_well_conditioned():
+    """The oracle's central difference, formed from the solution change, equals the plain
+    (L(kappa + h) - L(kappa - h)) / 2h of two separately solved losses where the plain form
+    has digits to spare (a small grid and a small loss), and matches the adjoint gradient."""
+    N = 11
+    kap = gi.kappa_grf(N, 5)
+    op = Operator(VARK2D, N, (1.0,), kap)
+    b = gi.rhs(op.n, 21)
+    x0 = adjoint.solve(op, b)
+    xstar = x0 + 1e-2 * gi.random_dense(op.n, 22)           # a small loss, so subtraction keeps digits
+    nodes = gi.kappa_fd_nodes(N, 6, 1)
+    fd = adjoint.finite_difference(op, b, xstar, nodes, rel_step=1e-3)
+    plain = []
+    for p in nodes:
+        dk = 1e-3 * kap[p]
+        vals = []
+        for sgn in (+1, -1):
+            k2 = kap.copy()
+            k2[p] += sgn * dk
+            x = adjoint.solve(Operator(VARK2D, N, (1.0,), k2), b)
+            vals.append(0.5 * float((x - xstar) @ (x - xstar)))
+        plain.append((vals[0] - vals[1]) / (2 * dk))
+    plain = np.array(plain)
+    assert np.allclose(fd, plain, rtol=1e-6, atol=1e-9 * np.abs(plain).max())
+    _, grad, _, _ = adjoint.loss_and_gradient(op, b, xstar)
+    assert np.allclose(grad[nodes], fd, rtol=1e-5, atol=1e-8 * np.abs(fd).max())
