@@ -626,6 +626,10 @@ extern "C" int tg_setup_operator(tg_op **op_out, int kind, const int64_t *dims, 
             op->fine.A = A; op->fine.AT = AT; op->coarse.A = C; op->coarse.AT = CT;
         }
     }
+    for (DevOp *d : {&op->fine.A, &op->fine.AT, &op->coarse.A, &op->coarse.AT}) {
+        d->fN = FastDiv::of((unsigned)std::max(d->N, 1));
+        d->fNN = FastDiv::of((unsigned)std::max<int64_t>((int64_t)d->N * d->N, 1));
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(cuda_status(e, "tg_setup_operator"));

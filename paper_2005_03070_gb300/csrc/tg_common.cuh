@@ -127,10 +127,35 @@ template <class P> __device__ __forceinline__ P warp_sum(P v) {
 enum DevKind { DK_CD2D = 0, DK_CD3D = 1, DK_U1 = 2, DK_VAR2D = 3, DK_U1C = 4 };
 
 // Device-side description of one operator level (passed by value to kernels).
+// floor(n / d) for 0 <= n < 2^32 by one high multiply, add and shifts: unsigned division
+// by an invariant integer (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, unsigned case): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n), q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+// A runtime integer division costs tens of instructions; the stencils need two or three per
+// point, which bounded the float32 kernels.
+struct FastDiv {
+    unsigned m;
+    int s1, s2;
+    __host__ static FastDiv of(unsigned d) {
+        int l = 0;
+        while ((1ull << l) < d) ++l;
+        FastDiv f;
+        f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+        f.s1 = l < 1 ? l : 1;
+        f.s2 = l > 1 ? l - 1 : 0;
+        return f;
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const {
+        const unsigned t = __umulhi(m, n);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+};
+
 struct DevOp {
     int kind;
     int N;          // points per axis (grids) or L (lattice)
     int n;          // unknowns (sites); the host rejects n >= 2^31
+    FastDiv fN, fNN;   // division by N and by N^2 (set with the operator)
     // constant-coefficient stencil (cd2d / cd3d), already including 1/h^2 and beta/(2h)
     double c0, cxm, cxp, cym, cyp, czm, czp;
     // variable coefficient: coefficient arrays [5][n]: diag, west, east, south, north
@@ -167,7 +192,7 @@ template <class LD>
 __device__ __forceinline__ double apply_real_d(const DevOp &op, int idx, LD ld) {
     const int N = op.N;
     if (op.kind == DK_CD2D) {
-        int i = idx % N, j = idx / N;
+        const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
         double y = op.c0 * ld(idx);
         if (i > 0) y = fma(op.cxm, ld(idx - 1), y);
         if (i < N - 1) y = fma(op.cxp, ld(idx + 1), y);
@@ -176,7 +201,8 @@ __device__ __forceinline__ double apply_real_d(const DevOp &op, int idx, LD ld) 
         return y;
     } else if (op.kind == DK_CD3D) {
         int NN = N * N;
-        int i = idx % N, j = (idx / N) % N, k = idx / NN;
+        const int q = (int)op.fN.div((unsigned)idx), k = (int)op.fNN.div((unsigned)idx);
+        const int i = idx - q * N, j = q - k * N;
         double y = op.c0 * ld(idx);
         if (i > 0) y = fma(op.cxm, ld(idx - 1), y);
         if (i < N - 1) y = fma(op.cxp, ld(idx + 1), y);
@@ -186,7 +212,7 @@ __device__ __forceinline__ double apply_real_d(const DevOp &op, int idx, LD ld) 
         if (k < N - 1) y = fma(op.czp, ld(idx + NN), y);
         return y;
     } else {  // DK_VAR2D
-        int i = idx % N, j = idx / N;
+        const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
         const int n = op.n;
         const double *c = op.vc;
         double y = c[idx] * ld(idx);
@@ -202,7 +228,7 @@ template <class LD>
 __device__ __forceinline__ float apply_real_f(const DevOp &op, const DevOp32 &o, int idx, LD ld) {
     const int N = op.N;
     if (op.kind == DK_CD2D) {
-        int i = idx % N, j = idx / N;
+        const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
         float y = o.c0 * ld(idx);
         if (i > 0) y = fmaf(o.cxm, ld(idx - 1), y);
         if (i < N - 1) y = fmaf(o.cxp, ld(idx + 1), y);
@@ -211,7 +237,8 @@ __device__ __forceinline__ float apply_real_f(const DevOp &op, const DevOp32 &o,
         return y;
     } else if (op.kind == DK_CD3D) {
         int NN = N * N;
-        int i = idx % N, j = (idx / N) % N, k = idx / NN;
+        const int q = (int)op.fN.div((unsigned)idx), k = (int)op.fNN.div((unsigned)idx);
+        const int i = idx - q * N, j = q - k * N;
         float y = o.c0 * ld(idx);
         if (i > 0) y = fmaf(o.cxm, ld(idx - 1), y);
         if (i < N - 1) y = fmaf(o.cxp, ld(idx + 1), y);
@@ -221,7 +248,7 @@ __device__ __forceinline__ float apply_real_f(const DevOp &op, const DevOp32 &o,
         if (k < N - 1) y = fmaf(o.czp, ld(idx + NN), y);
         return y;
     } else {
-        int i = idx % N, j = idx / N;
+        const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
         const int n = op.n;
         const float *c = op.vc32;
         float y = c[idx] * ld(idx);

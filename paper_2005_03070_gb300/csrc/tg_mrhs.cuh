@@ -36,7 +36,7 @@ __device__ __forceinline__ VecR<R> applyR(const DevOp &op, const DevOp32 &o, int
     VecR<R> y;
     const int N = op.N;
     if (op.kind == DK_CD2D || op.kind == DK_VAR2D) {
-        const int i = idx % N, j = idx / N;
+        const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
         float c0, cw, ce, cs, cn;
         if (op.kind == DK_CD2D) {
             c0 = o.c0; cw = o.cxm; ce = o.cxp; cs = o.cym; cn = o.cyp;
@@ -64,7 +64,8 @@ __device__ __forceinline__ VecR<R> applyR(const DevOp &op, const DevOp32 &o, int
     }
     // 3D
     const int NN = N * N;
-    const int i = idx % N, j = (idx / N) % N, k = idx / NN;
+    const int q = (int)op.fN.div((unsigned)idx), k = (int)op.fNN.div((unsigned)idx);
+    const int i = idx - q * N, j = q - k * N;
     VecR<R> a = ldR<R>(u, idx);
 #pragma unroll
     for (int r = 0; r < R; ++r) y.v[r] = o.c0 * a.v[r];

@@ -177,6 +177,7 @@ def test_coarse_gmresdr_float32_basis(tg, kind, N, beta):
         x = top.prolong(cu(out[prec][0]))
         status, st = top.solve(bt, x, out[prec][3], precision=prec, rtol=1e-10, ncyc=20, restart_mvps=0)
         assert status == tg.TG_OK, (prec, st)
+        assert st[0]["fp64_cycles"] == 0, st           # the float32 cycles did the work
         xh = host(x)
         assert np.linalg.norm(b - oop.apply(xh)) / np.linalg.norm(b) <= 1e-10
         mv[prec] = st[0]["mvps"]
