@@ -1395,6 +1395,13 @@ static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t
         GdrGraph ent;
         ent.V = V; ent.H = H; ent.j0 = j0; ent.m = m; ent.k = a.k; ent.nev = a.nev; ent.rtolev = a.rtolev;
         ent.transpose = transpose; ent.esz = (int)sizeof(T); ent.gen = op->ws_gen;
+        // a bounded cache: an operator reused with many (k, nev, rtolev) settings drops its
+        // oldest shapes first
+        constexpr size_t kMaxGraphs = 16;
+        if (op->graphs.size() >= kMaxGraphs) {
+            if (op->graphs.front().exec) cudaGraphExecDestroy(op->graphs.front().exec);
+            op->graphs.erase(op->graphs.begin());
+        }
         op->graphs.push_back(ent);
         return body(s_caller);
     }
