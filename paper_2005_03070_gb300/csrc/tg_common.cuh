@@ -226,36 +226,55 @@ __device__ __forceinline__ double apply_real_d(const DevOp &op, int idx, LD ld) 
 
 template <class LD>
 __device__ __forceinline__ float apply_real_f(const DevOp &op, const DevOp32 &o, int idx, LD ld) {
+    // every operand is loaded first (predicated on the boundary tests), then the terms are
+    // summed in the fixed order of the float64 stencil: the loads of a point are in flight
+    // together instead of one per dependent step of the sum (the float32 kernels are bound by
+    // load latency)
     const int N = op.N;
     if (op.kind == DK_CD2D) {
         const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
-        float y = o.c0 * ld(idx);
-        if (i > 0) y = fmaf(o.cxm, ld(idx - 1), y);
-        if (i < N - 1) y = fmaf(o.cxp, ld(idx + 1), y);
-        if (j > 0) y = fmaf(o.cym, ld(idx - N), y);
-        if (j < N - 1) y = fmaf(o.cyp, ld(idx + N), y);
+        const bool bw = i > 0, be = i < N - 1, bs = j > 0, bn = j < N - 1;
+        const float xc = ld(idx);
+        const float xw = bw ? ld(idx - 1) : 0.0f, xe = be ? ld(idx + 1) : 0.0f;
+        const float xs = bs ? ld(idx - N) : 0.0f, xn = bn ? ld(idx + N) : 0.0f;
+        float y = o.c0 * xc;
+        y = bw ? fmaf(o.cxm, xw, y) : y;
+        y = be ? fmaf(o.cxp, xe, y) : y;
+        y = bs ? fmaf(o.cym, xs, y) : y;
+        y = bn ? fmaf(o.cyp, xn, y) : y;
         return y;
     } else if (op.kind == DK_CD3D) {
-        int NN = N * N;
+        const int NN = N * N;
         const int q = (int)op.fN.div((unsigned)idx), k = (int)op.fNN.div((unsigned)idx);
         const int i = idx - q * N, j = q - k * N;
-        float y = o.c0 * ld(idx);
-        if (i > 0) y = fmaf(o.cxm, ld(idx - 1), y);
-        if (i < N - 1) y = fmaf(o.cxp, ld(idx + 1), y);
-        if (j > 0) y = fmaf(o.cym, ld(idx - N), y);
-        if (j < N - 1) y = fmaf(o.cyp, ld(idx + N), y);
-        if (k > 0) y = fmaf(o.czm, ld(idx - NN), y);
-        if (k < N - 1) y = fmaf(o.czp, ld(idx + NN), y);
+        const bool bw = i > 0, be = i < N - 1, bs = j > 0, bn = j < N - 1, bd = k > 0, bu = k < N - 1;
+        const float xc = ld(idx);
+        const float xw = bw ? ld(idx - 1) : 0.0f, xe = be ? ld(idx + 1) : 0.0f;
+        const float xs = bs ? ld(idx - N) : 0.0f, xn = bn ? ld(idx + N) : 0.0f;
+        const float xd = bd ? ld(idx - NN) : 0.0f, xu = bu ? ld(idx + NN) : 0.0f;
+        float y = o.c0 * xc;
+        y = bw ? fmaf(o.cxm, xw, y) : y;
+        y = be ? fmaf(o.cxp, xe, y) : y;
+        y = bs ? fmaf(o.cym, xs, y) : y;
+        y = bn ? fmaf(o.cyp, xn, y) : y;
+        y = bd ? fmaf(o.czm, xd, y) : y;
+        y = bu ? fmaf(o.czp, xu, y) : y;
         return y;
     } else {
         const int j = (int)op.fN.div((unsigned)idx), i = idx - j * N;
         const int n = op.n;
         const float *c = op.vc32;
-        float y = c[idx] * ld(idx);
-        if (i > 0) y = fmaf(c[n + idx], ld(idx - 1), y);
-        if (i < N - 1) y = fmaf(c[2 * n + idx], ld(idx + 1), y);
-        if (j > 0) y = fmaf(c[3 * n + idx], ld(idx - N), y);
-        if (j < N - 1) y = fmaf(c[4 * n + idx], ld(idx + N), y);
+        const bool bw = i > 0, be = i < N - 1, bs = j > 0, bn = j < N - 1;
+        const float xc = ld(idx), cc = c[idx];
+        const float xw = bw ? ld(idx - 1) : 0.0f, cw = bw ? c[n + idx] : 0.0f;
+        const float xe = be ? ld(idx + 1) : 0.0f, ce = be ? c[2 * n + idx] : 0.0f;
+        const float xs = bs ? ld(idx - N) : 0.0f, cs = bs ? c[3 * n + idx] : 0.0f;
+        const float xn = bn ? ld(idx + N) : 0.0f, cn = bn ? c[4 * n + idx] : 0.0f;
+        float y = cc * xc;
+        y = bw ? fmaf(cw, xw, y) : y;
+        y = be ? fmaf(ce, xe, y) : y;
+        y = bs ? fmaf(cs, xs, y) : y;
+        y = bn ? fmaf(cn, xn, y) : y;
         return y;
     }
 }
