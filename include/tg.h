@@ -97,8 +97,8 @@ const char *tg_last_error(void);
  *   ndim   1 (all kinds take one size; the grid dimension follows from kind)
  *   coarse_factor must be 2.
  * The coefficient arrays are copied; the caller may free them after the call.
- * Returns TG_BAD_ARG for an unknown kind, even N (grids), odd L, N < 3, or
- * |beta h / 2| >= 1 is allowed (no closed form needed).                               */
+ * Returns TG_BAD_ARG for an unknown kind, an even N (grids), an odd L (lattice) or
+ * N < 3.  Any beta is accepted: |beta h / 2| >= 1 (no closed-form spectrum) is fine.   */
 int tg_setup_operator(tg_op **op, int kind, const int64_t *dims, int ndim,
                       const double *beta, const double *mass, const void *coeffs,
                       int coarse_factor, void *stream);
@@ -174,8 +174,11 @@ int tg_project(const tg_op *op, const tg_defl *defl, void *x, void *r, void *str
  * the k = 0 case of Example 3).  method TG_BICGSTAB: BiCGStab(ncyc)-Proj(k), Section 4.1:
  * for icyc = 1..ncyc: project; rticyc = min((rtol ||b|| / ||r||)^(1/(ncyc-icyc+1)),
  * (||b|| / ||r||) rtol^(icyc/ncyc)); BiCGStab to rticyc (checked at half and full steps);
- * stop when ||r|| <= rtol ||b||.  ncyc = 0 selects fixed-length restarting: cycles of at
- * most restart_mvps products (Example 2).  method TG_GMRES: GMRES(m3)-Proj(k), Section
+ * stop when ||r|| <= rtol ||b||.  If the ncyc scheduled cycles end above rtol (the paper's
+ * box stops at icyc = ncyc and is silent on this case), later cycles aim at
+ * rticyc = rtol ||b|| / ||r|| (the step-3b value at icyc = ncyc) until convergence or
+ * max_mvps.  ncyc = 0 selects fixed-length restarting: cycles of at most restart_mvps
+ * products (Example 2); with ncyc > 0, restart_mvps > 0 also caps every cycle.  method TG_GMRES: GMRES(m3)-Proj(k), Section
  * 2.2.  The true residual b - A x is recomputed in float64 at every restart.
  * precision TG_F32_IR: each cycle solves the correction equation in float32 (projection
  * included) and adds the correction to the float64 x (iterative refinement).  A cycle

@@ -19,10 +19,16 @@ Readings taken where the paper is silent:
     full step; it also stops after `restart_mvps` operator applications if that cap is
     set (fixed-length restarting, Example 2).
   * Breakdown (rho = 0, <r_hat, v> = 0, <t, t> = 0) ends the cycle early; the restart
-    and the next projection are the remedy.
+    and the next projection are the remedy.  A cycle that ends before its first product
+    ends the solve (nothing would change in the next one).
   * The true residual b - A x is recomputed at every restart.
   * Fixed-length mode (ncyc = 0): cycles of at most `restart_mvps` products, each with
     tolerance rtol ||b|| / ||r||, until convergence or `max_mvps`.
+  * Past ncyc: the box loops icyc = 1..ncyc and says nothing of a solve whose last
+    scheduled cycle ends above rtol (its recursive residual met rticyc while the true
+    residual did not, or a breakdown or product cap ended it).  The solve then goes on
+    with cycles whose tolerance is rtol ||b|| / ||r|| (the value step 3b gives at
+    icyc = ncyc), until convergence or `max_mvps`.
 """
 from __future__ import annotations
 
@@ -186,14 +192,12 @@ def bicgstab_proj(apply, b, x0, defl: Deflation | None, rtol=1e-8, ncyc=20,
     icyc = 0
     while True:
         icyc += 1
-        if ncyc and icyc > ncyc:
-            break
         x, r = project(defl, x, r)                              # step a
         nr = nrm(r)
-        if ncyc:
+        if ncyc and icyc <= ncyc:
             rt = cycle_tolerance(rtol, nb, nr, icyc, ncyc)      # step b
         else:
-            rt = rtol * nb / nr
+            rt = rtol * nb / nr                                 # fixed-length mode, or past ncyc
         hist.append((icyc, nr / nb, rt, mvps))
         cap = restart_mvps if restart_mvps else None
         if cap is not None:
@@ -206,8 +210,10 @@ def bicgstab_proj(apply, b, x0, defl: Deflation | None, rtol=1e-8, ncyc=20,
             break
         if mvps >= max_mvps:
             break
+        if res.mvps == 0:                                       # a cycle without progress
+            break
     relres = nrm(b - apply(x)) / nb
-    return SolveResult(x, relres <= rtol, mvps, icyc if not ncyc else min(icyc, ncyc), relres, hist)
+    return SolveResult(x, relres <= rtol, mvps, icyc, relres, hist)
 
 
 # ----------------------------------------------------------------------------- GMRES

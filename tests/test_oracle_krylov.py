@@ -295,3 +295,70 @@ def test_finite_difference_equals_plain_subtraction_when_well_conditioned():
     assert np.allclose(fd, plain, rtol=1e-6, atol=1e-9 * np.abs(plain).max())
     _, grad, _, _ = adjoint.loss_and_gradient(op, b, xstar)
     assert np.allclose(grad[nodes], fd, rtol=1e-5, atol=1e-8 * np.abs(fd).max())
+
+
+def _hessenberg_with_spectrum(blocks, seed):
+    """A real upper Hessenberg matrix orthogonally similar to the block-diagonal matrix
+    of the given 1x1 / 2x2 blocks (its eigenvalues are those of the blocks), and the
+    orthogonal factor Q with M = Q B Q^T."""
+    import scipy.linalg as sla
+    n = sum(len(b) for b in blocks)
+    B = np.zeros((n, n))
+    i = 0
+    for b in blocks:
+        b = np.atleast_2d(np.asarray(b, dtype=float))
+        B[i:i + len(b), i:i + len(b)] = b
+        i += len(b)
+    Q0 = np.linalg.qr(gi.random_dense((n, n), seed))[0]
+    Hm, Qh = sla.hessenberg(Q0 @ B @ Q0.T, calc_q=True)    # Q0 B Q0^T = Qh Hm Qh^T
+    return Hm, (Qh.T @ Q0)
+
+
+@pytest.mark.parametrize("k,kk_expected", [(1, 1), (2, 2), (3, 4), (4, 4), (5, 5)])
+def test_select_k_conjugate_pair_rule(k, kk_expected):
+    """Section 2.1 keeps k harmonic Ritz vectors; a real basis cannot hold one member of a
+    complex-conjugate pair without its partner, so when the k-th value (order |theta|,
+    Re, Im >= 0 first) is the Im > 0 member, k + 1 are kept.  With h_{m+1,m} = 0 the
+    harmonic Ritz values are the eigenvalues of H_m, fixed here by construction:
+    1, 2, 3 +- i (|.| = sqrt 10), 5, 7."""
+    blocks = [[1.0], [2.0], [[3.0, 1.0], [-1.0, 3.0]], [5.0], [7.0]]
+    Hm, Q = _hessenberg_with_spectrum(blocks, 41)
+    m = Hm.shape[0]
+    Hbar = np.vstack([Hm, np.zeros((1, m))])
+    theta, G = harmonic_ritz(Hbar)
+    idx = select_k(theta, k, True)
+    assert len(idx) == kk_expected
+    want = np.array([1.0, 2.0, 3.0 + 1.0j, 3.0 - 1.0j, 5.0, 7.0])[:kk_expected]
+    assert np.allclose(theta[idx], want, atol=1e-12)
+    # the real basis spans exactly the invariant subspace of the kept values (both partners):
+    # B's invariant subspace of its first kk coordinates, mapped by Q
+    from oracle.gmresdr import real_span_basis
+    Bk = np.linalg.qr(real_span_basis(G, theta, idx, True))[0]
+    assert Bk.shape[1] == kk_expected
+    exact = Q[:, :kk_expected]                  # orthonormal, spans the same subspace
+    s = np.linalg.svd(exact.T @ Bk, compute_uv=False)
+    assert np.min(s) > 1 - 1e-10                  # cosines of the principal angles
+
+
+def test_select_k_complex_problem_keeps_k():
+    """Complex arithmetic needs no partner: exactly k are kept even when the k-th value
+    has a conjugate partner in the spectrum."""
+    blocks = [[1.0], [[3.0, 1.0], [-1.0, 3.0]], [5.0]]
+    Hm, _ = _hessenberg_with_spectrum(blocks, 42)
+    Hbar = np.vstack([Hm, np.zeros((1, Hm.shape[0]))]).astype(np.complex128)
+    theta, _ = harmonic_ritz(Hbar)
+    assert len(select_k(theta, 2, False)) == 2
+
+
+def test_bicgstab_proj_continues_past_ncyc():
+    """Reading of Section 4.1 step 3: when the ncyc scheduled cycles end above rtol (here
+    each is capped at 10 products), the solve goes on with cycles aiming at rtol, and
+    still reaches the dense-LU solution."""
+    op = Operator(CD2D, 15, (1.0,))
+    b = gi.rhs(op.n, 7)
+    res = krylov.bicgstab_proj(op.apply, b, np.zeros(op.n), None, rtol=1e-11, ncyc=2,
+                               restart_mvps=10, max_mvps=20000)
+    assert res.converged and res.cycles > 2
+    assert _rel(res.x, _dense_solve(op, b)) < 1e-8
+    for icyc, relres, rt, _ in res.history[2:]:
+        assert abs(rt * relres - 1e-11) <= 1e-11 * 1e-12

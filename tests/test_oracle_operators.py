@@ -180,3 +180,36 @@ def test_lattice_coarse_gauge_covariant():
     import scipy.sparse as sp
     G = sp.diags(gc)
     assert abs(Ac2 - G @ Ac1 @ G.conj()).max() < 1e-13
+
+
+def _dense_of(op):
+    """The operator's dense matrix, column by column from its matrix-free apply."""
+    n = op.n
+    A = np.zeros((n, n), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        e[j] = 1.0
+        A[:, j] = op.apply(e)
+        e[j] = 0.0
+    return A
+
+
+def test_lattice_tuned_mass_free_field():
+    """Free field (theta = 0): the hopping term's largest eigenvalue is 8 by Fourier
+    (2 sum_mu cos 0), so the mass that puts lambda_min at 1e-3 is exactly 1e-3."""
+    from oracle.operators import lattice_tuned_mass
+    L = 4
+    m = lattice_tuned_mass(np.ones((4, L ** 4), dtype=np.complex128), L, lam_min=1e-3)
+    assert abs(m - 1e-3) < 1e-9
+
+
+@pytest.mark.parametrize("seed", [0, 5])
+def test_lattice_tuned_mass_random_field(seed):
+    """On a random U(1) field the tuned mass makes the smallest eigenvalue of the dense
+    Hermitian matrix (LAPACK eigvalsh) equal to the requested 1e-3."""
+    from oracle.operators import lattice_tuned_mass
+    L = 4
+    links = gi.u1_links(L, seed)
+    m = lattice_tuned_mass(links, L, lam_min=1e-3)
+    lam = np.linalg.eigvalsh(_dense_of(Operator(U1_4D, L, links=links, mass=m)))
+    assert abs(lam[0] - 1e-3) < 1e-9
