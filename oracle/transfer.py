@@ -127,6 +127,25 @@ def restrict(uf: np.ndarray, N: int, dim: int) -> np.ndarray:
     return (P.T @ uf) / 2.0 ** dim
 
 
+def restrict_stencil(uf: np.ndarray, N: int, dim: int) -> np.ndarray:
+    """The same full weighting written as its stencil (vectorised, for large grids): the
+    coarse value at node I is 2^-dim times the sum over the fine nodes 2I + o,
+    o in {-1, 0, 1}^dim, of u(2I + o) times prod_axes w(o_a), w(0) = 1, w(+-1) = 1/2 -- the
+    transpose of the bilinear / trilinear weights (fine values beyond the grid are zero)."""
+    Nc = (N - 1) // 2
+    F = np.zeros((N + 2,) * dim)
+    F[(slice(1, N + 1),) * dim] = uf.reshape((N,) * dim)     # [.., j, i], 0..N+1 with zero borders
+    out = np.zeros((Nc,) * dim)
+    w = {-1: 0.5, 0: 1.0, 1: 0.5}
+    for offs in np.ndindex(*(3,) * dim):
+        o = [v - 1 for v in offs]
+        wt = np.prod([w[v] for v in o])
+        # fine index 2I + o for I = 1..Nc  ->  padded index 2I + o
+        sl = tuple(slice(2 + v, 2 * Nc + 1 + v, 2) for v in o)
+        out += wt * F[sl]
+    return out.reshape(-1) / 2.0 ** dim
+
+
 # ----------------------------------------------------------------------------- lattice
 
 def lattice_prolongation(links: np.ndarray, L: int):

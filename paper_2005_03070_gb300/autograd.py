@@ -35,7 +35,8 @@ def _forward_solve(op, b, c):
 
 
 class TwoGridSolve(torch.autograd.Function):
-    """x = A(kappa)^{-1} b, differentiable with respect to kappa."""
+    """x = A(kappa)^{-1} b, differentiable with respect to kappa and b (dL/db is the
+    adjoint solution lambda)."""
 
     @staticmethod
     def forward(ctx, kappa: torch.Tensor, b: torch.Tensor, cfg: _Cfg):
@@ -67,7 +68,8 @@ class TwoGridSolve(torch.autograd.Function):
                                       restart_mvps=cfg.restart_mvps, precision=cfg.precision)
         if status != tg.TG_OK:
             raise tg.TgError(status, "adjoint two-grid solve")
-        return dk, None, None
+        # x = A^{-1} b, so dL/db = A^{-T} dL/dx = lambda
+        return dk, (lam if ctx.needs_input_grad[1] else None), None
 
 
 def two_grid_solve(kappa, b, N, beta=1.0, m=40, k=20, nev=None, rtolev=1e-2, rtol=1e-8, ncyc=20,

@@ -411,7 +411,10 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
             using E = typename std::conditional<sizeof(T) == 8, double, float>::type;
             constexpr int R = PipeRows<E>::value;
             const size_t smem = (size_t)kPipeStages * (ncol + 1) * R * sizeof(E);
-            smem_attr_once((const void *)k_gemv_t_pipe<E>, max_dyn_smem());
+            if (smem_attr_once((const void *)k_gemv_t_pipe<E>, max_dyn_smem()) != cudaSuccess) {
+                (void)cudaGetLastError();
+                goto plain;      // the limit could not be raised: the non-pipelined kernel needs none
+            }
             const int per_sm = smem <= 100 * 1024 ? 2 : 1;
             const int nchunks = (n + R - 1) / R;
             const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
@@ -422,6 +425,7 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
             return gb;
         }
     }
+plain:
     const int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
     k_gemv_t_part<T><<<std::max(gb, 1), kThreads, 0, s>>>(V, ldv, ncol, w, n, part);
     *used_pipe = false;
@@ -1360,8 +1364,9 @@ static int gdr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, size_t
     auto body = [&](cudaStream_t s) -> int {
         for (int j = j0; j < m; ++j) TG_CHECK((arnoldi_step<T, HT>(op, A, A32, V, ldv, nc, j, H, ldh, s)));
         TG_CHECK_CUDA(cudaMemsetAsync(H2, 0, (size_t)ldh * m * sizeof(HT), s));
-        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<HT>(a, s));
-        TG_LAUNCH_CHECK();
+        cudaError_t le = cudaSuccess;
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, le = launch_gmresdr_restart<HT>(a, s));
+        if (le != cudaSuccess) return cuda_status(le, "launching k_gmresdr_restart (shared-memory limit or launch)");
         // x_c += V_m d
         TG_PROF(P_GEMV_N, (m + 2.0) * nc * sizeof(T), 2.0 * m * nc,
                 k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, ldv, m, a.d, 1.0, xc, nc));
@@ -1691,8 +1696,9 @@ extern "C" int tg_harmonic_ritz(const void *Hbar, int m, int k, int complex_, vo
         a.wi = wi.as<double>(); a.order = ord.as<int>(); a.eres = er.as<double>(); a.P = P.as<T>(); a.Hnew = Hn.as<T>();
         a.cnew = cn.as<T>(); a.work = work.as<T>(); a.ywork = yw.as<cplx>(); a.gwork = gw.as<cplx>();
         a.info = inf.as<GdrInfo>();
-        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, launch_gmresdr_restart<T>(a, s));
-        TG_LAUNCH_CHECK();
+        cudaError_t le = cudaSuccess;
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, le = launch_gmresdr_restart<T>(a, s));
+        if (le != cudaSuccess) return cuda_status(le, "launching k_gmresdr_restart (shared-memory limit or launch)");
         return TG_OK;
     };
     TG_CHECK(complex_ ? launch(cplx{}) : launch(double{}));

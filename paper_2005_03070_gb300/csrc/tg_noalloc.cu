@@ -107,8 +107,7 @@ int run(const void *Hbar, int m, int k, void *theta_out, void *basis_out, void *
     const double one = 1.0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(c, &one, sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return tg::cuda_status(e, "tg_harmonic_ritz_noalloc: clearing the scratch");
-    tg::launch_gmresdr_restart<T>(a, s);
-    e = cudaGetLastError();
+    e = tg::launch_gmresdr_restart<T>(a, s);
     if (e != cudaSuccess) return tg::cuda_status(e, "tg_harmonic_ritz_noalloc: launch");
     tg::GdrInfo info;
     e = cudaMemcpyAsync(&info, a.info, sizeof(info), cudaMemcpyDeviceToHost, s);

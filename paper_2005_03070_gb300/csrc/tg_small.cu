@@ -1289,7 +1289,7 @@ void launch_small_gemv(const D *M, int k, const D *c, D *out, cudaStream_t s) {
     k_small_gemv<D><<<1, kSmallThreads, 0, s>>>(M, k, c, out);
 }
 template <class T>
-void launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
+cudaError_t launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
     GdrArgs<T> a = a_in;
     // W, Z, B (T) and the eigenvector work Y (complex, m x m) go to shared memory in that
     // order while they fit
@@ -1301,8 +1301,13 @@ void launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
         smem += parts[q];
         a.smem = q + 1;
     }
-    if (smem > 48 * 1024) smem_attr_once((const void *)k_gmresdr_restart<T>, (int)kGdrSmemMax);
+    if (smem > 48 * 1024) {
+        // without the raised limit the launch would fail; report the attribute call instead
+        const cudaError_t e = smem_attr_once((const void *)k_gmresdr_restart<T>, (int)kGdrSmemMax);
+        if (e != cudaSuccess) return e;
+    }
     k_gmresdr_restart<T><<<1, kGdrThreads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 template <class D>
 void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s) {
@@ -1317,7 +1322,7 @@ void launch_givens_solve(const D *H, int ldh, const D *g, D *y, const GivensStat
     template void launch_chol_inv<D>(const D *, int, D *, D *, int *, cudaStream_t);                 \
     template void launch_inverse<D>(const D *, int, D *, D *, int *, cudaStream_t);                  \
     template void launch_small_gemv<D>(const D *, int, const D *, D *, cudaStream_t);                \
-    template void launch_gmresdr_restart<D>(const GdrArgs<D> &, cudaStream_t);                       \
+    template cudaError_t launch_gmresdr_restart<D>(const GdrArgs<D> &, cudaStream_t);                \
     template void launch_givens_step<D>(D *, int, int, D *, D *, D *, GivensState *, cudaStream_t);  \
     template void launch_givens_solve<D>(const D *, int, const D *, D *, const GivensState *, cudaStream_t);
 TG_INST(double)

@@ -55,7 +55,9 @@ struct GivensState {
 template <class D> void launch_chol_inv(const D *G, int k, D *R, D *Rinv, int *info, cudaStream_t s);
 template <class D> void launch_inverse(const D *H, int k, D *Hinv, D *W, int *info, cudaStream_t s);
 template <class D> void launch_small_gemv(const D *M, int k, const D *c, D *out, cudaStream_t s);
-template <class T> void launch_gmresdr_restart(const GdrArgs<T> &a, cudaStream_t s);
+// Returns the error of raising the kernel's shared-memory limit (nothing is launched then)
+// or of the launch itself.
+template <class T> cudaError_t launch_gmresdr_restart(const GdrArgs<T> &a, cudaStream_t s);
 template <class D>
 void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s);
 template <class D>

@@ -213,3 +213,13 @@ def test_lattice_tuned_mass_random_field(seed):
     m = lattice_tuned_mass(links, L, lam_min=1e-3)
     lam = np.linalg.eigvalsh(_dense_of(Operator(U1_4D, L, links=links, mass=m)))
     assert abs(lam[0] - 1e-3) < 1e-9
+
+
+@pytest.mark.parametrize("N,dim", [(15, 2), (9, 3), (31, 2)])
+def test_restrict_stencil_equals_sparse_transpose(N, dim):
+    """The vectorised full-weighting stencil is the transpose of the entry-by-entry sparse
+    prolongation divided by 2^dim."""
+    u = gi.random_dense(N ** dim, 9)
+    a = transfer.restrict(u, N, dim)
+    b = transfer.restrict_stencil(u, N, dim)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
