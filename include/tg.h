@@ -48,7 +48,7 @@ extern "C" {
 #define TG_SYNC_TIMEOUT  7  /* a bounded device-side wait gave up                          */
 
 /* ----------------------------------------------------------------------- enumerations */
-enum { TG_CD2D = 0, TG_CD3D = 1, TG_U1_4D = 2, TG_VARK2D = 3 };   /* operator kinds     */
+enum { TG_CD2D = 0, TG_CD3D = 1, TG_U1_4D = 2, TG_VARK2D = 3, TG_EXP2D = 4 };  /* operator kinds */
 enum { TG_BICGSTAB = 0, TG_GMRES = 1 };                            /* fine-grid method   */
 enum { TG_PROJ_MINRES = 0, TG_PROJ_GALERKIN = 1 };                 /* projection kind    */
 enum { TG_F64 = 0, TG_F32_IR = 1 };                                /* precision mode     */
@@ -86,14 +86,20 @@ const char *tg_last_error(void);
  * Builds the fine operator and its coarse partner (Section 3: the coarse problem is the
  * same PDE at h_c = 2h, Example 1 and Example 4; for the lattice, the Galerkin product
  * P^H A P of the 2^4 block-transport prolongation).
- *   kind   TG_CD2D   -u_xx - u_yy + beta[0] u_x, 5-point centred, dims = {N}, N odd
- *          TG_CD3D   -Lap u + beta . grad u, 7-point centred, dims = {N}, N odd, beta[3]
+ *   kind   TG_CD2D   -u_xx - u_yy + beta[0] u_x + c u, 5-point centred, dims = {N}, N odd
+ *          TG_CD3D   -Lap u + beta . grad u + c u, 7-point centred, dims = {N}, N odd, beta[3]
+ *          TG_EXP2D  -exp(beta[2] x y)(u_xx + u_yy) + beta[0] u_x + beta[1] u_y + c u,
+ *                    5-point centred at x = i h, y = j h, dims = {N}, N odd, beta[3]
+ *                    (Example 1: beta = {40, 40, 5}, c = 0)
  *          TG_VARK2D -div(kappa grad u) + beta[0] u_x, dims = {N}, N odd;
  *                    coeffs = device float64 kappa on the (N+2)^2 node grid, index
  *                    j*(N+2)+i; faces use the arithmetic mean of their two nodes
  *          TG_U1_4D  (m+8) psi(x) - sum_mu [U_mu(x) psi(x+mu) + conj(U_mu(x-mu)) psi(x-mu)],
  *                    dims = {L}, L even, periodic; *mass = m; coeffs = device complex128
  *                    links U[mu][site], mu = 0..3
+ *   mass   lattice: the mass m (required); TG_CD2D / TG_CD3D / TG_EXP2D: the reaction
+ *          coefficient c (NULL means 0; Example 4's Helmholtz operator -Lap u - 100^2 u is
+ *          TG_CD2D with beta = 0, c = -1e4), on the coarse level too; TG_VARK2D: NULL or 0
  *   ndim   1 (all kinds take one size; the grid dimension follows from kind)
  *   coarse_factor must be 2.
  * The coefficient arrays are copied; the caller may free them after the call.
@@ -194,6 +200,25 @@ int tg_solve_proj(tg_op *op, const tg_defl *defl, int method, int precision,
                   const void *b, void *x, int nrhs, double rtol, int ncyc,
                   int restart_mvps, int m3, int64_t max_mvps, tg_stats *stats,
                   void *stream);
+
+/* IDR(ncyc)-Proj(k) (Section 4.1: the box's step 3 runs "BiCGStab or IDR"; the paper's
+ * IDR is van Gijzen and Sonneveld's biorthogonal IDR(s), default s = 4): the schedule of
+ * tg_solve_proj (projection, rticyc, cycles past ncyc, true residual at every restart) with
+ * cycles of IDR(s).  Each cycle starts from e = 0 with G = U = 0, M = I, omega = 1; omega
+ * is the residual-minimising <t, r> / <t, t>, enlarged by kappa / |rho| when the cosine
+ * |rho| = |<t, r>| / (||t|| ||r||) is below kappa (0.7 is the published default; 0 turns
+ * the safeguard off).  Convergence (||r|| <= rticyc ||r_cycle_start||) and the product cap
+ * are checked after every residual update.
+ *   s   shadow-space dimension, 1..8 (and < n)
+ *   P   device, n x s column-major (float64 / complex128): the shadow columns, linearly
+ *       independent (random normal is the usual choice); the library orthonormalises them
+ *       by CholQR2 (the QR factor with a positive-diagonal R) and uses the same space in
+ *       every cycle.  TG_BAD_ARG when they are numerically dependent.
+ * precision must be TG_F64 (float64 / complex128).  Other arguments, stats and the return
+ * value as for tg_solve_proj.  Synchronises `stream`.                                   */
+int tg_solve_idr(tg_op *op, const tg_defl *defl, int precision, const void *b, void *x, int nrhs,
+                 double rtol, int ncyc, int restart_mvps, int s, const void *P, double kappa,
+                 int64_t max_mvps, tg_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ adjoint (added form)
  * Not in the paper: the gradient of a loss L(x) through the solve A(kappa) x = b for

@@ -10,6 +10,9 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
   cycle_tolerance                     Section 4.1, step 3b.
   bicgstab_proj                       BiCGStab(ncyc)-Proj(k), Section 4.1.
   gmres_cycle / gmres_proj            GMRES(m)-Proj(k), Section 2.2.
+  idr_cycle / idr_proj                IDR(s) (van Gijzen and Sonneveld's biorthogonal IDR,
+                                      the paper's other fine-grid solver) and
+                                      IDR(ncyc)-Proj(k), Section 4.1.
 
 Readings taken where the paper is silent:
   * ||r0|| in the cycle tolerance is ||b||, so "relative residual" is ||b - Ax|| / ||b||.
@@ -283,3 +286,138 @@ def gmres_proj(apply, b, x0, defl: Deflation | None, m=20, rtol=1e-8, max_mvps=1
         r = b - apply(x)
     relres = nrm(b - apply(x)) / nb
     return SolveResult(x, relres <= rtol, mvps, cyc, relres, hist)
+
+
+# ----------------------------------------------------------------------------- IDR(s)
+
+def shadow_space(P_raw: np.ndarray) -> np.ndarray:
+    """Orthonormal shadow space from random columns: the Q of the QR factorisation whose R
+    has a positive diagonal (unique, so that any orthonormalisation with that convention
+    gives the same P)."""
+    Q, R = np.linalg.qr(P_raw)
+    sg = np.sign(np.real(np.diag(R)))
+    sg[sg == 0] = 1.0
+    return Q * sg[None, :]
+
+
+def idr_cycle(apply, x, r, P, target, max_mvps=None, kappa=0.7):
+    """One cycle of IDR(s) from e = 0 on A e = r (updating copies of x and r), in the
+    biorthogonal form of van Gijzen and Sonneveld (the IDR the paper runs, Section 4.1; s
+    = P's column count, P orthonormal).  Stops when ||r|| <= target (checked after every
+    residual update), on breakdown (M_kk = 0 or omega = 0), or after max_mvps products.
+
+    Each round of s + 1 products:
+      f = P^H r
+      for k = 1..s:
+        c = M[k:, k:]^{-1} f[k:]              (M lower triangular)
+        v = r - G[:, k:] c
+        U[:, k] = U[:, k:] c + omega v
+        G[:, k] = A U[:, k]                   (one product)
+        for i < k:  a = P_i^H G_k / M_ii;  G_k -= a G_i;  U_k -= a U_i
+        M[k:, k] = P[:, k:]^H G_k
+        beta = f_k / M_kk;  r -= beta G_k;  x += beta U_k
+        f[k+1:] -= beta M[k+1:, k]
+      t = A r                                  (one product)
+      omega = <t, r> / <t, t>, enlarged to omega kappa / |rho| when the cosine
+              rho = <t, r> / (||t|| ||r||) is below kappa in modulus
+      x += omega r;  r -= omega t
+    """
+    x = x.copy()
+    r = r.copy()
+    n, s = P.shape
+    G = np.zeros((n, s), dtype=r.dtype)
+    U = np.zeros((n, s), dtype=r.dtype)
+    M = np.eye(s, dtype=r.dtype)
+    om = 1.0
+    mvps = 0
+    hist = []
+
+    def cap_hit():
+        return max_mvps is not None and mvps >= max_mvps
+
+    if nrm(r) <= target:
+        return CycleResult(x, r, 0, 0, True, False, hist)
+    rounds = 0
+    while True:
+        f = P.conj().T @ r
+        for k in range(s):
+            c = np.linalg.solve(np.tril(M[k:, k:]), f[k:])
+            v = r - G[:, k:] @ c
+            U[:, k] = U[:, k:] @ c + om * v
+            G[:, k] = apply(U[:, k])
+            mvps += 1
+            for i in range(k):
+                a = dot(P[:, i], G[:, k]) / M[i, i]
+                G[:, k] = G[:, k] - a * G[:, i]
+                U[:, k] = U[:, k] - a * U[:, i]
+            M[k:, k] = P[:, k:].conj().T @ G[:, k]
+            if abs(M[k, k]) < TINY:
+                return CycleResult(x, r, mvps, rounds, False, True, hist)
+            beta = f[k] / M[k, k]
+            r = r - beta * G[:, k]
+            x = x + beta * U[:, k]
+            nr = nrm(r)
+            hist.append(nr)
+            if nr <= target:
+                return CycleResult(x, r, mvps, rounds, True, False, hist)
+            if cap_hit():
+                return CycleResult(x, r, mvps, rounds, False, False, hist)
+            if k + 1 < s:
+                f[k + 1:] = f[k + 1:] - beta * M[k + 1:, k]
+        t = apply(r)
+        mvps += 1
+        tt = dot(t, t).real
+        if tt < TINY:
+            return CycleResult(x, r, mvps, rounds, False, True, hist)
+        tr = dot(t, r)
+        om = tr / tt
+        rho = abs(tr) / np.sqrt(tt * dot(r, r).real)
+        if rho < kappa:
+            om = om * kappa / rho
+        if abs(om) < TINY:
+            return CycleResult(x, r, mvps, rounds, False, True, hist)
+        x = x + om * r
+        r = r - om * t
+        rounds += 1
+        nr = nrm(r)
+        hist.append(nr)
+        if nr <= target:
+            return CycleResult(x, r, mvps, rounds, True, False, hist)
+        if cap_hit():
+            return CycleResult(x, r, mvps, rounds, False, False, hist)
+
+
+def idr_proj(apply, b, x0, defl: Deflation | None, P, rtol=1e-8, ncyc=20, restart_mvps=None,
+             max_mvps=100000, kappa=0.7):
+    """IDR(ncyc)-Proj(k), Section 4.1 step 3 with IDR(s) in place of BiCGStab: the same
+    cycle schedule (projection, rticyc, a cycle of IDR(s) to rticyc, true residual), with
+    the same readings as bicgstab_proj (||r0|| = ||b||, cycles past ncyc aim at rtol, one
+    shadow space P for every cycle)."""
+    nb = nrm(b)
+    x = x0.copy()
+    r = b - apply(x)
+    mvps = 0
+    hist = []
+    icyc = 0
+    while True:
+        icyc += 1
+        x, r = project(defl, x, r)                              # step a
+        nr = nrm(r)
+        if ncyc and icyc <= ncyc:
+            rt = cycle_tolerance(rtol, nb, nr, icyc, ncyc)      # step b
+        else:
+            rt = rtol * nb / nr
+        hist.append((icyc, nr / nb, rt, mvps))
+        cap = max_mvps - mvps
+        if restart_mvps:
+            cap = min(cap, restart_mvps)
+        res = idr_cycle(apply, x, r, P, rt * nr, cap, kappa)    # step c
+        x = res.x
+        mvps += res.mvps
+        r = b - apply(x)
+        if nrm(r) <= rtol * nb:                                 # step d
+            break
+        if mvps >= max_mvps or res.mvps == 0:
+            break
+    relres = nrm(b - apply(x)) / nb
+    return SolveResult(x, relres <= rtol, mvps, icyc, relres, hist)

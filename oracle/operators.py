@@ -6,9 +6,14 @@ The paper solves A x = b from finite-difference discretisations of PDEs on the u
 square with zero Dirichlet boundaries (Section 1; Example 1, Section 3; Example 4,
 Section 5.1) and a lattice operator (Example 8, Section 5.4).  The operators here:
 
-  cd2d   -u_xx - u_yy + beta u_x, 5-point centred differences, h = 1/(N+1)
-  cd3d   -Lap u + beta . grad u, 7-point centred differences
+  cd2d   -u_xx - u_yy + beta u_x + c u, 5-point centred differences, h = 1/(N+1)
+  cd3d   -Lap u + beta . grad u + c u, 7-point centred differences
+  exp2d  -exp(gamma x y)(u_xx + u_yy) + beta_x u_x + beta_y u_y + c u at x = i h, y = j h
+         (Example 1: gamma = 5, beta = (40, 40)); beta = (beta_x, beta_y, gamma)
   vark2d -div(kappa grad u) + beta u_x, kappa on the nodes, arithmetic face means
+
+The reaction coefficient c (field `mass` on the grid kinds, 0 by default) gives the
+Helmholtz operator of Example 4, -u_xx - u_yy - 100^2 u, as cd2d with beta = 0, c = -1e4.
   u1_4d  (m + 8) psi(x) - sum_mu [U_mu(x) psi(x+mu) + conj(U_mu(x-mu)) psi(x-mu)],
          periodic L^4 lattice, complex128
 
@@ -26,22 +31,24 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-CD2D, CD3D, U1_4D, VARK2D = 0, 1, 2, 3
+CD2D, CD3D, U1_4D, VARK2D, EXP2D = 0, 1, 2, 3, 4
 
 
 @dataclass
 class Operator:
     kind: int
     N: int                       # interior points per axis (grids) or L (lattice)
-    beta: tuple = (0.0,)         # convection speeds (cd2d/vark2d: (bx,), cd3d: (bx, by, bz))
+    beta: tuple = (0.0,)         # convection speeds (cd2d/vark2d: (bx,), cd3d: (bx, by, bz),
+                                 # exp2d: (bx, by, gamma))
     kappa: np.ndarray | None = None   # vark2d: (N+2)^2 node values
     links: np.ndarray | None = None   # u1_4d: (4, L^4) complex links
-    mass: float = 0.0                 # u1_4d
+    mass: float = 0.0                 # u1_4d: the mass m; cd2d/cd3d/exp2d: reaction coefficient c
+    transpose: bool = False           # exp2d: apply A^T (the other kinds form A^T by their parameters)
     _sparse: object = field(default=None, repr=False)
 
     @property
     def n(self) -> int:
-        if self.kind == CD2D or self.kind == VARK2D:
+        if self.kind in (CD2D, VARK2D, EXP2D):
             return self.N * self.N
         if self.kind == CD3D:
             return self.N ** 3
@@ -57,16 +64,19 @@ class Operator:
         against the sparse transpose by the tests, not assumed."""
         if self.kind == U1_4D:
             raise ValueError("the lattice operator is Hermitian; use the conjugate transpose")
-        return Operator(self.kind, self.N, tuple(-b for b in self.beta), self.kappa, None, 0.0)
+        if self.kind == EXP2D:
+            return Operator(EXP2D, self.N, self.beta, None, None, self.mass, transpose=not self.transpose)
+        return Operator(self.kind, self.N, tuple(-b for b in self.beta), self.kappa, None, self.mass)
 
     def apply(self, u: np.ndarray) -> np.ndarray:
         return {CD2D: _apply_cd2d, CD3D: _apply_cd3d, VARK2D: _apply_vark2d,
-                U1_4D: _apply_u1}[self.kind](self, u)
+                U1_4D: _apply_u1, EXP2D: _apply_exp2d}[self.kind](self, u)
 
     def sparse(self):
         if self._sparse is None:
             self._sparse = {CD2D: _assemble_cd2d, CD3D: _assemble_cd3d,
-                            VARK2D: _assemble_vark2d, U1_4D: _assemble_u1}[self.kind](self)
+                            VARK2D: _assemble_vark2d, U1_4D: _assemble_u1,
+                            EXP2D: _assemble_exp2d}[self.kind](self)
         return self._sparse
 
 
@@ -81,8 +91,37 @@ def _apply_cd2d(op: Operator, u):
     c = U[1:-1, 1:-1]
     xm, xp = U[1:-1, :-2], U[1:-1, 2:]
     ym, yp = U[:-2, 1:-1], U[2:, 1:-1]
-    Au = (4.0 * c - xm - xp - ym - yp) / h**2 + bx * (xp - xm) / (2.0 * h)
+    Au = (4.0 * c - xm - xp - ym - yp) / h**2 + bx * (xp - xm) / (2.0 * h) + op.mass * c
     return Au.reshape(-1)
+
+
+def _exp2d_a(N, gamma):
+    """The diffusion coefficient exp(gamma x y) at the interior nodes, [j, i], x = i h, y = j h."""
+    h = 1.0 / (N + 1)
+    t = np.arange(1, N + 1) * h
+    return np.exp(gamma * t[:, None] * t[None, :])     # symmetric in (x, y)
+
+
+def _apply_exp2d(op: Operator, u):
+    """A u = a (-Lap_h u) + bx D_x u + by D_y u + c u with a = exp(gamma x y); the transpose
+    is A^T u = -Lap_h (a u) - bx D_x u - by D_y u + c u (-Lap_h is symmetric, the centred
+    differences antisymmetric)."""
+    N = op.N
+    h = 1.0 / (N + 1)
+    bx, by, gamma = op.beta
+    a = _exp2d_a(N, gamma)
+    uu = u.reshape(N, N)
+    U = np.zeros((N + 2, N + 2))
+    U[1:-1, 1:-1] = a * uu if op.transpose else uu
+    lap = (4.0 * U[1:-1, 1:-1] - U[1:-1, :-2] - U[1:-1, 2:] - U[:-2, 1:-1] - U[2:, 1:-1]) / h**2
+    V = np.zeros((N + 2, N + 2))
+    V[1:-1, 1:-1] = uu
+    conv = (bx * (V[1:-1, 2:] - V[1:-1, :-2]) + by * (V[2:, 1:-1] - V[:-2, 1:-1])) / (2.0 * h)
+    if op.transpose:
+        Au = lap - conv
+    else:
+        Au = a * lap + conv
+    return (Au + op.mass * uu).reshape(-1)
 
 
 def _apply_cd3d(op: Operator, u):
@@ -96,7 +135,7 @@ def _apply_cd3d(op: Operator, u):
     ym, yp = U[1:-1, :-2, 1:-1], U[1:-1, 2:, 1:-1]
     zm, zp = U[:-2, 1:-1, 1:-1], U[2:, 1:-1, 1:-1]
     Au = ((6.0 * c - xm - xp - ym - yp - zm - zp) / h**2
-          + (bx * (xp - xm) + by * (yp - ym) + bz * (zp - zm)) / (2.0 * h))
+          + (bx * (xp - xm) + by * (yp - ym) + bz * (zp - zm)) / (2.0 * h) + op.mass * c)
     return Au.reshape(-1)
 
 
@@ -135,7 +174,7 @@ def _assemble_cd2d(op: Operator):
     jj, ii = np.meshgrid(np.arange(1, N + 1), np.arange(1, N + 1), indexing="ij")
     ii, jj = ii.reshape(-1), jj.reshape(-1)
     me = idx(ii, jj)
-    coefs = [((0, 0), 4.0 / h**2),
+    coefs = [((0, 0), 4.0 / h**2 + op.mass),
              ((-1, 0), -1.0 / h**2 - bx / (2 * h)), ((1, 0), -1.0 / h**2 + bx / (2 * h)),
              ((0, -1), -1.0 / h**2), ((0, 1), -1.0 / h**2)]
     for (di, dj), cval in coefs:
@@ -155,7 +194,7 @@ def _assemble_cd3d(op: Operator):
     ii, jj, kk = ii.reshape(-1), jj.reshape(-1), kk.reshape(-1)
     me = idx(ii, jj, kk)
     d = -1.0 / h**2
-    coefs = [((0, 0, 0), 6.0 / h**2),
+    coefs = [((0, 0, 0), 6.0 / h**2 + op.mass),
              ((-1, 0, 0), d - bx / (2 * h)), ((1, 0, 0), d + bx / (2 * h)),
              ((0, -1, 0), d - by / (2 * h)), ((0, 1, 0), d + by / (2 * h)),
              ((0, 0, -1), d - bz / (2 * h)), ((0, 0, 1), d + bz / (2 * h))]
@@ -168,6 +207,28 @@ def _assemble_cd3d(op: Operator):
     n = N ** 3
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(n, n))
+
+
+def _assemble_exp2d(op: Operator):
+    """Entry by entry: row (i, j) holds a(i, j) (4, -1, -1, -1, -1) / h^2 for the diffusion and
+    -+ b / (2h) for the convection towards the -/+ neighbour, plus c on the diagonal; the
+    transpose is assembled as the transpose of that matrix."""
+    N = op.N
+    h = 1.0 / (N + 1)
+    bx, by, gamma = op.beta
+    idx = _grid_coo(N, 2)
+    rows, cols, vals = [], [], []
+    for j in range(1, N + 1):
+        for i in range(1, N + 1):
+            a = np.exp(gamma * (i * h) * (j * h))
+            me = idx(i, j)
+            rows.append(me); cols.append(me); vals.append(4.0 * a / h**2 + op.mass)
+            for (di, dj, b) in ((-1, 0, -bx), (1, 0, bx), (0, -1, -by), (0, 1, by)):
+                ni, nj = i + di, j + dj
+                if 1 <= ni <= N and 1 <= nj <= N:
+                    rows.append(me); cols.append(idx(ni, nj)); vals.append(-a / h**2 + b / (2 * h))
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(N * N, N * N))
+    return M.T.tocsr() if op.transpose else M
 
 
 def _assemble_vark2d(op: Operator):
@@ -258,7 +319,7 @@ def coarse_operator(op: Operator) -> Operator:
         K = op.kappa.reshape(op.N + 2, op.N + 2)
         kc = K[::2, ::2].reshape(-1).copy()
         assert kc.size == (Nc + 2) ** 2
-    return Operator(op.kind, Nc, op.beta, kc, None, 0.0)
+    return Operator(op.kind, Nc, op.beta, kc, None, op.mass, transpose=op.transpose)
 
 
 def cd2d_eigenvalues(N: int, beta: float) -> np.ndarray:

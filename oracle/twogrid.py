@@ -19,7 +19,7 @@ import scipy.sparse.linalg as spla
 
 from . import krylov, transfer
 from .gmresdr import gmresdr
-from .operators import CD2D, CD3D, U1_4D, VARK2D, Operator, coarse_operator
+from .operators import CD2D, CD3D, EXP2D, U1_4D, VARK2D, Operator, coarse_operator
 
 
 @dataclass
@@ -32,7 +32,7 @@ class CoarseLevel:
 
 
 def coarse_level(op: Operator) -> CoarseLevel:
-    if op.kind in (CD2D, VARK2D):
+    if op.kind in (CD2D, VARK2D, EXP2D):
         opc = coarse_operator(op)
         return CoarseLevel(opc, opc.apply, lambda v: transfer.prolong2d(v, opc.N),
                            lambda v: transfer.restrict(v, op.N, 2), opc.n)

@@ -16,6 +16,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "tg_idr.cuh"
 #include "tg_kernels.cuh"
 #include "tg_mrhs.cuh"
 #include "tg_setup.cuh"
@@ -77,12 +78,12 @@ static int tiles_grid(int64_t n, int per_sm) {
 enum ProfClass {
     P_APPLY, P_DOT, P_RESIDUAL, P_BI_INIT, P_BI_V, P_BI_S, P_BI_T, P_BI_X, P_GEMV_T, P_SUM_PART, P_GEMV_N,
     P_PROJ, P_TSM, P_GRAM, P_SMALL, P_GDR_RESTART, P_SCALE, P_TRANSFER, P_SETUP, P_CONVERT, P_GRAD, P_GIVENS,
-    P_NOOP, P_REORTH, P_COUNT
+    P_NOOP, P_REORTH, P_IDR_MV, P_IDR_UPD, P_COUNT
 };
 static const char *kProfName[P_COUNT] = {
     "apply", "dot", "residual", "bicg_init", "bicg_v", "bicg_s", "bicg_t", "bicg_x", "gemv_t", "sum_part",
     "gemv_n", "proj_update", "tsm", "gram", "small_dense", "gmresdr_restart", "scale", "transfer", "setup",
-    "convert", "kappa_grad", "givens", "bicg_noop", "reorth_pass"};
+    "convert", "kappa_grad", "givens", "bicg_noop", "reorth_pass", "idr_apply", "idr_update"};
 
 struct ProfRec {
     int cls;
@@ -200,6 +201,7 @@ enum Slot {
     S_GORD, S_GERES, S_GWORK, S_GY, S_GG, S_GINFO, S_GTMP, S_GB, S_GH1, S_GHV,
     S_FV, S_FH, S_FCS, S_FSN, S_FG, S_FY, S_FSTATE, S_BC,
     S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC, S_XBAK,
+    S_IG, S_IU, S_IP, S_IPR, S_IPRI, S_IT, S_IINFO,
     S_COUNT
 };
 
@@ -275,6 +277,23 @@ static int wsx(tg_op *op, Slot s, size_t bytes) {
     return rc;
 }
 
+// Layout of the small result area (bytes): device scalars of the solvers.  Vectors of
+// coefficients hold up to kMaxCols complex entries (kMaxCols * 16 <= 8192).
+struct SmallArea {
+    static constexpr size_t bistate = 0;        // BiState
+    static constexpr size_t dot_out = 1024;     // dot_host results
+    static constexpr size_t res_out = 2048;     // true-residual norms
+    static constexpr size_t idr = 4096;         // IdrState
+    static constexpr size_t proj_c = 8192;      // projection coefficients c
+    static constexpr size_t proj_d = 16384;     // projection coefficients d
+    static constexpr size_t arn_h1 = 24576;     // Arnoldi: V^H w, first pass (and ||w||^2)
+    static constexpr size_t arn_h2 = 32768;     // Arnoldi: second pass
+    static constexpr size_t arn_nrm = 40960;    // ||w||^2, 1 / ||w|| (+ 32), re-orthogonalisation flag (+ 64)
+    static constexpr size_t gmres_inv = 41984;  // 1 / ||r|| of a GMRES cycle
+    static constexpr size_t bytes = 1 << 16;
+};
+static_assert(kMaxCols * 16 <= 8192, "coefficient vectors must fit their slots");
+
 // reduction scratch: partials (sized generously), a ticket, a small result area
 // The ticket is zeroed on the stream that will use it (a plain cudaMemset runs on the
 // legacy stream, which streams created non-blocking do not wait for).
@@ -284,7 +303,7 @@ static int red_ready(tg_op *op, size_t part_bytes, cudaStream_t s) {
         TG_CHECK(wsx(op, S_TICKET, 64));
         TG_CHECK_CUDA(cudaMemsetAsync(op->ws[S_TICKET].p, 0, 64, s));
     }
-    TG_CHECK(wsx(op, S_SMALL, 1 << 16));
+    TG_CHECK(wsx(op, S_SMALL, SmallArea::bytes));
     TG_CHECK(op->pin.ensure(1 << 16));
     return TG_OK;
 }
@@ -304,7 +323,7 @@ static int dot_host(tg_op *op, const T *a, const T *b, int n, double *aa, typena
     using D = typename ST<T>::D;
     TG_CHECK(red_ready(op, 0, s));
     int g = grid_for(n, 4);
-    D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 1024);
+    D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + SmallArea::dot_out);
     TG_PROF(P_DOT, (b ? 2.0 : 1.0) * n * sizeof(T), (b ? 4.0 : 2.0) * n, k_dot<T><<<g, kThreads, 0, s>>>(a, b, n, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out));
     TG_LAUNCH_CHECK();
     TG_CHECK(readback(op, out, 2 * sizeof(D), s));
@@ -369,7 +388,13 @@ static int tsm(const T *In, size_t ldi, int p, const T *S, int lds, int q, T *Ou
 template <class TO>
 static int tsm_f(const float *In, size_t ldi, int p, const double *S, int lds, int q, TO *Out, size_t ldo, int n,
                  cudaStream_t s) {
-    TG_ARG(q >= 1 && q <= 128 && p >= 1, "float32 tall-skinny product: need 1 <= q <= 128 (q=%d)", q);
+    TG_ARG(q >= 1 && p >= 1, "float32 tall-skinny product: need q, p >= 1 (q=%d, p=%d)", q, p);
+    if (q > 128) {                 // column groups of at most 128 output columns
+        for (int c0 = 0; c0 < q; c0 += 128)
+            TG_CHECK(tsm_f<TO>(In, ldi, p, S + (size_t)c0 * lds, lds, std::min(128, q - c0), Out + (size_t)c0 * ldo,
+                               ldo, n, s));
+        return TG_OK;
+    }
     TG_ARG(!((uintptr_t)In & 15) && ldi % 4 == 0 && ldi >= (size_t)(n + 63) / 64 * 64,
            "float32 tall-skinny product: In needs 16-byte aligned columns and 64-row padding");
     TG_ARG(((uintptr_t)Out & 15) == 0, "float32 tall-skinny product: Out must be 16-byte aligned");
@@ -399,7 +424,7 @@ static bool pipe_ok(const T *V, size_t ldv, const T *w, int n, int ncol) {
     const int R = sizeof(T) == 8 ? PipeRows<double>::value : PipeRows<float>::value;
     if ((ldv * sizeof(T)) % 16 || ldv < (size_t)((n + R - 1) / R) * R) return false;
     if (((uintptr_t)V | (uintptr_t)w) & 15) return false;
-    return ncol + 1 <= 136 && n >= R;
+    return ncol >= 1 && n >= R;
 }
 
 // partials of V^H w into part (gb blocks); returns gb
@@ -410,7 +435,8 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
         if (pipe_ok<T>(V, ldv, w, n, ncol)) {
             using E = typename std::conditional<sizeof(T) == 8, double, float>::type;
             constexpr int R = PipeRows<E>::value;
-            const size_t smem = (size_t)kPipeStages * (ncol + 1) * R * sizeof(E);
+            const int ngr = (ncol + kPipeCols - 1) / kPipeCols;            // column groups (grid y)
+            const size_t smem = (size_t)kPipeStages * (std::min(ncol, kPipeCols) + 1) * R * sizeof(E);
             if (smem_attr_once((const void *)k_gemv_t_pipe<E>, max_dyn_smem()) != cudaSuccess) {
                 (void)cudaGetLastError();
                 goto plain;      // the limit could not be raised: the non-pipelined kernel needs none
@@ -418,7 +444,7 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
             const int per_sm = smem <= 100 * 1024 ? 2 : 1;
             const int nchunks = (n + R - 1) / R;
             const int gb = std::max(1, std::min(nchunks, num_sms() * per_sm));
-            k_gemv_t_pipe<E><<<gb, kThreads, smem, s>>>(reinterpret_cast<const E *>(V), ldv, ncol,
+            k_gemv_t_pipe<E><<<dim3(gb, ngr), kThreads, smem, s>>>(reinterpret_cast<const E *>(V), ldv, ncol,
                                                         reinterpret_cast<const E *>(w), n,
                                                         reinterpret_cast<double *>(part));
             *used_pipe = true;
@@ -427,7 +453,8 @@ static int gemv_t_part_launch(const T *V, size_t ldv, int ncol, const T *w, int 
     }
 plain:
     const int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
-    k_gemv_t_part<T><<<std::max(gb, 1), kThreads, 0, s>>>(V, ldv, ncol, w, n, part);
+    k_gemv_t_part<T><<<dim3(std::max(gb, 1), (ncol + kGemvTCols - 1) / kGemvTCols), kThreads, 0, s>>>(V, ldv, ncol,
+                                                                                                    w, n, part);
     *used_pipe = false;
     return std::max(gb, 1);
 }
@@ -446,27 +473,37 @@ static int gemv_t(tg_op *op, const T *V, size_t ldv, int ncol, const T *w, int n
     return TG_OK;
 }
 
-// G = A^H B (k x k, device D array, column-major)
+// G = A^H B (k x k, device D array, column-major), sym = 1 for A = B (upper triangle
+// computed, the lower one mirrored)
 template <class T, int EPT>
 static int gram_ept(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int sym, typename ST<T>::D *G,
                     cudaStream_t s) {
     using D = typename ST<T>::D;
-    int gb = tiles_grid(n, 1);
-    TG_CHECK(red_ready(op, (size_t)gb * k * k * sizeof(D), s));
-    size_t smem = (size_t)2 * 32 * k * sizeof(T);
-    TG_CHECK(set_smem<T>((const void *)k_gram_part<T, EPT>, smem));
-    TG_PROF(P_GRAM, (A == B ? 1.0 : 2.0) * k * n * sizeof(T), (sym ? 1.0 * k * (k + 1) : 2.0 * k * k) * n * (sizeof(T) == 16 ? 4 : 1), k_gram_part<T, EPT><<<gb, kThreads, smem, s>>>(A, B, ld, k, n, sym, wsp<D>(op, S_PART)));
+    const int nent = sym ? k * (k + 1) / 2 : k * k;
+    const int gy = (nent + kThreads * EPT - 1) / (kThreads * EPT);
+    const int gx = std::max(1, tiles_grid(n, 4) / gy);
+    TG_CHECK(red_ready(op, (size_t)gx * nent * sizeof(D) + (size_t)nent * sizeof(D), s));
+    D *part = wsp<D>(op, S_PART);
+    D *packed = part + (size_t)gx * nent;
+    const size_t smem = (size_t)(A == B ? 1 : 2) * 33 * k * sizeof(T);
+    TG_CHECK(set_smem<T>((const void *)k_gram_packed<T, EPT>, smem));
+    TG_PROF(P_GRAM, (A == B ? 1.0 : 2.0) * k * n * sizeof(T), 2.0 * nent * n * (sizeof(T) == 16 ? 4 : 1),
+            k_gram_packed<T, EPT><<<dim3(gx, gy), kThreads, smem, s>>>(A, B, ld, k, n, sym, nent, part));
     TG_LAUNCH_CHECK();
-    TG_PROF(P_SUM_PART, (double)gb * k * k * sizeof(D), (double)gb * k * k, k_sum_part<D><<<(k * k + 7) / 8, 256, 0, s>>>(wsp<D>(op, S_PART), gb, k * k, G, 0));
+    TG_PROF(P_SUM_PART, (double)gx * nent * sizeof(D), (double)gx * nent,
+            k_sum_part<D><<<(nent + 7) / 8, 256, 0, s>>>(part, gx, nent, packed, 0));
+    TG_PROF(P_SMALL, 0, 0, k_gram_unpack<D><<<(nent + 255) / 256, 256, 0, s>>>(packed, k, sym, G));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
 template <class T>
 static int gram(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int sym, typename ST<T>::D *G,
                 cudaStream_t s) {
-    if (k * k <= 4 * kThreads) return gram_ept<T, 4>(op, A, B, ld, k, n, sym, G, s);
-    if (k * k <= 16 * kThreads) return gram_ept<T, 16>(op, A, B, ld, k, n, sym, G, s);
-    return gram_ept<T, 64>(op, A, B, ld, k, n, sym, G, s);
+    const int nent = sym ? k * (k + 1) / 2 : k * k;
+    if (nent <= kThreads) return gram_ept<T, 1>(op, A, B, ld, k, n, sym, G, s);
+    if (nent <= 2 * kThreads) return gram_ept<T, 2>(op, A, B, ld, k, n, sym, G, s);
+    if (nent <= 4 * kThreads) return gram_ept<T, 4>(op, A, B, ld, k, n, sym, G, s);
+    return gram_ept<T, 8>(op, A, B, ld, k, n, sym, G, s);
 }
 
 // CholQR2: A (n x k) = Q R.  Writes Q (n x k), R and Rinv (k x k, device D).
@@ -513,11 +550,12 @@ extern "C" const char *tg_status_string(int status) {
 
 extern "C" const char *tg_last_error(void) { return g_err.c_str(); }
 
-static void const_coefs(DevOp &A, DevOp &AT, DevOp32 &A32, DevOp32 &AT32, int kind, int N, const double *beta) {
+static void const_coefs(DevOp &A, DevOp &AT, DevOp32 &A32, DevOp32 &AT32, int kind, int N, const double *beta,
+                        double shift) {
     const double h = 1.0 / (N + 1);
     const double d = -1.0 / (h * h);
     const int dim = kind == TG_CD3D ? 3 : 2;
-    A.c0 = 2.0 * dim / (h * h);
+    A.c0 = 2.0 * dim / (h * h) + shift;
     double bx = beta[0], by = dim == 3 ? beta[1] : 0.0, bz = dim == 3 ? beta[2] : 0.0;
     A.cxm = d - bx / (2 * h);
     A.cxp = d + bx / (2 * h);
@@ -543,7 +581,8 @@ extern "C" int tg_setup_operator(tg_op **op_out, int kind, const int64_t *dims, 
     *op_out = nullptr;
     TG_ARG(dims != nullptr && ndim >= 1, "dims must give the grid size");
     TG_ARG(coarse_factor == 2, "coarse_factor must be 2 (got %d)", coarse_factor);
-    TG_ARG(kind == TG_CD2D || kind == TG_CD3D || kind == TG_U1_4D || kind == TG_VARK2D, "unknown operator kind %d", kind);
+    TG_ARG(kind == TG_CD2D || kind == TG_CD3D || kind == TG_U1_4D || kind == TG_VARK2D || kind == TG_EXP2D,
+           "unknown operator kind %d", kind);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = dims[0];
     tg_op *op = new tg_op();
@@ -590,8 +629,30 @@ extern "C" int tg_setup_operator(tg_op **op_out, int kind, const int64_t *dims, 
         op->Nc = (int)(N - 1) / 2;
         op->n = (int)nn;
         op->nc = dim == 3 ? op->Nc * op->Nc * op->Nc : op->Nc * op->Nc;
-        for (int a = 0; a < dim && a < 3; ++a) op->beta[a] = beta[a];
-        if (kind == TG_VARK2D) {
+        for (int a = 0; a < 3; ++a) op->beta[a] = (a < dim || kind == TG_EXP2D) ? beta[a] : 0.0;
+        op->mass = mass ? *mass : 0.0;      // reaction coefficient (diagonal shift) of the grid PDEs
+        if (kind == TG_VARK2D && op->mass != 0.0) { set_error("TG_VARK2D takes no shift"); return fail(TG_BAD_ARG); }
+        if (kind == TG_EXP2D) {
+            const int n = op->n, nc = op->nc;
+            if ((rc = op->coef.ensure((size_t)5 * n * 8)) || (rc = op->coef32.ensure((size_t)5 * n * 4)) ||
+                (rc = op->coefT.ensure((size_t)5 * n * 8)) || (rc = op->coefT32.ensure((size_t)5 * n * 4)) ||
+                (rc = op->ccoef.ensure((size_t)5 * nc * 8)) || (rc = op->ccoef32.ensure((size_t)5 * nc * 4)) ||
+                (rc = op->ccoefT.ensure((size_t)5 * nc * 8)) || (rc = op->ccoefT32.ensure((size_t)5 * nc * 4)))
+                return fail(rc);
+            const double bx = beta[0], by = beta[1], gm = beta[2], sh = op->mass;
+            launch_exp2d_coefs(grid_for(n, 8), s, (int)N, bx, by, gm, sh, 0, op->coef.as<double>(), op->coef32.as<float>());
+            launch_exp2d_coefs(grid_for(n, 8), s, (int)N, bx, by, gm, sh, 1, op->coefT.as<double>(), op->coefT32.as<float>());
+            launch_exp2d_coefs(grid_for(nc, 8), s, op->Nc, bx, by, gm, sh, 0, op->ccoef.as<double>(), op->ccoef32.as<float>());
+            launch_exp2d_coefs(grid_for(nc, 8), s, op->Nc, bx, by, gm, sh, 1, op->ccoefT.as<double>(), op->ccoefT32.as<float>());
+            DevOp A{};
+            A.kind = DK_VAR2D; A.N = (int)N; A.n = n;
+            DevOp AT = A, C = A, CT = A;
+            A.vc = op->coef.as<double>(); A.vc32 = op->coef32.as<float>();
+            AT.vc = op->coefT.as<double>(); AT.vc32 = op->coefT32.as<float>();
+            C.N = op->Nc; C.n = nc; C.vc = op->ccoef.as<double>(); C.vc32 = op->ccoef32.as<float>();
+            CT.N = op->Nc; CT.n = nc; CT.vc = op->ccoefT.as<double>(); CT.vc32 = op->ccoefT32.as<float>();
+            op->fine.A = A; op->fine.AT = AT; op->coarse.A = C; op->coarse.AT = CT;
+        } else if (kind == TG_VARK2D) {
             if (!coeffs) { set_error("TG_VARK2D needs kappa"); return fail(TG_BAD_ARG); }
             const int NP = (int)N + 2, NPc = op->Nc + 2;
             const int n = op->n, nc = op->nc;
@@ -625,8 +686,8 @@ extern "C" int tg_setup_operator(tg_op **op_out, int kind, const int64_t *dims, 
             A.n = AT.n = op->n;
             C.N = CT.N = op->Nc;
             C.n = CT.n = op->nc;
-            const_coefs(A, AT, op->fine.A32, op->fine.AT32, kind, (int)N, op->beta);
-            const_coefs(C, CT, op->coarse.A32, op->coarse.AT32, kind, op->Nc, op->beta);
+            const_coefs(A, AT, op->fine.A32, op->fine.AT32, kind, (int)N, op->beta, op->mass);
+            const_coefs(C, CT, op->coarse.A32, op->coarse.AT32, kind, op->Nc, op->beta, op->mass);
             op->fine.A = A; op->fine.AT = AT; op->coarse.A = C; op->coarse.AT = CT;
         }
     }
@@ -775,8 +836,8 @@ static int project_impl(tg_op *op, const tg_defl *df, const T *W, const T *B1, c
     using D = typename ST<T>::D;
     const int kk = df->kk;
     TG_CHECK(red_ready(op, 0, s));
-    D *cvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192);
-    D *dvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 8192 + 4096);
+    D *cvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + SmallArea::proj_c);
+    D *dvec = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + SmallArea::proj_d);
     TG_CHECK(gemv_t<T>(op, W, n, kk, r, n, cvec, s));
     TG_PROF(P_SMALL, 0, 2.0 * kk * kk, launch_small_gemv<D>(df->M.as<D>(), kk, cvec, dvec, s));
     TG_LAUNCH_CHECK();
@@ -816,7 +877,7 @@ static int defl_create(tg_op *op, int transpose, int kk, int proj, int precision
 extern "C" int tg_defl_from_basis(tg_op *op, int transpose, const void *Y, int k, int proj, int precision,
                                   tg_defl **defl_out, void *stream) {
     TG_ARG(op && Y && defl_out, "NULL argument");
-    TG_ARG(k >= 1 && k <= 128, "k must be in 1..128 (got %d)", k);
+    TG_ARG(k >= 1 && k <= kMaxM, "k must be in 1..%d (got %d)", kMaxM, k);
     TG_ARG(proj == TG_PROJ_MINRES || proj == TG_PROJ_GALERKIN, "bad projection kind");
     TG_ARG(precision == TG_F64 || precision == TG_F32_IR, "bad precision");
     TG_ARG(!(op->cplx_ && precision == TG_F32_IR), "the lattice path is complex128 only");
@@ -909,7 +970,7 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     TG_CHECK(red_ready(op, (size_t)g * 4 * sizeof(D), s));
     D *part = wsp<D>(op, S_PART);
     unsigned *tk = wsp<unsigned>(op, S_TICKET);
-    BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL));
+    BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL) + SmallArea::bistate);
     TG_PROF(P_BI_INIT, 3.0 * n * sizeof(T), 2.0 * n, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
     TG_LAUNCH_CHECK();
     int chunk = 2;
@@ -1005,7 +1066,7 @@ static int true_residual(tg_op *op, const DevOp &A, const T *b, const T *x, T *r
     const int n = A.n;
     const int g = grid_for(n, 8);
     TG_CHECK(red_ready(op, (size_t)g * 2 * sizeof(D), s));
-    D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + 2048);
+    D *out = reinterpret_cast<D *>(wsp<char>(op, S_SMALL) + SmallArea::res_out);
     double xb, fl;
     op_cost(A, &xb, &fl);
     TG_PROF(P_RESIDUAL, (3.0 * sizeof(T) + xb) * n, (fl + 6) * n, k_residual<T><<<g, kThreads, 0, s>>>(A, b, x, r, wsp<D>(op, S_PART), wsp<unsigned>(op, S_TICKET), out));
@@ -1156,6 +1217,141 @@ static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const doub
     return status;
 }
 
+// ----------------------------------------------------------------------------- IDR(s)
+struct IdrCfg {
+    int s;
+    double kappa;
+    const void *P_in;      // caller's n x s shadow columns (orthonormalised once per solve)
+};
+
+// One IDR(s) cycle on A e = r (updating x and r); device-resident scalars, status read
+// once per batch of rounds.
+template <class T>
+static int idr_cycle(tg_op *op, const DevOp &A, T *x, T *r, int n, const T *P, int sd, double kappa, double target2,
+                     int cap, CycleOut *out, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    const size_t ld = (size_t)n;
+    TG_CHECK(wsx(op, S_IG, (size_t)n * sd * sizeof(T)));
+    TG_CHECK(wsx(op, S_IU, (size_t)n * sd * sizeof(T)));
+    TG_CHECK(wsx(op, S_IT, (size_t)n * sizeof(T)));
+    T *G = wsp<T>(op, S_IG), *U = wsp<T>(op, S_IU), *t = wsp<T>(op, S_IT);
+    const int g = grid_for(n, 8);
+    TG_CHECK(red_ready(op, (size_t)g * (kIdrMaxS + 1) * sizeof(D) + sizeof(IdrState<D>), s));
+    D *part = wsp<D>(op, S_PART);
+    unsigned *tk = wsp<unsigned>(op, S_TICKET);
+    IdrState<D> *st = reinterpret_cast<IdrState<D> *>(wsp<char>(op, S_SMALL) + SmallArea::idr);
+    const double es = sizeof(T);
+    double xb, fl;
+    op_cost(A, &xb, &fl);
+    const double cf = sizeof(T) == 16 ? 4.0 : 1.0;
+    TG_PROF(P_IDR_UPD, (1.0 + sd) * n * es, 2.0 * (sd + 1) * n * cf,
+            k_idr_init<T><<<g, kThreads, 0, s>>>(r, P, ld, n, sd, target2, cap, kappa, part, tk, st));
+    TG_LAUNCH_CHECK();
+    int batch = 1, launched = 0;
+    IdrState<D> h{};
+    while (true) {
+        for (int b = 0; b < batch; ++b) {
+            const int first = launched + b == 0;
+            for (int k = 0; k < sd; ++k) {
+                TG_PROF(P_IDR_UPD, (2.0 + (first ? 0.0 : 2.0 * (sd - k))) * n * es, 4.0 * (sd - k) * n * cf,
+                        k_idr_u<T><<<g, kThreads, 0, s>>>(r, G, U, ld, n, k, first, st));
+                TG_PROF(P_IDR_MV, (2.0 + sd) * n * es + xb * n, (fl + 2.0 * sd * cf) * n,
+                        k_idr_g<T><<<g, kThreads, 0, s>>>(A, U, G, P, ld, k, part, tk, st));
+                TG_PROF(P_IDR_UPD, (2.0 * k + 8.0) * n * es, (4.0 * k + 6.0) * n * cf,
+                        k_idr_upd<T><<<g, kThreads, 0, s>>>(G, U, ld, r, x, n, k, part, tk, st));
+            }
+            TG_PROF(P_IDR_MV, 2.0 * n * es + xb * n, (fl + 6.0 * cf) * n,
+                    k_idr_t<T><<<g, kThreads, 0, s>>>(A, r, t, part, tk, st));
+            TG_PROF(P_IDR_UPD, (5.0 + sd) * n * es, (4.0 + 2.0 * (sd + 1)) * n * cf,
+                    k_idr_xr<T><<<g, kThreads, 0, s>>>(x, r, t, P, ld, n, part, tk, st));
+        }
+        TG_LAUNCH_CHECK();
+        launched += batch;
+        TG_CHECK(readback(op, st, sizeof(IdrState<D>), s));
+        memcpy(&h, op->pin.p, sizeof(h));
+        if (h.status != 0) break;
+        if ((int64_t)launched * (sd + 1) > (int64_t)cap + 2 * (sd + 1)) {   // the cap test ends the cycle first
+            set_error("IDR cycle exceeded its product cap");
+            return TG_SYNC_TIMEOUT;
+        }
+        const int left = (h.cap - h.mvps) / (sd + 1) + 1;
+        batch = std::max(1, std::min(std::min(2 * batch, left), 16));
+    }
+    out->mvps = h.mvps;
+    out->iters = h.rounds;
+    out->status = h.status;
+    out->rr = h.rr;
+    return TG_OK;
+}
+
+// IDR(ncyc)-Proj(k) in float64 / complex128: the Section 4.1 schedule of solve_bicg64 with
+// IDR(s) cycles.  The shadow space is the caller's n x s columns orthonormalised by CholQR2
+// (positive-diagonal R), the same for every cycle.
+template <class T>
+static int solve_idr64(tg_op *op, const tg_defl *df, const T *b, T *x, const SolveCfg &cfg, const IdrCfg &ic,
+                       tg_stats *st, cudaStream_t s) {
+    const DevOp &A = pick(op, TG_FINE, 0);
+    const int n = op->n, sv = ic.s;
+    TG_CHECK(wsx(op, S_R64, (size_t)n * sizeof(T)));
+    TG_CHECK(wsx(op, S_IP, (size_t)n * sv * sizeof(T)));
+    TG_CHECK(wsx(op, S_IPR, (size_t)sv * sv * sizeof(T)));
+    TG_CHECK(wsx(op, S_IPRI, (size_t)sv * sv * sizeof(T)));
+    TG_CHECK(wsx(op, S_IINFO, 64));
+    TG_CHECK_CUDA(cudaMemsetAsync(op->ws[S_IINFO].p, 0, 64, s));
+    T *P = wsp<T>(op, S_IP);
+    TG_CHECK(cholqr2<T>(op, static_cast<const T *>(ic.P_in), sv, n, P, wsp<T>(op, S_IPR), wsp<T>(op, S_IPRI),
+                        wsp<int>(op, S_IINFO), s));
+    {
+        int info[2] = {0, 0};
+        TG_CHECK(readback(op, wsp<int>(op, S_IINFO), 2 * sizeof(int), s));
+        memcpy(info, op->pin.p, sizeof(info));
+        if (info[0] || info[1]) {
+            set_error("the shadow columns are linearly dependent (Cholesky of P^H P failed)");
+            return TG_BAD_ARG;
+        }
+    }
+    T *r = wsp<T>(op, S_R64);
+    double nr, nb;
+    TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
+    int64_t mvps = 0;
+    int cyc = 0;
+    int status = TG_NOT_CONVERGED;
+    if (!std::isfinite(nr)) status = TG_NAN;
+    else if (nb == 0.0 || nr <= cfg.rtol * nb) status = TG_OK;
+    while (status == TG_NOT_CONVERGED) {
+        ++cyc;
+        const bool sched = cfg.ncyc && cyc <= cfg.ncyc;
+        if (df && df->kk > 0) {
+            TG_CHECK(project64<T>(op, df, x, r, s));
+            double rr;
+            TG_CHECK(dot_host<T>(op, r, nullptr, n, &rr, nullptr, s));
+            nr = sqrt(rr);
+        }
+        const double rt = sched ? cycle_tol(cfg.rtol, nb, nr, cyc, cfg.ncyc) : cfg.rtol * nb / nr;
+        hist_push(st, nr / nb, rt, mvps);
+        int64_t cap64 = cfg.max_mvps - mvps;
+        if (cfg.restart_mvps > 0 && cap64 > cfg.restart_mvps) cap64 = cfg.restart_mvps;
+        if (cap64 > INT_MAX / 2) cap64 = INT_MAX / 2;
+        CycleOut co;
+        TG_CHECK(idr_cycle<T>(op, A, x, r, n, P, sv, ic.kappa, (rt * nr) * (rt * nr), (int)cap64, &co, s));
+        mvps += co.mvps;
+        if (co.status == 4) { status = TG_NAN; break; }
+        TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
+        if (!std::isfinite(nr)) { status = TG_NAN; break; }
+        if (nr <= cfg.rtol * nb) { status = TG_OK; break; }
+        if (mvps >= cfg.max_mvps) break;
+        if (co.mvps == 0) { status = TG_BREAKDOWN; break; }
+    }
+    if (st) {
+        st->mvps = mvps;
+        st->cycles = cyc;
+        st->relres = nb > 0 ? nr / nb : 0.0;
+        st->status = status;
+        st->vops = mvps * (4 * sv + 8) / (sv + 1);
+    }
+    return status;
+}
+
 // ----------------------------------------------------------------------------- Arnoldi (CGS2)
 // Extends V (ld ldv, columns 0..j orthonormal) by column j+1 = A v_j orthogonalised; writes
 // Hbar column j (ld ldh).  Two classical Gram-Schmidt passes as tall-skinny products.
@@ -1184,11 +1380,11 @@ static int arnoldi_step(tg_op *op, const DevOp &A, const DevOp32 &A32, T *V, siz
     TG_CHECK(launch_apply<T>(A, A32, V + (size_t)j * ldv, w, s));
     TG_CHECK(red_ready(op, 0, s));
     char *sm = wsp<char>(op, S_SMALL);
-    D *h1 = reinterpret_cast<D *>(sm + 16384);           // j+2 entries: V_j^H w and ||w||^2
-    D *h2 = reinterpret_cast<D *>(sm + 16384 + 4096);
-    double *nrm = reinterpret_cast<double *>(sm + 16384 + 8192);
+    D *h1 = reinterpret_cast<D *>(sm + SmallArea::arn_h1);   // j+2 entries: V_j^H w and ||w||^2
+    D *h2 = reinterpret_cast<D *>(sm + SmallArea::arn_h2);
+    double *nrm = reinterpret_cast<double *>(sm + SmallArea::arn_nrm);
     double *inv = nrm + 4;
-    int *flag = reinterpret_cast<int *>(sm + 16384 + 8192 + 64);
+    int *flag = reinterpret_cast<int *>(sm + SmallArea::arn_nrm + 64);
     const int g = grid_for(n, 8);
     const int gb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)num_sms() * 8);
     const int ncol = j + 1;
@@ -1261,7 +1457,7 @@ static int solve_gmres64(tg_op *op, int transpose, const tg_defl *df, const T *b
         GivensState h0{};
         h0.target = cfg.rtol * nb;
         h0.resid = nr;
-        double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
+        double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + SmallArea::gmres_inv);
         double hinv = 1.0 / nr;
         TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
         TG_CHECK_CUDA(cudaMemcpyAsync(gs, &h0, sizeof(h0), cudaMemcpyHostToDevice, s));
@@ -1315,7 +1511,7 @@ extern "C" int tg_solve_proj(tg_op *op, const tg_defl *defl, int method, int pre
     TG_ARG(rtol > 0 && rtol < 1, "rtol must be in (0, 1)");
     TG_ARG(ncyc >= 0 && restart_mvps >= 0, "ncyc and restart_mvps must be >= 0");
     TG_ARG(ncyc > 0 || restart_mvps > 0 || method == TG_GMRES, "fixed-length restarting needs restart_mvps > 0");
-    TG_ARG(method != TG_GMRES || (m3 >= 1 && m3 <= 128), "m3 must be in 1..128");
+    TG_ARG(method != TG_GMRES || (m3 >= 1 && m3 <= kMaxM), "m3 must be in 1..%d", kMaxM);
     TG_ARG(max_mvps > 0, "max_mvps must be > 0");
     TG_ARG(!defl || (defl->n == op->n && !defl->transposed), "deflation handle does not match this operator");
     TG_ARG(!defl || precision == TG_F64 || defl->precision == TG_F32_IR,
@@ -1342,6 +1538,41 @@ extern "C" int tg_solve_proj(tg_op *op, const tg_defl *defl, int method, int pre
             rc = op->cplx_ ? solve_bicg64<cplx>(op, 0, defl, (const cplx *)bc, (cplx *)xc, cfg, st, s)
                            : solve_bicg64<double>(op, 0, defl, (const double *)bc, (double *)xc, cfg, st, s);
         }
+        if (rc != TG_OK && worst == TG_OK) worst = rc;
+        if (rc == TG_CUDA_ERROR || rc == TG_OOM || rc == TG_BAD_ARG) return rc;
+    }
+    return worst;
+}
+
+extern "C" int tg_solve_idr(tg_op *op, const tg_defl *defl, int precision, const void *b, void *x, int nrhs,
+                            double rtol, int ncyc, int restart_mvps, int s, const void *P, double kappa,
+                            int64_t max_mvps, tg_stats *stats, void *stream) {
+    TG_ARG(op && b && x && P, "NULL argument");
+    TG_ARG(nrhs >= 1, "nrhs must be >= 1");
+    TG_ARG(precision == TG_F64, "IDR(s)-Proj runs in float64 / complex128");
+    TG_ARG(s >= 1 && s <= kIdrMaxS, "s must be in 1..%d (got %d)", kIdrMaxS, s);
+    TG_ARG(s < op->n, "s must be smaller than the problem size");
+    TG_ARG(rtol > 0 && rtol < 1, "rtol must be in (0, 1)");
+    TG_ARG(ncyc >= 0 && restart_mvps >= 0, "ncyc and restart_mvps must be >= 0");
+    TG_ARG(ncyc > 0 || restart_mvps > 0, "fixed-length restarting needs restart_mvps > 0");
+    TG_ARG(kappa >= 0 && kappa < 1, "kappa must be in [0, 1)");
+    TG_ARG(max_mvps > 0, "max_mvps must be > 0");
+    TG_ARG(!defl || (defl->n == op->n && !defl->transposed), "deflation handle does not match this operator");
+    cudaStream_t st = (cudaStream_t)stream;
+    SolveCfg cfg{rtol, ncyc, restart_mvps, 0, max_mvps};
+    IdrCfg ic{s, kappa, P};
+    int worst = TG_OK;
+    const size_t es = elem_size(op);
+    for (int c = 0; c < nrhs; ++c) {
+        tg_stats *sp = stats ? stats + c : nullptr;
+        if (sp) {
+            sp->history_len = 0;
+            sp->coarse_mvps = 0;
+        }
+        const char *bc = (const char *)b + (size_t)c * op->n * es;
+        char *xc = (char *)x + (size_t)c * op->n * es;
+        const int rc = op->cplx_ ? solve_idr64<cplx>(op, defl, (const cplx *)bc, (cplx *)xc, cfg, ic, sp, st)
+                                 : solve_idr64<double>(op, defl, (const double *)bc, (double *)xc, cfg, ic, sp, st);
         if (rc != TG_OK && worst == TG_OK) worst = rc;
         if (rc == TG_CUDA_ERROR || rc == TG_OOM || rc == TG_BAD_ARG) return rc;
     }
@@ -1505,7 +1736,7 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         TG_LAUNCH_CHECK();
     } else {
         TG_CHECK_CUDA(cudaMemcpyAsync(V, bc, (size_t)nc * es, cudaMemcpyDeviceToDevice, s));
-        double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + 30000);
+        double *inv = reinterpret_cast<double *>(wsp<char>(op, S_SMALL) + SmallArea::gmres_inv);
         double hinv = 1.0 / nbc;
         TG_CHECK_CUDA(cudaMemcpyAsync(inv, &hinv, sizeof(double), cudaMemcpyHostToDevice, s));
         TG_PROF(P_SCALE, 2.0 * nc * sizeof(T), nc, k_scale_by<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, nc, inv));
@@ -1556,8 +1787,8 @@ static int gmresdr_impl(tg_op *op, int transpose, const void *b_fine, int m, int
         {
             using DD = typename ST<T>::D;
             T *w = V + (size_t)kk * ldv;
-            DD *h1 = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384);
-            DD *nrm = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + 16384 + 8192);
+            DD *h1 = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + SmallArea::arn_h1);
+            DD *nrm = reinterpret_cast<DD *>(wsp<char>(op, S_SMALL) + SmallArea::arn_nrm);
             TG_CHECK(gemv_t<T>(op, V, ldv, kk, w, nc, h1, s));
             TG_PROF(P_GEMV_N, (kk + 2.0) * nc * sizeof(T), 2.0 * kk * nc, k_gemv_n<T><<<grid_for(nc, 8), kThreads, 0, s>>>(V, ldv, kk, h1, -1.0, w, nc));
             TG_PROF(P_DOT, 1.0 * nc * sizeof(T), 2.0 * nc, k_dot<T><<<grid_for(nc, 4), kThreads, 0, s>>>(w, nullptr, nc, wsp<DD>(op, S_PART), wsp<unsigned>(op, S_TICKET), nrm));

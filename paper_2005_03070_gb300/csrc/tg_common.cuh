@@ -328,6 +328,11 @@ template <> struct Apply<cplx> {
     }
 };
 
+// ----------------------------------------------------------------------------- sizes
+constexpr int kMaxM = 256;              // largest GMRES-DR / GMRES subspace dimension m, and
+                                        // largest deflation basis k
+constexpr int kMaxCols = kMaxM + 2;     // coefficient vectors staged per block (m + 1 columns)
+
 // ----------------------------------------------------------------------------- launch shape
 constexpr int kThreads = 256;
 int num_sms();
@@ -382,21 +387,21 @@ __device__ __forceinline__ cplx ldcg(const cplx *p) {
     return {v.x, v.y};
 }
 
-// In the last block: totals[d] = sum over blocks of part[b * ND + d].  Warp d reduces
-// entry d: lane l adds blocks l, l + 32, ... in order, then the lanes are combined by the
+// In the last block: totals[d] = sum over blocks of part[b * ND + d].  A warp reduces each
+// entry: lane l adds blocks l, l + 32, ... in order, then the lanes are combined by the
 // fixed shuffle tree, so the result does not depend on block scheduling.
 template <class D>
 __device__ __forceinline__ D dzero() { return D{}; }
 
 template <class D, int ND>
 __device__ __forceinline__ void final_sum(const D *part, D *totals_smem, unsigned *ticket) {
-    static_assert(ND <= kThreads / 32, "one warp per reduced entry");
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < ND) {
+    // warp w reduces entries w, w + 8, ... (more entries than warps take several rounds)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int d = warp; d < ND; d += nw) {
         D s = dzero<D>();
-        for (int b = lane; b < (int)gridDim.x; b += 32) s = dadd(s, ldcg(part + (size_t)b * ND + warp));
+        for (int b = lane; b < (int)gridDim.x; b += 32) s = dadd(s, ldcg(part + (size_t)b * ND + d));
         s = warp_sum(s);
-        if (lane == 0) totals_smem[warp] = s;
+        if (lane == 0) totals_smem[d] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) *ticket = 0u;

@@ -346,17 +346,20 @@ __global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restr
 
 // ----------------------------------------------------------------------------- tall-skinny
 // Partial products of h = V^H w over row tiles: part[block][c] = sum over the block's rows
-// of conj(V[row, c]) w[row], c < ncol.  Warp w owns columns w, w + 8, ...; each pass covers
-// 128 rows (4 rows per lane) so that four loads per column are in flight per lane.
+// of conj(V[row, c]) w[row], c < ncol.  Columns come in groups of kGemvTCols (blockIdx.y);
+// within a group warp w owns columns w, w + 8, ...; each pass covers 128 rows (4 rows per
+// lane) so that four loads per column are in flight per lane.
+constexpr int kGemvTCols = 136;          // 8 warps x 17 columns
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ V, size_t ldv, int ncol,
                                                            const T *__restrict__ w, int n,
                                                            typename ST<T>::D *part, const int *cond = nullptr) {
     using P = typename Part<T>::P;
     if (cond && !*cond) return;     // a skipped re-orthogonalisation pass
-    constexpr int kMaxPerWarp = 17;   // 8 warps x 17 columns >= 129
+    constexpr int kMaxPerWarp = kGemvTCols / 8;
     constexpr int kU = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cbase = blockIdx.y * kGemvTCols;
     P acc[kMaxPerWarp];
 #pragma unroll
     for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = ST<T>::zero();
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
         }
 #pragma unroll
         for (int q = 0; q < kMaxPerWarp; ++q) {
-            const int c = warp + 8 * q;
+            const int c = cbase + warp + 8 * q;
             if (c < ncol) {
                 const T *vc = V + (size_t)c * ldv;
                 T vv[kU];
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
     }
 #pragma unroll
     for (int q = 0; q < kMaxPerWarp; ++q) {
-        const int c = warp + 8 * q;
+        const int c = cbase + warp + 8 * q;
         if (c < ncol) {       // reduce only the columns this warp owns
             P s = warp_sum(acc[q]);
             if (lane == 0) part[(size_t)blockIdx.x * ncol + c] = to_d(s);
@@ -396,14 +399,16 @@ __global__ void __launch_bounds__(kThreads) k_gemv_t_part(const T *__restrict__ 
 // the rows are walked in chunks of PipeRows<E> rows (64 float64 / 128 float32 rows, 512
 // bytes per column) staged in shared memory by a 3-deep cp.async pipeline, so that loads of
 // the next chunks are in flight while the arithmetic pipe works on the current one.  Block
-// b takes chunks b, b + G, ...  Warp w owns columns w, w + 8, ...; lane l rows l + 32 u of a
-// chunk.  Accumulation in E; partials written as float64.  Shared memory:
-// 3 x (ncol + 1) x PipeRows<E> elements (w is the extra column).
+// b takes chunks b, b + G, ...  Columns come in groups of kPipeCols (blockIdx.y); within a
+// group warp w owns columns w, w + 8, ...; lane l rows l + 32 u of a chunk.  Accumulation in
+// E; partials written as float64 to part[block x][column].  Shared memory:
+// 3 x (group columns + 1) x PipeRows<E> elements (w is the extra column).
 template <class E> struct PipeRows;
 template <> struct PipeRows<double> { static constexpr int value = 64; };
 template <> struct PipeRows<float> { static constexpr int value = 128; };
 constexpr int kPipeRows = 64;          // float64 chunk (the float32 chunk holds the same bytes)
 constexpr int kPipeStages = 3;
+constexpr int kPipeCols = 128;         // columns per group: 3 x 129 x 512 B of shared memory
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -415,12 +420,16 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 template <class E>
 __global__ void __launch_bounds__(kThreads, 2) k_gemv_t_pipe(const E *__restrict__ V, size_t ldv, int ncol,
                                                            const E *__restrict__ w, int n, double *part) {
-    constexpr int kMaxPerWarp = 17;
+    constexpr int kMaxPerWarp = kPipeCols / 8;
     constexpr int R = PipeRows<E>::value;
     constexpr int PE = 16 / sizeof(E);           // elements per 16-byte piece
     constexpr int U = R / 32;                    // rows per lane per chunk
     extern __shared__ __align__(16) unsigned char smem_raw[];
     E *buf = reinterpret_cast<E *>(smem_raw);
+    const int cbase = blockIdx.y * kPipeCols;    // this block's columns: cbase .. cbase + ng - 1
+    const int ncol_all = ncol;
+    ncol = min(ncol_all - cbase, kPipeCols);
+    V += (size_t)cbase * ldv;
     const int cols = ncol + 1;                      // w staged as column ncol
     const size_t stage_elems = (size_t)cols * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemv_t_pipe(const E *__restrict
         const int c = warp + 8 * q;
         if (c < ncol) {
             const E s = warp_sum(acc[q]);
-            if (lane == 0) part[(size_t)blockIdx.x * ncol + c] = (double)s;
+            if (lane == 0) part[(size_t)blockIdx.x * ncol_all + cbase + c] = (double)s;
         }
     }
 }
@@ -497,14 +506,14 @@ __global__ void k_sum_part(const D *__restrict__ part, int nblk, int nent, D *ou
     if (lane == 0) out[e] = mode ? dadd(out[e], s) : s;
 }
 
-// w[row] += sign * sum_c V[row, c] h[c]   (h: device, D type, ncol <= 129)
+// w[row] += sign * sum_c V[row, c] h[c]   (h: device, D type, ncol <= kMaxCols)
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gemv_n(const T *__restrict__ V, size_t ldv, int ncol,
                                                       const typename ST<T>::D *__restrict__ h, double sign,
                                                       T *__restrict__ w, int n) {
     // coefficients converted to the vector type once per block (a per-element float64 ->
     // float32 conversion would run on the float64 pipe)
-    __shared__ T hs[130];
+    __shared__ T hs[kMaxCols];
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = KS<T>::of(h[c]);
     __syncthreads();
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
@@ -530,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n_norm(const T *__restrict__ 
     using D = typename ST<T>::D;
     using P = typename Part<T>::P;
     if (cond && !*cond) return;
-    __shared__ T hs[130];      // coefficients in the vector type, converted once per block
+    __shared__ T hs[kMaxCols];   // coefficients in the vector type, converted once per block
     __shared__ D red[(kThreads / 32)];
     __shared__ D tot[1];
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = KS<T>::of(h[c]);
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_gemv_n_norm_f4(const float *__rest
                                                               const double *__restrict__ h, float *__restrict__ w,
                                                               int n, double *part, unsigned *ticket,
                                                               double *nrm2_out) {
-    __shared__ float hs[130];
+    __shared__ float hs[kMaxCols];
     __shared__ double red[(kThreads / 32)];
     __shared__ double tot[1];
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) hs[c] = (float)h[c];
@@ -694,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_proj_update(const T *__restrict__ 
                                                            const typename ST<T>::D *__restrict__ d,
                                                            const typename ST<T>::D *__restrict__ e,
                                                            T *__restrict__ x, T *__restrict__ r, int n) {
-    __shared__ T ds[130], es[130];      // in the vector type, converted once per block
+    __shared__ T ds[kMaxCols], es[kMaxCols];   // in the vector type, converted once per block
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         ds[c] = KS<T>::of(d[c]);
         es[c] = KS<T>::of(e[c]);
@@ -738,47 +747,91 @@ __global__ void __launch_bounds__(kThreads) k_tsm(const T *__restrict__ In, size
     }
 }
 
-// Partial Gram products G = A^H B over 32-row tiles: part[block][i + j*k] for the
-// entries the block owns (all k*k; sym = 1 computes i <= j only and leaves the rest 0).
-template <class T, int kEPT>
-__global__ void __launch_bounds__(kThreads) k_gram_part(const T *__restrict__ A, const T *__restrict__ B,
-                                                         size_t ld, int k, int n, int sym,
-                                                         typename ST<T>::D *part) {
-    // kEPT entries per thread: kThreads * kEPT >= k * k
+// Partial Gram products G = A^H B over 32-row tiles, on a packed list of output entries:
+// sym = 1 takes the upper triangle i <= j column by column (entry e = j (j + 1) / 2 + i; the
+// lower triangle is its conjugate), sym = 0 all k^2 entries (e = i + j k).  Block (x, y)
+// takes row tiles x, x + gridDim.x, ... and entries y * kThreads * EPT + threadIdx.x +
+// q * kThreads, q < EPT, and writes part[x * nent + e].  Tiles are staged with a row stride of
+// 33 elements, so the lanes of a warp (consecutive i) read distinct shared-memory banks; each
+// lane's FMAs are for live entries only (no idle half for the symmetric case).
+template <class T, int EPT>
+__global__ void __launch_bounds__(kThreads) k_gram_packed(const T *__restrict__ A, const T *__restrict__ B,
+                                                           size_t ld, int k, int n, int sym, int nent,
+                                                           typename ST<T>::D *part) {
     using D = typename ST<T>::D;
+    constexpr int kS = 33;                   // staged row stride (elements)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *ta = reinterpret_cast<T *>(smem_raw);
-    T *tb = ta + 32 * k;
-    D acc[kEPT];
+    const bool same = A == B;
+    T *tb = same ? ta : ta + (size_t)kS * k;
+    int ii[EPT], jj[EPT];
+    D acc[EPT];
 #pragma unroll
-    for (int e = 0; e < kEPT; ++e) acc[e] = D{};
-    const int nent = k * k;
+    for (int q = 0; q < EPT; ++q) {
+        acc[q] = D{};
+        const int e = blockIdx.y * (kThreads * EPT) + threadIdx.x + q * kThreads;
+        int i = -1, j = 0;
+        if (e < nent) {
+            if (sym) {
+                j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                while (j > 0 && j * (j + 1) / 2 > e) --j;
+                while ((j + 1) * (j + 2) / 2 <= e) ++j;
+                i = e - j * (j + 1) / 2;
+            } else {
+                j = e / k;
+                i = e - j * k;
+            }
+        }
+        ii[q] = i;
+        jj[q] = j;
+    }
     for (int row0 = blockIdx.x * 32; row0 < n; row0 += gridDim.x * 32) {
         __syncthreads();
         for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) {
             const int r = e & 31, c = e >> 5;
             const int row = row0 + r;
-            ta[c * 32 + r] = row < n ? A[(size_t)c * ld + row] : ST<T>::zero();
-            tb[c * 32 + r] = row < n ? B[(size_t)c * ld + row] : ST<T>::zero();
+            ta[c * kS + r] = row < n ? A[(size_t)c * ld + row] : ST<T>::zero();
+            if (!same) tb[c * kS + r] = row < n ? B[(size_t)c * ld + row] : ST<T>::zero();
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kEPT; ++q) {
-            const int e = threadIdx.x + q * kThreads;
-            if (e < nent) {
-                const int i = e % k, j = e / k;
-                if (!sym || i <= j) {
-                    typename Part<T>::P s = ST<T>::zero();
-                    for (int r = 0; r < 32; ++r) s = ST<T>::fma_cm(ta[i * 32 + r], tb[j * 32 + r], s);
-                    acc[q] = dadd(acc[q], to_d(s));
-                }
+        for (int q = 0; q < EPT; ++q) {
+            if (ii[q] >= 0) {
+                const T *a = ta + ii[q] * kS, *b = tb + jj[q] * kS;
+                typename Part<T>::P s = ST<T>::zero();
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) s = ST<T>::fma_cm(a[r], b[r], s);
+                acc[q] = dadd(acc[q], to_d(s));
             }
         }
     }
 #pragma unroll
-    for (int q = 0; q < kEPT; ++q) {
-        const int e = threadIdx.x + q * kThreads;
+    for (int q = 0; q < EPT; ++q) {
+        const int e = blockIdx.y * (kThreads * EPT) + threadIdx.x + q * kThreads;
         if (e < nent) part[(size_t)blockIdx.x * nent + e] = acc[q];
+    }
+}
+
+// G (k x k, column-major) from the packed entries; sym: the lower triangle is the conjugate.
+__device__ __forceinline__ double dconj(double a) { return a; }
+__device__ __forceinline__ cplx dconj(cplx a) { return conj(a); }
+template <class D>
+__global__ void k_gram_unpack(const D *__restrict__ packed, int k, int sym, D *G) {
+    const int nent = sym ? k * (k + 1) / 2 : k * k;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
+        int i, j;
+        if (sym) {
+            j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (j > 0 && j * (j + 1) / 2 > e) --j;
+            while ((j + 1) * (j + 2) / 2 <= e) ++j;
+            i = e - j * (j + 1) / 2;
+        } else {
+            j = e / k;
+            i = e - j * k;
+        }
+        const D v = packed[e];
+        G[i + (size_t)j * k] = v;
+        if (sym && i != j) G[j + (size_t)i * k] = dconj(v);
     }
 }
 

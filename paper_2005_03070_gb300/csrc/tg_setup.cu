@@ -1,6 +1,7 @@
 // Operator set-up and grid-transfer kernels of the tg library.
 //
-//  - variable-coefficient stencil coefficients from node kappa (arithmetic face means);
+//  - variable-coefficient stencil coefficients from node kappa (arithmetic face means), and
+//    those of Example 1's operator -exp(gamma x y) Lap u + beta . grad u;
 //  - lattice block-transport weights P[x, X] = (1/4) conj(W(x)) and the Galerkin coarse
 //    operator P^H A P as a 9-point stencil (Section 5.4's lattice problem; the paper's
 //    Schwinger-model coarse operator is not specified, this build uses 2^4 blocking);
@@ -29,6 +30,41 @@ __global__ void k_vark_coefs(const double *__restrict__ kappa, int N, double bet
         const double ws = (kc + kappa[(j - 1) * NP + i]) * s;
         const double wn = (kc + kappa[(j + 1) * NP + i]) * s;
         const double c[5] = {ww + we + ws + wn, -ww - cb, -we + cb, -ws, -wn};
+        for (int q = 0; q < 5; ++q) {
+            coef[(size_t)q * n + idx] = c[q];
+            coef32[(size_t)q * n + idx] = (float)c[q];
+        }
+    }
+}
+
+// coef[5][n] of -exp(gamma x y)(u_xx + u_yy) + bx u_x + by u_y + shift u (Example 1's operator
+// with gamma = 5, bx = by = 40), centred differences, x = i h, y = j h: for A (transpose = 0)
+// the coefficients of u_nb in (A u)(i, j); for A^T (transpose = 1) those of (A^T u)(i, j),
+// i.e. A[nb, (i, j)]: the diffusion weight is taken at the neighbour and the convection sign
+// flips (A = D_a L + C with L symmetric and C antisymmetric, so A^T = L D_a - C).
+__global__ void k_exp2d_coefs(int N, double bx, double by, double gamma, double shift, int transpose,
+                              double *__restrict__ coef, float *__restrict__ coef32) {
+    const int n = N * N;
+    const double h = 1.0 / (N + 1);
+    const double ih2 = 1.0 / (h * h);
+    const double cx = bx / (2.0 * h), cy = by / (2.0 * h);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int i = idx % N + 1, j = idx / N + 1;
+        const double x = i * h, y = j * h;
+        const double a = exp(gamma * x * y);
+        double c[5];
+        c[0] = 4.0 * a * ih2 + shift;
+        if (!transpose) {
+            c[1] = -a * ih2 - cx;
+            c[2] = -a * ih2 + cx;
+            c[3] = -a * ih2 - cy;
+            c[4] = -a * ih2 + cy;
+        } else {
+            c[1] = -exp(gamma * (x - h) * y) * ih2 + cx;     // A[(i-1, j), (i, j)]
+            c[2] = -exp(gamma * (x + h) * y) * ih2 - cx;     // A[(i+1, j), (i, j)]
+            c[3] = -exp(gamma * x * (y - h)) * ih2 + cy;     // A[(i, j-1), (i, j)]
+            c[4] = -exp(gamma * x * (y + h)) * ih2 - cy;     // A[(i, j+1), (i, j)]
+        }
         for (int q = 0; q < 5; ++q) {
             coef[(size_t)q * n + idx] = c[q];
             coef32[(size_t)q * n + idx] = (float)c[q];
@@ -266,6 +302,8 @@ __global__ void k_d2f(const double *__restrict__ a, float *__restrict__ b, size_
     void launch_##name params { k_##name<<<grid, kThreads, 0, s>>> args; }
 TG_L(vark_coefs, (int grid, cudaStream_t s, const double *kappa, int N, double beta, int sgn, double *coef, float *coef32),
      (kappa, N, beta, sgn, coef, coef32))
+TG_L(exp2d_coefs, (int grid, cudaStream_t s, int N, double bx, double by, double gamma, double shift, int transpose,
+                   double *coef, float *coef32), (N, bx, by, gamma, shift, transpose, coef, coef32))
 TG_L(inject_kappa, (int grid, cudaStream_t s, const double *kappa, int N, double *kc), (kappa, N, kc))
 TG_L(lattice_weights, (int grid, cudaStream_t s, const cplx *links, int L, cplx *pw), (links, L, pw))
 TG_L(lattice_coarse, (int grid, cudaStream_t s, const cplx *links, const cplx *pw, int L, double mdiag, cplx *cst),

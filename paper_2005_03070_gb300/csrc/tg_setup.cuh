@@ -8,6 +8,8 @@ namespace tg {
 
 void launch_vark_coefs(int grid, cudaStream_t s, const double *kappa, int N, double beta, int sgn, double *coef,
                        float *coef32);
+void launch_exp2d_coefs(int grid, cudaStream_t s, int N, double bx, double by, double gamma, double shift,
+                        int transpose, double *coef, float *coef32);
 void launch_inject_kappa(int grid, cudaStream_t s, const double *kappa, int N, double *kc);
 void launch_lattice_weights(int grid, cudaStream_t s, const cplx *links, int L, cplx *pw);
 void launch_lattice_coarse(int grid, cudaStream_t s, const cplx *links, const cplx *pw, int L, double mdiag, cplx *cst);

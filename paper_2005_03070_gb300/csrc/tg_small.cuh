@@ -8,7 +8,6 @@ namespace tg {
 constexpr int kSmallThreads = 256;
 constexpr int kGdrThreads = 128;                 // GMRES-DR restart kernel block
 constexpr size_t kGdrSmemMax = 210 * 1024;       // shared memory for W and Z when they fit
-constexpr int kMaxM = 128;          // largest GMRES-DR subspace dimension m
 
 struct GdrInfo {
     double rnorm;   // ||c - Hbar d||

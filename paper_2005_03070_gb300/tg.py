@@ -19,13 +19,13 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtg.so")
 
 TG_OK, TG_NOT_CONVERGED, TG_BREAKDOWN, TG_NAN, TG_BAD_ARG, TG_OOM, TG_CUDA_ERROR, TG_SYNC_TIMEOUT = range(8)
-TG_CD2D, TG_CD3D, TG_U1_4D, TG_VARK2D = 0, 1, 2, 3
+TG_CD2D, TG_CD3D, TG_U1_4D, TG_VARK2D, TG_EXP2D = 0, 1, 2, 3, 4
 TG_BICGSTAB, TG_GMRES = 0, 1
 TG_PROJ_MINRES, TG_PROJ_GALERKIN = 0, 1
 TG_F64, TG_F32_IR = 0, 1
 TG_FINE, TG_COARSE = 0, 1
 
-KIND = {"cd2d": TG_CD2D, "cd3d": TG_CD3D, "u1_4d": TG_U1_4D, "vark2d": TG_VARK2D}
+KIND = {"cd2d": TG_CD2D, "cd3d": TG_CD3D, "u1_4d": TG_U1_4D, "vark2d": TG_VARK2D, "exp2d": TG_EXP2D}
 METHOD = {"bicgstab": TG_BICGSTAB, "gmres": TG_GMRES}
 PROJ = {"minres": TG_PROJ_MINRES, "galerkin": TG_PROJ_GALERKIN}
 PREC = {"f64": TG_F64, "f32_ir": TG_F32_IR}
@@ -33,7 +33,7 @@ PREC = {"f64": TG_F64, "f32_ir": TG_F32_IR}
 EXPORTS = [
     "tg_status_string", "tg_last_error", "tg_setup_operator", "tg_destroy_op", "tg_op_size", "tg_apply",
     "tg_prolong", "tg_restrict", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
-    "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_adjoint_solve", "tg_kappa_gradient",
+    "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_solve_idr", "tg_adjoint_solve", "tg_kappa_gradient",
     "tg_harmonic_ritz", "tg_harmonic_ritz_noalloc", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
     "tg_batch_create", "tg_batch_layout", "tg_batch_setup", "tg_batch_solve", "tg_destroy_batch",
 ]
@@ -87,6 +87,7 @@ def load() -> C.CDLL:
         "tg_defl_copy": (i32, [vp, i32, vp, C.POINTER(i32), vp]),
         "tg_project": (i32, [vp, vp, vp, vp, vp]),
         "tg_solve_proj": (i32, [vp, vp, i32, i32, vp, vp, i32, dbl, i32, i32, i32, i64, C.POINTER(TgStats), vp]),
+        "tg_solve_idr": (i32, [vp, vp, i32, vp, vp, i32, dbl, i32, i32, i32, vp, dbl, i64, C.POINTER(TgStats), vp]),
         "tg_adjoint_solve": (i32, [vp, vp, vp, vp, vp, vp, dbl, i32, i32, i32, C.POINTER(TgStats), vp]),
         "tg_kappa_gradient": (i32, [vp, vp, vp, vp, vp]),
         "tg_harmonic_ritz": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
@@ -131,9 +132,10 @@ def _stream(stream=None):
 class Operator:
     """tg_setup_operator: the fine operator and its coarse partner.
 
-    kind: "cd2d" | "cd3d" | "vark2d" | "u1_4d"; N: points per axis (odd) or lattice L;
-    beta: convection speeds; kappa: (N+2)^2 float64 CUDA tensor (vark2d); links: (4, L^4)
-    complex128 CUDA tensor and mass (u1_4d)."""
+    kind: "cd2d" | "cd3d" | "vark2d" | "exp2d" | "u1_4d"; N: points per axis (odd) or lattice L;
+    beta: convection speeds (exp2d: (beta_x, beta_y, gamma) of -exp(gamma x y) Lap u + beta . grad u);
+    kappa: (N+2)^2 float64 CUDA tensor (vark2d); links: (4, L^4) complex128 CUDA tensor and mass
+    (u1_4d); mass on the grid kinds: the reaction coefficient c of + c u (Helmholtz: -k^2)."""
 
     def __init__(self, kind, N, beta=(0.0,), kappa=None, links=None, mass=None, stream=None):
         lib = load()
@@ -226,6 +228,33 @@ class Operator:
             d = s.as_dict()
             if history:
                 n = min(s.history_len, history)
+                d["history"] = [tuple(bufs[i][3 * j:3 * j + 3]) for j in range(n)]
+            out.append(d)
+        return status, out
+
+    def solve_idr(self, b, x, P, defl=None, rtol=1e-8, ncyc=20, restart_mvps=0, kappa=0.7, max_mvps=10 ** 7,
+                  nrhs=1, history=0, stream=None):
+        """tg_solve_idr: IDR(s)-Proj(k) with s = P's column count; P is an (s, n) tensor whose
+        rows are the shadow columns (the library orthonormalises them)."""
+        s = P.shape[0]
+        stats = (TgStats * nrhs)()
+        bufs = []
+        if history:
+            for st in stats:
+                buf = (C.c_double * (3 * history))()
+                bufs.append(buf)
+                st.history = C.cast(buf, C.POINTER(C.c_double))
+                st.history_cap = history
+        status = _lib.tg_solve_idr(self._h, defl.handle if defl is not None else None, TG_F64, _ptr(b), _ptr(x),
+                                   nrhs, rtol, ncyc, restart_mvps, s, _ptr(P.contiguous()), kappa, max_mvps, stats,
+                                   _stream(stream))
+        if status in (TG_BAD_ARG, TG_OOM, TG_CUDA_ERROR):
+            _check(status, "tg_solve_idr")
+        out = []
+        for i, st in enumerate(stats):
+            d = st.as_dict()
+            if history:
+                n = min(st.history_len, history)
                 d["history"] = [tuple(bufs[i][3 * j:3 * j + 3]) for j in range(n)]
             out.append(d)
         return status, out

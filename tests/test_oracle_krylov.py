@@ -362,3 +362,66 @@ def test_bicgstab_proj_continues_past_ncyc():
     assert _rel(res.x, _dense_solve(op, b)) < 1e-8
     for icyc, relres, rt, _ in res.history[2:]:
         assert abs(rt * relres - 1e-11) <= 1e-11 * 1e-12
+
+
+def test_idr1_is_bicgstab():
+    """IDR(1) with the shadow vector r0 / ||r0|| and omega taken as the plain minimiser
+    (kappa = 0) is BiCGStab (Sonneveld and van Gijzen's equivalence): the residual norms
+    after every product agree with the textbook BiCGStab cycle's half and full steps."""
+    op = Operator(CD2D, 15, (5.0,))
+    b = gi.rhs(op.n, 3)
+    P = (b / np.linalg.norm(b))[:, None]
+    ri = krylov.idr_cycle(op.apply, np.zeros(op.n), b, P, 0.0, max_mvps=24, kappa=0.0)
+    rb = krylov.bicgstab_cycle(op.apply, np.zeros(op.n), b, 0.0, max_mvps=24)
+    assert len(ri.history) == len(rb.history) == 24
+    assert np.allclose(ri.history, rb.history, rtol=1e-9, atol=0)
+    assert _rel(ri.x, rb.x) < 1e-9
+
+
+def test_idr_finite_termination():
+    """In exact arithmetic IDR(s) solves an n x n system within n + n/s products; on a
+    well-conditioned dense nonsymmetric 12 x 12 system with s = 4 it reaches rounding level
+    within 15."""
+    n, s = 12, 4
+    A = gi.random_dense((n, n), 21) + 4 * np.eye(n)
+    b = gi.random_dense(n, 22)
+    P = krylov.shadow_space(gi.random_dense((n, s), 23))
+    res = krylov.idr_cycle(lambda v: A @ v, np.zeros(n), b, P, 1e-12 * np.linalg.norm(b), max_mvps=40)
+    assert res.converged and res.mvps <= n + n // s
+    assert _rel(res.x, np.linalg.solve(A, b)) < 1e-10
+
+
+def test_idr_scalar_matrix_one_product():
+    """A = lambda I: the first IDR(s) step already gives the exact solution (one product)."""
+    n = 50
+    b = gi.random_dense(n, 24)
+    P = krylov.shadow_space(gi.random_dense((n, 4), 25))
+    res = krylov.idr_cycle(lambda v: 3.5 * v, np.zeros(n), b, P, 1e-13 * np.linalg.norm(b))
+    assert res.mvps == 1 and _rel(res.x, b / 3.5) < 1e-14
+
+
+def test_shadow_space_unique():
+    """The positive-diagonal QR convention fixes the orthonormal shadow space: it equals
+    Gram-Schmidt of the random columns in order, and P^H P = I."""
+    R0 = gi.random_dense((40, 4), 26)
+    P = krylov.shadow_space(R0)
+    assert np.allclose(P.T @ P, np.eye(4), atol=1e-14)
+    Q = np.zeros_like(R0)
+    for j in range(4):
+        w = R0[:, j] - Q[:, :j] @ (Q[:, :j].T @ R0[:, j])
+        Q[:, j] = w / np.linalg.norm(w)
+    assert np.allclose(P, Q, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind,N,beta", [(CD2D, 15, (1.0,)), (CD3D, 7, (2.0, 1.0, 0.5))])
+def test_idr_proj_brute_force(kind, N, beta):
+    op = Operator(kind, N, beta)
+    b = gi.rhs(op.n, 27)
+    xs = _dense_solve(op, b)
+    P = krylov.shadow_space(gi.random_dense((op.n, 4), 28))
+    Y = gi.random_dense((op.n, 6), 29)
+    defl = krylov.make_deflation(op.apply, Y, "minres")
+    for ncyc, cap in ((10, None), (0, 25), (3, 9)):
+        res = krylov.idr_proj(op.apply, b, np.zeros(op.n), defl, P, rtol=1e-11, ncyc=ncyc,
+                              restart_mvps=cap, max_mvps=20000)
+        assert res.converged and _rel(res.x, xs) < 1e-8

@@ -223,3 +223,78 @@ def test_restrict_stencil_equals_sparse_transpose(N, dim):
     a = transfer.restrict(u, N, dim)
     b = transfer.restrict_stencil(u, N, dim)
     assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))
+
+
+def test_reaction_shift_closed_form():
+    """cd2d with the reaction term c u (Example 4's Helmholtz form): the spectrum is the
+    closed-form convection-diffusion spectrum shifted by c (LAPACK eig of the assembled
+    matrix), and the shift survives transposition and coarsening."""
+    from oracle.operators import cd2d_eigenvalues
+    N, beta, c = 9, 3.0, -700.0
+    op = Operator(CD2D, N, (beta,), mass=c)
+    lam = np.sort(np.linalg.eigvals(op.sparse().toarray()).real)
+    assert np.max(np.abs(lam - (cd2d_eigenvalues(N, beta) + c))) <= 1e-10 * np.max(np.abs(lam))
+    u = gi.random_dense(op.n, 3)
+    assert np.allclose(op.apply(u), op.sparse() @ u, rtol=1e-13, atol=1e-10)
+    assert np.allclose(op.transposed().apply(u), op.sparse().T @ u, rtol=1e-13, atol=1e-10)
+    assert coarse_operator(op).mass == c
+
+
+def test_exp2d_without_exponent_closed_form():
+    """Example 1's operator with gamma = 0 is -Lap + bx d_x + by d_y, diagonally similar to a
+    symmetric matrix when |b h / 2| < 1 in both directions: its eigenvalues are
+    [4 - 2 sqrt(1 - gx^2) cos(p pi h) - 2 sqrt(1 - gy^2) cos(q pi h)] / h^2, gx = bx h / 2."""
+    from oracle.operators import EXP2D
+    N, bx, by = 9, 3.0, -5.0
+    h = 1.0 / (N + 1)
+    p = np.arange(1, N + 1)
+    tx = 2 - 2 * np.sqrt(1 - (bx * h / 2) ** 2) * np.cos(p * np.pi * h)
+    ty = 2 - 2 * np.sqrt(1 - (by * h / 2) ** 2) * np.cos(p * np.pi * h)
+    closed = np.sort((tx[:, None] + ty[None, :]).reshape(-1) / h**2)
+    op = Operator(EXP2D, N, (bx, by, 0.0))
+    lam = np.sort(np.linalg.eigvals(op.sparse().toarray()).real)
+    assert np.max(np.abs(lam - closed)) <= 1e-10 * closed[-1]
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_exp2d_matrix_free_equals_assembled(transpose):
+    from oracle.operators import EXP2D
+    op = Operator(EXP2D, 15, (40.0, 40.0, 5.0), mass=-3.0)
+    if transpose:
+        A = op.sparse().T
+        op = op.transposed()
+    else:
+        A = op.sparse()
+    u = gi.random_dense(op.n, 4)
+    y = op.apply(u)
+    assert np.max(np.abs(y - A @ u)) <= 1e-12 * np.max(np.abs(y))
+    c = coarse_operator(op)
+    assert c.N == 7 and c.beta == op.beta and c.transpose == op.transpose
+
+
+@pytest.mark.parametrize("kind", ["exp2d", "helmholtz"])
+def test_continuum_limit(kind):
+    """Applied to samples of a smooth u with zero boundary values, the discrete operator
+    approaches the differential operator at the nodes with O(h^2) error (centred
+    differences): -exp(5xy) Lap u + 40 u_x + 40 u_y (Example 1) and -Lap u - 100^2 u
+    (Example 4), u = sin(pi x) sin(2 pi y), derivatives by hand."""
+    from oracle.operators import EXP2D
+    errs = []
+    for N in (63, 127, 255):
+        h = 1.0 / (N + 1)
+        t = np.arange(1, N + 1) * h
+        Y, X = np.meshgrid(t, t, indexing="ij")            # [j, i]
+        u = np.sin(np.pi * X) * np.sin(2 * np.pi * Y)
+        lap = -5 * np.pi ** 2 * u
+        ux = np.pi * np.cos(np.pi * X) * np.sin(2 * np.pi * Y)
+        uy = 2 * np.pi * np.sin(np.pi * X) * np.cos(2 * np.pi * Y)
+        if kind == "exp2d":
+            op = Operator(EXP2D, N, (40.0, 40.0, 5.0))
+            exact = -np.exp(5 * X * Y) * lap + 40 * ux + 40 * uy
+        else:
+            op = Operator(CD2D, N, (0.0,), mass=-1e4)
+            exact = -lap - 1e4 * u
+        errs.append(np.max(np.abs(op.apply(u.reshape(-1)) - exact.reshape(-1))) / np.max(np.abs(exact)))
+    assert errs[-1] < 1e-3
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 3.5 < e0 / e1 < 4.5, errs
