@@ -220,6 +220,29 @@ int tg_solve_idr(tg_op *op, const tg_defl *defl, int precision, const void *b, v
                  double rtol, int ncyc, int restart_mvps, int s, const void *P, double kappa,
                  int64_t max_mvps, tg_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------ phase 2: improvement
+ * Arnoldi-E improvement of the moved eigenvectors on the fine grid (Section 3 box and
+ * Section 4.1 box, step 2; Example 7: "Arnoldi-E(150,100) ... with the 10 smallest
+ * approximate eigenvectors used as starting vectors"; Example 8: "targeting only the
+ * smallest five").  With k = the handle's kk:
+ *   0. Rayleigh-Ritz on span(Y): the Ritz pairs of Y^H A Y, ordered like the harmonic
+ *      Ritz values of tg_coarse_gmresdr (|theta|, Re, Im >= 0 first), k kept;
+ *   cycle c = 0..cycles-1: S = span{u, A u, ..., A^(m-k) u} + span(Y), u the Ritz vector
+ *      number (c mod nstart) of the previous Rayleigh-Ritz step (smallest first; its
+ *      largest coefficient made real and positive, real problems take its real part),
+ *      dimension m (u lies in span(Y): the dependent direction is dropped); Rayleigh-Ritz
+ *      on S (the same ordering, k kept, k + 1 when a complex pair would split), Y <- an
+ *      orthonormal real basis of the kept span;
+ *   stop after `cycles`, or once the nev smallest pairs have ||A y - theta y|| <=
+ *      rtolev |theta| (rtolev > 0).
+ * The handle's basis is replaced by the improved one and A Y and its factorisation (and the
+ * float32 copies of a TG_F32_IR handle) are rebuilt.  kk < m <= 256, 1 <= nstart <= kk.
+ * theta_out (host, may be NULL): 2 kk doubles, the kept Ritz values (re, im) in order.
+ * stats (host, may be NULL): cycles run, fine products (mvps), kk, pairs converged.
+ * Synchronises `stream`.                                                                */
+int tg_improve_defl(tg_op *op, tg_defl *defl, int m, int cycles, int nstart, int nev, double rtolev,
+                    double *theta_out, tg_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------ adjoint (added form)
  * Not in the paper: the gradient of a loss L(x) through the solve A(kappa) x = b for
  * TG_VARK2D.  Solves A^T lambda = g with the same two-grid deflated BiCGStab using a

@@ -200,3 +200,88 @@ def gmresdr(apply, b, m, k, nev=None, rtolev=1e-6, rtol=1e-8, max_cycles=300, x0
         c = np.zeros(m + 1, dtype=dtype)
         c[:kk + 1] = cn
         j0 = kk
+
+
+# ----------------------------------------------------------------------------- Arnoldi-E
+
+def rayleigh_ritz(S, AS, k, real_problem):
+    """Ritz pairs of span(S) (S orthonormal, AS = A S): eigenpairs of H = S^H A S, ordered
+    as the harmonic Ritz values above, k kept (k + 1 if a pair would split).  Returns
+    (theta of all pairs in order, kept indices into that order, eigenvectors G of H,
+    the residual norms ||A S g - theta S g|| of the kept pairs, ||g|| = 1)."""
+    H = S.conj().T @ AS
+    theta, G = np.linalg.eig(H)
+    idx = select_k(theta, k, real_problem)
+    eres = []
+    for i in idx:
+        g = G[:, i] / np.linalg.norm(G[:, i])
+        eres.append(np.linalg.norm(AS @ g - theta[i] * (S @ g)))
+    return theta, idx, G, np.array(eres)
+
+
+def start_vector(S, G, i, real_problem):
+    """The Ritz vector S g_i with the largest entry of g_i made real and positive (the
+    smallest index on ties); real problems take its real part; unit norm."""
+    g = G[:, i]
+    j = int(np.argmax(np.abs(g)))
+    g = g * (np.conj(g[j]) / abs(g[j]))
+    if real_problem:
+        g = g.real
+    u = S @ g
+    return u / np.linalg.norm(u)
+
+
+def arnoldi_e(apply, Y, m, cycles, nstart, nev=0, rtolev=0.0, dtype=np.float64):
+    """Arnoldi-E(m, k) improvement of k approximate eigenvectors (the paper's phase 2,
+    Section 3 box step 2 and Section 4.1 box step 2, Example 7: "Arnoldi-E(150,100) ...
+    with the 10 smallest approximate eigenvectors used as starting vectors").
+
+    Readings taken (the paper defers to its Arnoldi-E reference):
+      * a Rayleigh-Ritz step on span(Y) first orders the given vectors as Ritz vectors;
+      * cycle c works in S = span{u, A u, ..., A^(m-k) u} + span(Y), u the Ritz vector
+        number (c mod nstart) of the previous step (smallest first), of dimension m
+        (u lies in span(Y), so one appended direction is dependent and dropped);
+      * Rayleigh-Ritz on S (standard Ritz values, ordered and selected like the harmonic
+        ones of GMRES-DR), Y <- orthonormal real basis of the kept span;
+      * stop after `cycles` cycles, or earlier once the nev smallest pairs have residual
+        <= rtolev |theta| (rtolev > 0).
+    Returns (Y, theta of the kept pairs, their residual norms, cycles run, products)."""
+    real_problem = not np.issubdtype(dtype, np.complexfloating)
+    n, k = Y.shape
+    p = m - k
+    S = np.linalg.qr(Y)[0]
+    AS = np.stack([apply(S[:, j]) for j in range(k)], axis=1)
+    mvps = k
+    theta, idx, G, eres = rayleigh_ritz(S, AS, k, real_problem)
+    basis = np.linalg.qr(real_span_basis(G, theta, idx, real_problem))[0]
+    Y = S @ basis
+    u = start_vector(S, G, idx[0 % nstart], real_problem)
+    done = 0
+    for c in range(cycles):
+        # Krylov part from u (Arnoldi, classical Gram-Schmidt twice), then span(Y)
+        V = np.zeros((n, p + 1), dtype=dtype)
+        Hk = np.zeros((p + 1, p), dtype=dtype)
+        V[:, 0] = u
+        V, Hk = arnoldi_extend(apply, V, Hk, 0, p)
+        mvps += p
+        cols = [V[:, j] for j in range(p + 1)]
+        for j in range(Y.shape[1]):
+            w = Y[:, j].copy()
+            w0 = np.linalg.norm(w)
+            Q = np.stack(cols, axis=1)
+            for _ in range(2):
+                w = w - Q @ (Q.conj().T @ w)
+            if np.linalg.norm(w) > 1e-10 * w0:
+                cols.append(w / np.linalg.norm(w))
+        S = np.stack(cols, axis=1)
+        AS = np.stack([apply(S[:, j]) for j in range(S.shape[1])], axis=1)
+        mvps += S.shape[1]
+        theta, idx, G, eres = rayleigh_ritz(S, AS, k, real_problem)
+        basis = np.linalg.qr(real_span_basis(G, theta, idx, real_problem))[0]
+        Y = S @ basis
+        done = c + 1
+        nconv = int(np.sum(eres[:nev] <= rtolev * np.abs(theta[idx[:nev]]))) if rtolev > 0 else 0
+        if rtolev > 0 and nconv >= nev:
+            break
+        u = start_vector(S, G, idx[(c + 1) % nstart], real_problem)
+    return Y, theta[idx], eres, done, mvps

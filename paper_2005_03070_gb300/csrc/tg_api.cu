@@ -202,6 +202,8 @@ enum Slot {
     S_FV, S_FH, S_FCS, S_FSN, S_FG, S_FY, S_FSTATE, S_BC,
     S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC, S_XBAK,
     S_IG, S_IU, S_IP, S_IPR, S_IPRI, S_IT, S_IINFO,
+    S_AE_S, S_AE_W, S_AE_H, S_AE_WW, S_AE_HA, S_AE_Y, S_AE_U, S_AE_P, S_AE_Z, S_AE_TH, S_AE_WR, S_AE_WI,
+    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM,
     S_COUNT
 };
 
@@ -842,7 +844,10 @@ static int project_impl(tg_op *op, const tg_defl *df, const T *W, const T *B1, c
     TG_PROF(P_SMALL, 0, 2.0 * kk * kk, launch_small_gemv<D>(df->M.as<D>(), kk, cvec, dvec, s));
     TG_LAUNCH_CHECK();
     const D *e = df->proj == TG_PROJ_MINRES ? cvec : dvec;
-    TG_PROF(P_PROJ, (2.0 * kk + 4) * n * sizeof(T), 4.0 * kk * n * (sizeof(T) == 16 ? 4 : 1), k_proj_update<T><<<grid_for(n, 8), kThreads, 0, s>>>(B1, B2, n, kk, dvec, e, x, r, n));
+    if (kk <= kSmallCols)
+        TG_PROF(P_PROJ, (2.0 * kk + 4) * n * sizeof(T), 4.0 * kk * n * (sizeof(T) == 16 ? 4 : 1), k_proj_update<T, kSmallCols><<<grid_for(n, 8), kThreads, 0, s>>>(B1, B2, n, kk, dvec, e, x, r, n));
+    else
+        TG_PROF(P_PROJ, (2.0 * kk + 4) * n * sizeof(T), 4.0 * kk * n * (sizeof(T) == 16 ? 4 : 1), k_proj_update<T><<<grid_for(n, 8), kThreads, 0, s>>>(B1, B2, n, kk, dvec, e, x, r, n));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
@@ -1363,11 +1368,15 @@ static void gemv_n_norm_launch(int g, const T *V, size_t ldv, int ncol, const ty
                                const typename ST<T>::D *nrm_before, int *flag, double eta2, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (ldv % 4 == 0 && !(((uintptr_t)V | (uintptr_t)w) & 15)) {
-            k_gemv_n_norm_f4<<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, part, tk, nrm);
+            if (ncol <= kSmallCols) k_gemv_n_norm_f4<kSmallCols><<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, part, tk, nrm);
+            else k_gemv_n_norm_f4<><<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, part, tk, nrm);
             return;
         }
     }
-    k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, nullptr, part, tk, nrm, nrm_before, flag, eta2);
+    if (ncol <= kSmallCols)
+        k_gemv_n_norm<T, kSmallCols><<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, nullptr, part, tk, nrm, nrm_before, flag, eta2);
+    else
+        k_gemv_n_norm<T><<<g, kThreads, 0, s>>>(V, ldv, ncol, h, w, n, nullptr, part, tk, nrm, nrm_before, flag, eta2);
 }
 
 template <class T, class HT = T>
@@ -1868,6 +1877,199 @@ extern "C" int tg_coarse_gmresdr(tg_op *op, int transpose, const void *b_fine, i
 }
 
 // ============================================================================= adjoint
+// ============================================================================= Arnoldi-E
+namespace tg {
+
+// Orthogonalises column j of V (leading dimension ldv) against columns 0..j-1 by classical
+// Gram-Schmidt applied twice and normalises it; *kept = false (and nothing normalised) when
+// less than drop_rel of its norm survives, i.e. the column lies in the span of the others.
+template <class T>
+static int cgs2_column(tg_op *op, T *V, size_t ldv, int n, int j, double drop_rel, bool *kept, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    T *w = V + (size_t)j * ldv;
+    TG_CHECK(red_ready(op, (size_t)num_sms() * 8 * (j + 2) * sizeof(D), s));
+    char *sm = wsp<char>(op, S_SMALL);
+    D *h1 = reinterpret_cast<D *>(sm + SmallArea::arn_h1);
+    D *h2 = reinterpret_cast<D *>(sm + SmallArea::arn_h2);
+    double *nrm = reinterpret_cast<double *>(sm + SmallArea::arn_nrm);
+    double *inv = nrm + 4;
+    D *part = wsp<D>(op, S_PART);
+    unsigned *tk = wsp<unsigned>(op, S_TICKET);
+    const int g = grid_for(n, 8);
+    double before = 0.0, after = 0.0;
+    if (j == 0) {
+        TG_CHECK(dot_host<T>(op, w, nullptr, n, &before, nullptr, s));
+        after = before;
+        TG_CHECK_CUDA(cudaMemcpyAsync(nrm, &after, sizeof(double), cudaMemcpyHostToDevice, s));
+    } else {
+        bool piped = false;
+        int gbt = 1;
+        TG_PROF(P_GEMV_T, (double)(j + 1) * n * sizeof(T), 2.0 * (j + 1) * n, gbt = gemv_t_part_launch<T>(V, ldv, j + 1, w, n, part, s, &piped));
+        TG_PROF(P_SUM_PART, 0, 0, k_sum_part<D><<<(j + 1 + 7) / 8, 256, 0, s>>>(part, gbt, j + 1, h1, 0));
+        TG_PROF(P_GEMV_N, (j + 2.0) * n * sizeof(T), 2.0 * j * n,
+                gemv_n_norm_launch<T>(g, V, ldv, j, h1, w, n, part, tk, nrm, nullptr, nullptr, 0.0, s));
+        TG_PROF(P_GEMV_T, (double)(j + 1) * n * sizeof(T), 2.0 * j * n, gbt = gemv_t_part_launch<T>(V, ldv, j, w, n, part, s, &piped));
+        TG_PROF(P_SUM_PART, 0, 0, k_sum_part<D><<<(j + 7) / 8, 256, 0, s>>>(part, gbt, j, h2, 0));
+        TG_PROF(P_GEMV_N, (j + 2.0) * n * sizeof(T), 2.0 * j * n,
+                gemv_n_norm_launch<T>(g, V, ldv, j, h2, w, n, part, tk, nrm, nullptr, nullptr, 0.0, s));
+        TG_LAUNCH_CHECK();
+        TG_CHECK(readback(op, h1 + j, sizeof(D), s));
+        D hb;
+        memcpy(&hb, op->pin.p, sizeof(D));
+        before = dnorm2(hb);
+        TG_CHECK(readback(op, nrm, sizeof(double), s));
+        memcpy(&after, op->pin.p, sizeof(double));
+    }
+    *kept = after > drop_rel * drop_rel * before && after > 0.0;
+    if (*kept) {
+        TG_PROF(P_SMALL, 0, 1, launch_inv_sqrt(s, nrm, inv));
+        TG_PROF(P_SCALE, 2.0 * n * sizeof(T), n, k_scale_by<T><<<g, kThreads, 0, s>>>(w, n, inv));
+        TG_LAUNCH_CHECK();
+    }
+    return TG_OK;
+}
+
+// Rayleigh-Ritz on span(S) (cols orthonormal columns, leading dimension ld) with W = A S:
+// H = S^H W, WW = W^H W, the small dense kernel in Rayleigh-Ritz mode (ordered Ritz pairs,
+// k kept, k + 1 if a pair would split); then Y = S P_k and u = S z (Ritz vector start_q).
+template <class T>
+static int rayleigh_ritz(tg_op *op, const T *S, const T *W, size_t ld, int n, int cols, int k, int nev,
+                         double rtolev, int start_q, T *Y, T *u, GdrInfo *info_h, cudaStream_t s) {
+    using D = typename ST<T>::D;
+    const int m = cols;
+    TG_CHECK(wsx(op, S_AE_H, (size_t)m * m * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_WW, (size_t)m * m * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_P, (size_t)(m + 1) * (m + 2) * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_Z, (size_t)(m + 1) * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_TH, (size_t)2 * m * 8));
+    TG_CHECK(wsx(op, S_AE_WR, (size_t)m * 8));
+    TG_CHECK(wsx(op, S_AE_WI, (size_t)m * 8));
+    TG_CHECK(wsx(op, S_AE_ORD, (size_t)m * 4));
+    TG_CHECK(wsx(op, S_AE_ERES, (size_t)m * 8));
+    TG_CHECK(wsx(op, S_AE_WORK, ((size_t)(m + 1) * m + 2 * (size_t)m * m + 3 * (size_t)m + 4) * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_YW, (size_t)m * m * 16));
+    TG_CHECK(wsx(op, S_AE_GW, (size_t)m * m * 16));
+    TG_CHECK(wsx(op, S_AE_INFO, sizeof(GdrInfo)));
+    TG_CHECK(wsx(op, S_AE_DUM, (size_t)(m + 2) * (m + 2) * sizeof(T)));
+    T *H = wsp<T>(op, S_AE_H), *WW = wsp<T>(op, S_AE_WW);
+    TG_CHECK(gram<T>(op, S, W, ld, m, n, 0, reinterpret_cast<D *>(H), s));
+    TG_CHECK(gram<T>(op, W, W, ld, m, n, 1, reinterpret_cast<D *>(WW), s));
+    GdrArgs<T> a;
+    T *dum = wsp<T>(op, S_AE_DUM);
+    a.H = H; a.ldh = m; a.c = dum; a.m = m; a.k = k; a.nev = nev; a.rtolev = rtolev;
+    a.d = dum; a.res = dum; a.z = wsp<T>(op, S_AE_Z);
+    a.theta = wsp<double>(op, S_AE_TH); a.wr = wsp<double>(op, S_AE_WR); a.wi = wsp<double>(op, S_AE_WI);
+    a.order = wsp<int>(op, S_AE_ORD); a.eres = wsp<double>(op, S_AE_ERES); a.P = wsp<T>(op, S_AE_P);
+    a.Hnew = dum; a.cnew = dum; a.work = wsp<T>(op, S_AE_WORK); a.ywork = wsp<cplx>(op, S_AE_YW);
+    a.gwork = wsp<cplx>(op, S_AE_GW); a.info = wsp<GdrInfo>(op, S_AE_INFO);
+    a.mode = 1;
+    a.WW = WW;
+    a.start_q = start_q;
+    cudaError_t le = cudaSuccess;
+    TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m, le = launch_gmresdr_restart<T>(a, s));
+    if (le != cudaSuccess) return cuda_status(le, "launching the Rayleigh-Ritz step");
+    TG_CHECK(readback(op, a.info, sizeof(GdrInfo), s));
+    memcpy(info_h, op->pin.p, sizeof(GdrInfo));
+    if (info_h->status) {
+        set_error("Rayleigh-Ritz: the QR iteration did not converge");
+        return TG_NOT_CONVERGED;
+    }
+    const int kk = info_h->kk;
+    TG_CHECK(tsm<T>(S, ld, m, a.P, m + 1, kk, Y, ld, n, s));
+    TG_CHECK(tsm<T>(S, ld, m, a.z, m, 1, u, ld, n, s));
+    return TG_OK;
+}
+
+// Arnoldi-E improvement of a deflation basis on the fine grid (see tg_improve_defl).
+template <class T>
+static int improve_impl(tg_op *op, tg_defl *d, int m, int cycles, int nstart, int nev, double rtolev,
+                        double *theta_out, tg_stats *st, cudaStream_t s) {
+    const DevOp &A = pick(op, TG_FINE, d->transposed ? 1 : 0);
+    const DevOp32 &A32 = pick32(op, TG_FINE, d->transposed ? 1 : 0);
+    const int n = op->n, k = d->kk, p = m - k;
+    const size_t ld = ((size_t)n + 63) / 64 * 64;     // whole 64-row chunks: the pipelined V^H w applies
+    TG_CHECK(wsx(op, S_AE_S, ld * (m + 2) * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_W, ld * (m + 2) * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_HA, (size_t)(p + 1) * p * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_Y, ld * (k + 2) * sizeof(T)));
+    TG_CHECK(wsx(op, S_AE_U, ld * sizeof(T)));
+    T *S = wsp<T>(op, S_AE_S), *W = wsp<T>(op, S_AE_W), *Ha = wsp<T>(op, S_AE_HA);
+    T *Y = wsp<T>(op, S_AE_Y), *u = wsp<T>(op, S_AE_U);
+    TG_CHECK_CUDA(cudaMemsetAsync(S, 0, ld * (m + 2) * sizeof(T), s));
+    int64_t mvps = 0;
+    GdrInfo info{};
+    // Rayleigh-Ritz on span(Y) orders the given vectors as Ritz vectors
+    int cols = 0;
+    for (int c = 0; c < k; ++c) {
+        TG_CHECK_CUDA(cudaMemcpyAsync(S + (size_t)cols * ld, d->Y.as<T>() + (size_t)c * n, (size_t)n * sizeof(T),
+                                      cudaMemcpyDeviceToDevice, s));
+        bool kept = false;
+        TG_CHECK(cgs2_column<T>(op, S, ld, n, cols, 1e-10, &kept, s));
+        if (kept) ++cols;
+    }
+    TG_ARG(cols == k, "the deflation basis is numerically rank deficient");
+    for (int c = 0; c < cols; ++c) TG_CHECK(launch_apply<T>(A, A32, S + (size_t)c * ld, W + (size_t)c * ld, s));
+    mvps += cols;
+    TG_CHECK(rayleigh_ritz<T>(op, S, W, ld, n, cols, k, nev, rtolev, 0 % nstart, Y, u, &info, s));
+    int kk = info.kk, done = 0;
+    for (int cyc = 0; cyc < cycles; ++cyc) {
+        // Krylov part from u: S[:, 0..p] by Arnoldi (classical Gram-Schmidt twice)
+        TG_CHECK_CUDA(cudaMemcpyAsync(S, u, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        bool kept = false;
+        TG_CHECK(cgs2_column<T>(op, S, ld, n, 0, 0.0, &kept, s));
+        for (int j = 0; j < p; ++j) TG_CHECK((arnoldi_step<T, T>(op, A, A32, S, ld, n, j, Ha, p + 1, s)));
+        mvps += p;
+        cols = p + 1;
+        // then the current approximate eigenvectors (u lies in their span: one drops out)
+        for (int c = 0; c < kk && cols < m + 1; ++c) {
+            TG_CHECK_CUDA(cudaMemcpyAsync(S + (size_t)cols * ld, Y + (size_t)c * ld, (size_t)n * sizeof(T),
+                                          cudaMemcpyDeviceToDevice, s));
+            TG_CHECK(cgs2_column<T>(op, S, ld, n, cols, 1e-10, &kept, s));
+            if (kept) ++cols;
+        }
+        for (int c = 0; c < cols; ++c) TG_CHECK(launch_apply<T>(A, A32, S + (size_t)c * ld, W + (size_t)c * ld, s));
+        mvps += cols;
+        TG_CHECK(rayleigh_ritz<T>(op, S, W, ld, n, cols, k, nev, rtolev, (cyc + 1) % nstart, Y, u, &info, s));
+        kk = info.kk;
+        done = cyc + 1;
+        if (rtolev > 0 && nev > 0 && info.nconv >= nev) break;
+    }
+    if (theta_out) {
+        TG_CHECK(readback(op, wsp<double>(op, S_AE_TH), (size_t)2 * kk * 8, s));
+        memcpy(theta_out, op->pin.p, (size_t)2 * kk * 8);
+    }
+    // the improved basis replaces the handle's and its projection data are rebuilt
+    if (kk != d->kk) TG_CHECK(d->Y.ensure((size_t)n * kk * sizeof(T)));
+    TG_CHECK_CUDA(cudaMemcpy2DAsync(d->Y.p, (size_t)n * sizeof(T), Y, ld * sizeof(T), (size_t)n * sizeof(T), kk,
+                                    cudaMemcpyDeviceToDevice, s));
+    d->kk = kk;
+    TG_CHECK(build_defl<T>(op, d->transposed ? 1 : 0, d, s));
+    mvps += kk;
+    if (st) {
+        st->cycles = done;
+        st->mvps = mvps;
+        st->kk = kk;
+        st->eig_converged = info.nconv;
+        st->status = TG_OK;
+    }
+    return TG_OK;
+}
+
+}  // namespace tg
+
+extern "C" int tg_improve_defl(tg_op *op, tg_defl *defl, int m, int cycles, int nstart, int nev, double rtolev,
+                               double *theta_out, tg_stats *stats, void *stream) {
+    TG_ARG(op && defl, "NULL argument");
+    TG_ARG(defl->n == op->n, "deflation handle does not match this operator");
+    TG_ARG(m > defl->kk && m <= kMaxM, "need kk < m <= %d (kk = %d, m = %d)", kMaxM, defl->kk, m);
+    TG_ARG(m + 2 <= op->n, "m too large for the problem size");
+    TG_ARG(cycles >= 0 && nstart >= 1 && nstart <= defl->kk, "need cycles >= 0 and 1 <= nstart <= kk");
+    TG_ARG(nev >= 0 && nev <= defl->kk && rtolev >= 0, "bad nev / rtolev");
+    cudaStream_t s = (cudaStream_t)stream;
+    return op->cplx_ ? improve_impl<cplx>(op, defl, m, cycles, nstart, nev, rtolev, theta_out, stats, s)
+                     : improve_impl<double>(op, defl, m, cycles, nstart, nev, rtolev, theta_out, stats, s);
+}
+
 extern "C" int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *dkappa, void *stream) {
     TG_ARG(op && x && lambda && dkappa, "NULL argument");
     TG_ARG(op->kind == TG_VARK2D, "the kappa gradient needs a TG_VARK2D operator");

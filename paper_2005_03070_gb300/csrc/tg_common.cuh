@@ -332,6 +332,7 @@ template <> struct Apply<cplx> {
 constexpr int kMaxM = 256;              // largest GMRES-DR / GMRES subspace dimension m, and
                                         // largest deflation basis k
 constexpr int kMaxCols = kMaxM + 2;     // coefficient vectors staged per block (m + 1 columns)
+constexpr int kSmallCols = 136;         // the staging size of the kernels' common instance
 
 // ----------------------------------------------------------------------------- launch shape
 constexpr int kThreads = 256;

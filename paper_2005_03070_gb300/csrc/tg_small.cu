@@ -936,6 +936,17 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
     __shared__ int piv_s[kMaxM + 1];
 
     long long t_mark = clock64();
+    const bool rr_mode = a.mode == 1;
+    if (rr_mode) {
+        // Rayleigh-Ritz: the eigen matrix is H itself
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = e % m, j = e / m;
+            W[e] = a.H[i + (size_t)j * ldh];
+            Z[e] = (i == j) ? Cx<T>::one() : Cx<T>::zero();
+        }
+        if (threadIdx.x == 0) a.info->rnorm = 0.0;
+        __syncthreads();
+    } else {
     // ---- 1. least squares: d = argmin ||c - Hbar d||, res = c - Hbar d
     for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
         int i = e % rows, j = e / rows;
@@ -975,6 +986,7 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
 
     __syncthreads();
     if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[1] = _t - t_mark; t_mark = _t; }
+    }   // steps 1-2: GMRES-DR restart only
     // ---- 3. eigen-decomposition of M: Hessenberg, Schur, eigenvalues
     hessenberg<T>(W, m, Z, vtmp);
     __syncthreads();
@@ -1073,14 +1085,14 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
     }
     __syncthreads();
     __shared__ double znorm_s;
-    if (warp == 0) {
+    if (warp == 0 && !rr_mode) {
         double z2 = 0.0;
         for (int i = lane; i < rows; i += 32) z2 += Cx<T>::ab2(a.z[i]);
         z2 = warp_sum(z2);
         if (lane == 0) znorm_s = sqrt(z2);
     }
     __syncthreads();
-    const double znorm = znorm_s;
+    const double znorm = rr_mode ? 0.0 : znorm_s;
     for (int q = warp; q < kk; q += nwarps) {
         cplx *g = G + (size_t)q * m;
         double nr = 0.0;
@@ -1092,7 +1104,51 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
         // residual ||Hbar g - theta [g; 0]|| = |g_m| ||z||: an eigenpair of
         // H_m + |h|^2 f e_m^T satisfies H_m g - theta g = -|h|^2 f g_m, and the last row of
         // Hbar g is h g_m, so the residual vector is g_m z with z = [-|h|^2 f; h]
-        if (lane == 0) a.eres[q] = sqrt(abs2(g[m - 1])) * znorm;
+        if (!rr_mode) {
+            if (lane == 0) a.eres[q] = sqrt(abs2(g[m - 1])) * znorm;
+        } else {
+            // Rayleigh-Ritz: ||W g - theta Q g||^2 = g^H (W^H W) g - |theta|^2 for Q^H W g = theta g
+            double acc = 0.0;
+            for (int i = lane; i < m; i += 32) {
+                cplx wg = {0.0, 0.0};
+                for (int l = 0; l < m; ++l) {
+                    const T w = a.WW[i + (size_t)l * m];
+                    cplx wc;
+                    if constexpr (sizeof(T) == sizeof(double)) wc = mkc(*reinterpret_cast<const double *>(&w), 0.0);
+                    else wc = *reinterpret_cast<const cplx *>(&w);
+                    wg = wg + wc * g[l];
+                }
+                acc += (conj(g[i]) * wg).re;
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                const int j = ord[q];
+                a.eres[q] = sqrt(fmax(acc - (wr[j] * wr[j] + wi[j] * wi[j]), 0.0));
+            }
+        }
+    }
+    __syncthreads();
+    if (rr_mode && warp == 0 && a.start_q < kk) {
+        // coefficients of the start vector: Ritz vector start_q with its largest entry made
+        // real and positive (ties: the smallest index); real problems keep the real part
+        const cplx *g = G + (size_t)a.start_q * m;
+        double best = -1.0;
+        int imax = 0;
+        for (int i = lane; i < m; i += 32)
+            if (abs2(g[i]) > best) { best = abs2(g[i]); imax = i; }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, imax, o);
+            if (ob > best || (ob == best && oi < imax)) { best = ob; imax = oi; }
+        }
+        imax = __shfl_sync(0xffffffffu, imax, 0);
+        best = __shfl_sync(0xffffffffu, best, 0);
+        const cplx ph = conj(g[imax]) * (1.0 / sqrt(best));
+        for (int i = lane; i < m; i += 32) {
+            const cplx v = g[i] * ph;
+            if constexpr (sizeof(T) == sizeof(double)) reinterpret_cast<double *>(a.z)[i] = v.re;
+            else reinterpret_cast<cplx *>(a.z)[i] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1167,14 +1223,16 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
     }
     __syncthreads();
     const int nc = ncol_s;     // == kk
-    // append z as column kk
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) P[i + (size_t)nc * rows] = a.z[i];
+    // append z as column kk (GMRES-DR restart only)
+    if (!rr_mode)
+        for (int i = threadIdx.x; i < rows; i += blockDim.x) P[i + (size_t)nc * rows] = a.z[i];
     __syncthreads();
     // classical Gram-Schmidt applied twice over the nc + 1 columns (length m+1): per column,
     // the projections on the previous columns in parallel, then the update in parallel
     __shared__ T proj_s[kMaxM + 2];
     __shared__ double nrm_s;
-    for (int c = 0; c <= nc; ++c) {
+    const int clast = rr_mode ? nc - 1 : nc;
+    for (int c = 0; c <= clast; ++c) {
         T *pc = P + (size_t)c * rows;
         for (int pass = 0; pass < 2; ++pass) {
             for (int q = threadIdx.x; q < c; q += blockDim.x) {
@@ -1205,6 +1263,7 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
 
     __syncthreads();
     if (threadIdx.x == 0) { long long _t = clock64(); a.info->phase[6] = _t - t_mark; t_mark = _t; }
+    if (rr_mode) return;
     // ---- 7. Hnew = P_{k+1}^H Hbar P_k  ((kk+1) x kk, ld m+1 into a.Hnew), cnew = P_{k+1}^H res
     // T1 = Hbar P_k ((m+1) x kk) into W
     for (int e = threadIdx.x; e < rows * nc; e += blockDim.x) {

@@ -41,6 +41,16 @@ struct GdrArgs {
     cplx *gwork;     // scratch: m * m complex
     GdrInfo *info;
     int smem;        // set by the launcher: W and Z in shared memory
+    // Rayleigh-Ritz mode (mode = 1, the Arnoldi-E improvement): H is a dense m x m matrix
+    // Q^H A Q (ld ldh) of an orthonormal Q; the least-squares solve, the harmonic
+    // modification and the restart matrices are skipped; the Ritz pairs of H are ordered and
+    // selected as above, P gets the orthonormal m x kk basis of the kept span, eres the
+    // residuals ||A Q g - theta Q g|| = sqrt(g^H WW g - |theta|^2) (WW = (A Q)^H A Q, ld m,
+    // ||g|| = 1), and z the coefficients of Ritz vector start_q (phase fixed so that its
+    // largest entry is real and positive; real problems keep the real part).
+    int mode = 0;
+    const T *WW = nullptr;
+    int start_q = 0;
 };
 
 struct GivensState {

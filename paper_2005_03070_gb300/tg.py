@@ -33,7 +33,8 @@ PREC = {"f64": TG_F64, "f32_ir": TG_F32_IR}
 EXPORTS = [
     "tg_status_string", "tg_last_error", "tg_setup_operator", "tg_destroy_op", "tg_op_size", "tg_apply",
     "tg_prolong", "tg_restrict", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
-    "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_solve_idr", "tg_adjoint_solve", "tg_kappa_gradient",
+    "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_solve_idr", "tg_improve_defl", "tg_adjoint_solve",
+    "tg_kappa_gradient",
     "tg_harmonic_ritz", "tg_harmonic_ritz_noalloc", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
     "tg_batch_create", "tg_batch_layout", "tg_batch_setup", "tg_batch_solve", "tg_destroy_batch",
 ]
@@ -88,6 +89,7 @@ def load() -> C.CDLL:
         "tg_project": (i32, [vp, vp, vp, vp, vp]),
         "tg_solve_proj": (i32, [vp, vp, i32, i32, vp, vp, i32, dbl, i32, i32, i32, i64, C.POINTER(TgStats), vp]),
         "tg_solve_idr": (i32, [vp, vp, i32, vp, vp, i32, dbl, i32, i32, i32, vp, dbl, i64, C.POINTER(TgStats), vp]),
+        "tg_improve_defl": (i32, [vp, vp, i32, i32, i32, i32, dbl, C.POINTER(C.c_double), C.POINTER(TgStats), vp]),
         "tg_adjoint_solve": (i32, [vp, vp, vp, vp, vp, vp, dbl, i32, i32, i32, C.POINTER(TgStats), vp]),
         "tg_kappa_gradient": (i32, [vp, vp, vp, vp, vp]),
         "tg_harmonic_ritz": (i32, [vp, i32, i32, i32, vp, vp, vp, C.POINTER(i32), vp]),
@@ -305,6 +307,20 @@ class Deflation:
 
     def project(self, x, r, stream=None):
         _check(_lib.tg_project(self.op.handle, self._h, _ptr(x), _ptr(r), _stream(stream)), "tg_project")
+
+    def improve(self, m, cycles, nstart, nev=0, rtolev=0.0, stream=None):
+        """tg_improve_defl: Arnoldi-E(m, kk) cycles on the fine grid; returns (kept Ritz values
+        as a complex numpy array, stats dict)."""
+        import numpy as np
+        th = (C.c_double * (2 * (self.kk + 1)))()
+        st = TgStats()
+        _check(_lib.tg_improve_defl(self.op.handle, self._h, m, cycles, nstart, nev, rtolev, th, C.byref(st),
+                                    _stream(stream)), "tg_improve_defl")
+        kk = C.c_int()
+        _check(_lib.tg_defl_copy(self._h, 0, None, C.byref(kk), None), "tg_defl_copy")
+        self.kk = kk.value
+        a = np.array(th[:2 * self.kk]).reshape(-1, 2)
+        return a[:, 0] + 1j * a[:, 1], st.as_dict()
 
 
 def harmonic_ritz(Hbar_colmajor: torch.Tensor, m: int, k: int, complex_: bool = False, stream=None):

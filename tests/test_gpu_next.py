@@ -199,3 +199,39 @@ def test_projection_k150(tg):
     defl.project(xt, rt)
     assert rel(host(rt), rr) <= 1e-9
     assert rel(host(xt), xr) <= 1e-8
+
+
+@pytest.mark.parametrize("cycles", [0, 1, 3])
+def test_arnoldi_e_matches_oracle(tg, cycles):
+    """Arnoldi-E(24, 8) on Example 1's operator at 31^2 (complex Ritz pairs among the kept
+    ones): the kept Ritz values and the improved span agree with the oracle's."""
+    from oracle.gmresdr import arnoldi_e
+    N, k, m = 31, 8, 24
+    top, oop = tg.Operator("exp2d", N, EX1), OOp(EXP2D, N, EX1)
+    Y0 = gi.random_dense((oop.n, k), 54)
+    Yo, th_o, eres_o, done_o, _ = arnoldi_e(oop.apply, Y0, m, cycles, 4)
+    defl = top.defl_from_basis(cu(Y0.T.copy()), k)
+    th, st = defl.improve(m, cycles, 4)
+    assert st["cycles"] == done_o == cycles and defl.kk == Yo.shape[1]
+    assert np.max(np.abs(np.sort_complex(th) - np.sort_complex(th_o))) <= 1e-8 * np.max(np.abs(th_o))
+    Yg = host(defl.copy(0)).T
+    Qa, Qb = np.linalg.qr(Yo)[0], np.linalg.qr(Yg)[0]
+    c = np.clip(np.linalg.svd(Qa.T @ Qb, compute_uv=False), 0, 1)
+    assert np.max(np.sqrt(1 - c ** 2)) <= 1e-6
+
+
+def test_arnoldi_e_improves_moved_vectors(tg):
+    """The phase-2 use: coarse vectors moved to the fine grid, improved by Arnoldi-E until
+    the 6 smallest pairs reach residual 1e-3 |theta|; the two-grid solve still reaches the
+    direct solution."""
+    N = 127
+    top, oop = tg.Operator("exp2d", N, EX1), OOp(EXP2D, N, EX1)
+    b = gi.rhs(oop.n, 55)
+    bt = cu(b)
+    xc, defl, _, _ = top.coarse_gmresdr(bt, 40, 20, rtolev=1e-3, rtol=1e-8)
+    th, st = defl.improve(50, 30, 6, nev=6, rtolev=1e-3)
+    assert st["eig_converged"] >= 6 and st["cycles"] <= 30
+    x = top.prolong(xc)
+    status, s2 = top.solve(bt, x, defl, rtol=1e-10, ncyc=20, restart_mvps=0)
+    assert status == tg.TG_OK
+    assert rel(host(x), twogrid.exact_solution(oop, b)) <= 1e-6

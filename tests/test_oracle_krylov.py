@@ -425,3 +425,41 @@ def test_idr_proj_brute_force(kind, N, beta):
         res = krylov.idr_proj(op.apply, b, np.zeros(op.n), defl, P, rtol=1e-11, ncyc=ncyc,
                               restart_mvps=cap, max_mvps=20000)
         assert res.converged and _rel(res.x, xs) < 1e-8
+
+
+def test_arnoldi_e_symmetric_monotone_and_interlacing():
+    """Every Arnoldi-E cycle works in a subspace containing the previous span(Y), so for a
+    symmetric matrix (cd2d with beta = 0) the j-th smallest kept Ritz value can only go down
+    (Courant-Fischer) and never below the j-th eigenvalue (Cauchy interlacing); the values
+    approach the closed-form eigenvalues."""
+    from oracle.gmresdr import arnoldi_e
+    N, k = 31, 8
+    op = Operator(CD2D, N, (0.0,))
+    lam = cd2d_eigenvalues(N, 0.0)
+    Y = gi.random_dense((op.n, k), 31)
+    prev = None
+    for c in range(0, 7):
+        _, th, _, _, _ = arnoldi_e(op.apply, Y, 30, c, 4)
+        t = np.sort(th.real)[:k]
+        assert np.all(np.abs(th.imag) == 0)
+        assert np.all(t >= lam[:k] - 1e-9 * lam[-1])
+        if prev is not None:
+            assert np.all(t <= prev + 1e-9 * lam[-1])
+        prev = t
+    assert abs(prev[0] - lam[0]) <= 1e-6 * lam[0]
+
+
+def test_arnoldi_e_keeps_an_invariant_subspace():
+    """Exact eigenvectors (closed form for beta = 0: products of sines) give Ritz values
+    equal to their eigenvalues with zero residual, cycle after cycle."""
+    from oracle.gmresdr import arnoldi_e
+    N = 31
+    op = Operator(CD2D, N, (0.0,))
+    h = 1.0 / (N + 1)
+    t = np.arange(1, N + 1) * h
+    modes = [(1, 1), (1, 2), (2, 1), (2, 2), (1, 3), (3, 1)]
+    Y = np.stack([np.outer(np.sin(q * np.pi * t), np.sin(p * np.pi * t)).reshape(-1) for p, q in modes], axis=1)
+    exact = np.sort([(4 - 2 * np.cos(p * np.pi * h) - 2 * np.cos(q * np.pi * h)) / h**2 for p, q in modes])
+    _, th, eres, _, _ = arnoldi_e(op.apply, Y, 20, 2, 2)
+    assert np.allclose(np.sort(th.real), exact, rtol=1e-10)
+    assert np.max(eres) <= 1e-9 * exact[-1]
