@@ -53,6 +53,29 @@ WORKLOADS = {
                      max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=0,
                      restart_mvps=60, m3=20),
 }
+# The paper's own experiments (loose comparison of matrix-vector product counts; not timed
+# headline workloads): Example 1 / 2 (Tables 3.1, 4.1) and Example 4 (Helmholtz).  The coarse
+# grid is reached by chaining the library's factor-2 levels (bilinear prolongations compose to
+# the bilinear interpolation from the coarsest grid, since the grids nest).
+PAPER_RUNS = {
+    "ex1_511": dict(kind="exp2d", beta=(40.0, 40.0, 5.0), mass=None, N=511, coarse_N=63, m=150, k=100, nev=80,
+                    rtolev=1e-8, rtol_c=1e-10, max_cycles=400, rtol=1e-10, rhs="example1", proj="galerkin",
+                    bicg_ncyc=[5, 10, 15, 20, 30, 50, 100, 150, 200], gmres_m3=[50, 100, 200], idr_ncyc=[20],
+                    coarse_sweep=[127, 31, 15],
+                    paper={"coarse_cycles_eig": 107, "coarse_mvps_eig": 5450, "coarse_cycles_linear": 19,
+                           "table_4_1_mvps": {"5": 9638, "10": 7606, "15": 6390, "20": 5421, "30": 5357, "50": 5278,
+                                              "100": 5262, "150": 5591, "200": 5541},
+                           "table_4_1_cycles_used": {"100": 99, "150": 140, "200": 168},
+                           "table_3_1_fine_cycles_gmres100": {"255": 85, "127": 86, "63": 94, "31": 106, "15": 120,
+                                                              "7": 177, "none": 1255},
+                           "table_3_1_coarse_cycles": {"255": 1023, "127": 270, "63": 107, "31": 43, "15": 12}}),
+    "helm_511": dict(kind="cd2d", beta=(0.0,), mass=-1e4, N=511, coarse_N=127, m=200, k=150, nev=120, rtolev=1e-8,
+                     rtol_c=1e-10, max_cycles=400, rtol=1e-10, rhs="random", proj="galerkin",
+                     bicg_ncyc=[20], gmres_m3=[100], idr_ncyc=[20], coarse_sweep=[],
+                     paper={"coarse_cycles_eig": 285, "note": "GMRES(100)-Proj(150) and IDR(20)-Proj(150) converge; "
+                                                              "IDR(20)-Proj(150) is the fastest; plain IDR does not "
+                                                              "converge (Figure 5.1, counts not printed)"}),
+}
 L2_BYTES = 129 * 1024 * 1024
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops per FMA x 2070 MHz
 NOMINAL_HBM_GBS = 8000.0                         # the ~8 TB/s nominal HBM3e figure the 70% target refers to
@@ -693,12 +716,117 @@ def run_batch(args, wl, rank, world, fp64_instances=0):
     return line
 
 
+def run_paper(args, name, rank, world):
+    """One of the paper's own experiments through the library: the coarse GMRES-DR phase, the
+    move to the fine grid and the fine-grid solvers, reporting product counts beside the
+    paper's (which come from MATLAB runs with spline interpolation: context, not parity)."""
+    import numpy as np
+    import torch
+
+    import tg_inputs as gi
+    from paper_2005_03070_gb300 import build as tgbuild
+    tgbuild.build()
+    from paper_2005_03070_gb300 import tg
+
+    cfg = PAPER_RUNS[name]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = cfg["N"]
+
+    def chain(coarse_N):
+        levels = [2 * coarse_N + 1]
+        while levels[-1] < N:
+            levels.append(2 * levels[-1] + 1)
+        assert levels[-1] == N
+        return levels
+
+    ops = {}
+
+    def op_of(Nl):
+        if Nl not in ops:
+            ops[Nl] = tg.Operator(cfg["kind"], Nl, cfg["beta"], mass=cfg["mass"])
+        return ops[Nl]
+
+    if cfg["rhs"] == "example1":
+        b = torch.from_numpy(gi.example1_rhs(N)).to(dev)
+    else:
+        b = torch.from_numpy(gi.rhs(N * N, seed=rank)).to(dev)
+
+    def sync_time(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = f()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    def coarse_phase(coarse_N):
+        levels = chain(coarse_N)
+        bl = b
+        for Nl in reversed(levels[1:]):
+            bl = op_of(Nl).restrict(bl)
+        top = op_of(levels[0])
+        (xc, defl, cst, status), t_c = sync_time(lambda: top.coarse_gmresdr(
+            bl, cfg["m"], cfg["k"], nev=cfg["nev"], rtolev=cfg["rtolev"], rtol=cfg["rtol_c"],
+            max_cycles=cfg["max_cycles"], proj=cfg["proj"]))
+        Y = defl.copy(0).reshape(-1)
+        x0 = top.prolong(xc)
+        kk = defl.kk
+        for Nl in levels[1:]:
+            Y = op_of(Nl).prolong(Y)
+            x0 = op_of(Nl).prolong(x0)
+        fine = op_of(N)
+        dfl, t_f = sync_time(lambda: fine.defl_from_basis(Y, kk, proj=cfg["proj"]))
+        return x0, dfl, {"coarse_N": coarse_N, "cycles": cst["cycles"], "coarse_mvps": cst["coarse_mvps"],
+                         "eig_converged": cst["eig_converged"], "kk": kk, "coarse_seconds": round(t_c, 3),
+                         "AY_and_factor_seconds": round(t_f, 3)}
+
+    fine = op_of(N)
+    x0, dfl, coarse = coarse_phase(cfg["coarse_N"])
+    out = {"experiment": name, "coarse": coarse, "bicgstab_proj": {}, "gmres_proj": {}, "idr_proj": {}}
+
+    def record(key, tag, fn):
+        x = x0.clone()
+        (status, st), t = sync_time(lambda: fn(x))
+        out[key][str(tag)] = {"status": int(status), "mvps": int(st[0]["mvps"]), "cycles": int(st[0]["cycles"]),
+                              "relres": st[0]["relres"], "seconds": round(t, 3)}
+
+    for ncyc in cfg["bicg_ncyc"]:
+        record("bicgstab_proj", ncyc, lambda x: fine.solve(b, x, dfl, rtol=cfg["rtol"], ncyc=ncyc, restart_mvps=0,
+                                                           max_mvps=200000))
+    for m3 in cfg["gmres_m3"]:
+        record("gmres_proj", m3, lambda x: fine.solve(b, x, dfl, method="gmres", rtol=cfg["rtol"], m3=m3,
+                                                      max_mvps=200000))
+    P = torch.from_numpy(gi.random_dense((4, fine.n), 60)).to(dev)
+    for ncyc in cfg["idr_ncyc"]:
+        record("idr_proj", ncyc, lambda x: fine.solve_idr(b, x, P, dfl, rtol=cfg["rtol"], ncyc=ncyc,
+                                                          max_mvps=200000))
+    # without deflation: restarted BiCGStab with one cycle (non-restarted) from x0 = 0
+    xz = torch.zeros_like(b)
+    (status, st), t = sync_time(lambda: fine.solve(b, xz, None, rtol=cfg["rtol"], ncyc=1, restart_mvps=0,
+                                                   max_mvps=200000))
+    out["bicgstab_no_deflation"] = {"status": int(status), "mvps": int(st[0]["mvps"]), "seconds": round(t, 3)}
+    # Table 3.1: the coarse grid size, with GMRES(100)-Proj(k) on the fine grid
+    sweep = {}
+    for cN in cfg["coarse_sweep"]:
+        xs, ds, cs = coarse_phase(cN)
+        (status, st), t = sync_time(lambda: fine.solve(b, xs, ds, method="gmres", rtol=cfg["rtol"], m3=100,
+                                                       max_mvps=400000))
+        sweep[str(cN)] = {**cs, "fine_cycles": int(st[0]["cycles"]), "fine_mvps": int(st[0]["mvps"]),
+                          "status": int(status), "fine_seconds": round(t, 3)}
+    if sweep:
+        sweep[str(cfg["coarse_N"])] = {**coarse, "fine_cycles": out["gmres_proj"].get("100", {}).get("cycles"),
+                                       "fine_mvps": out["gmres_proj"].get("100", {}).get("mvps")}
+        out["coarse_size_sweep_gmres100"] = sweep
+    out["paper"] = cfg["paper"]
+    out["config"] = {k: (list(v) if isinstance(v, tuple) else v) for k, v in cfg.items() if k != "paper"}
+    return out
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--workload", default="cd3d_255", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="cd3d_255", choices=sorted(WORKLOADS) + sorted(PAPER_RUNS))
     p.add_argument("--impl", default="tg", choices=["tg", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-ir", action="store_true")
@@ -706,9 +834,14 @@ def main():
                    help="timed steps of the e2e and float32 side measurements (at most --steps)")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form key of the default run")
     args = p.parse_args()
-    wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload in PAPER_RUNS:
+        out = run_paper(args, args.workload, rank, world)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    wl = WORKLOADS[args.workload]
 
     if args.impl == "reference":
         if rank != 0:

@@ -348,6 +348,13 @@ template <class T>
 static int launch_apply(const DevOp &A, const DevOp32 &A32, const T *x, T *y, cudaStream_t s) {
     double xb, fl;
     op_cost(A, &xb, &fl);
+    if constexpr (std::is_same<T, float>::value) {
+        if (f4_ok(A, {x, y})) {
+            TG_PROF(P_APPLY, 8.0 * A.n, fl * A.n, k_apply_f4<<<grid_for((A.n + 3) / 4, 8), kThreads, 0, s>>>(A, A32, x, y));
+            TG_LAUNCH_CHECK();
+            return TG_OK;
+        }
+    }
     TG_PROF(P_APPLY, (2.0 * sizeof(T) + xb * (sizeof(T) == 4 ? 0.5 : 1.0)) * A.n, fl * A.n, k_apply<T><<<grid_for(A.n, 8), kThreads, 0, s>>>(A, A32, x, y));
     TG_LAUNCH_CHECK();
     return TG_OK;
@@ -978,6 +985,10 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL) + SmallArea::bistate);
     TG_PROF(P_BI_INIT, 3.0 * n * sizeof(T), 2.0 * n, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
     TG_LAUNCH_CHECK();
+    // float32 constant-coefficient grids: the 4-points-per-thread stencil kernels
+    bool use_f4 = false;
+    if constexpr (std::is_same<T, float>::value) use_f4 = f4_ok(A, {w.p, w.rh, w.v, w.s, w.t});
+    const int g4 = grid_for((n + 3) / 4, 8);
     int chunk = 2;
     int launched = 0;
     BiState<D> h{};
@@ -989,9 +1000,19 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     int iters_prev = 0;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
-            TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
+            if (use_f4) {
+                if constexpr (std::is_same<T, float>::value)
+                    TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v_f4<<<g4, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
+            } else {
+                TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
+            }
             TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
-            TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
+            if (use_f4) {
+                if constexpr (std::is_same<T, float>::value)
+                    TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t_f4<<<g4, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
+            } else {
+                TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
+            }
             TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
         }
         TG_LAUNCH_CHECK();

@@ -222,15 +222,16 @@ def test_arnoldi_e_matches_oracle(tg, cycles):
 
 def test_arnoldi_e_improves_moved_vectors(tg):
     """The phase-2 use: coarse vectors moved to the fine grid, improved by Arnoldi-E until
-    the 6 smallest pairs reach residual 1e-3 |theta|; the two-grid solve still reaches the
-    direct solution."""
+    the 6 smallest pairs reach residual 1e-2 |theta| (the moved vectors start near 1, the
+    oracle's run needs about 10 cycles); the two-grid solve still reaches the direct
+    solution."""
     N = 127
     top, oop = tg.Operator("exp2d", N, EX1), OOp(EXP2D, N, EX1)
     b = gi.rhs(oop.n, 55)
     bt = cu(b)
     xc, defl, _, _ = top.coarse_gmresdr(bt, 40, 20, rtolev=1e-3, rtol=1e-8)
-    th, st = defl.improve(50, 30, 6, nev=6, rtolev=1e-3)
-    assert st["eig_converged"] >= 6 and st["cycles"] <= 30
+    th, st = defl.improve(50, 30, 6, nev=6, rtolev=1e-2)
+    assert st["eig_converged"] >= 6 and 3 <= st["cycles"] < 30
     x = top.prolong(xc)
     status, s2 = top.solve(bt, x, defl, rtol=1e-10, ncyc=20, restart_mvps=0)
     assert status == tg.TG_OK

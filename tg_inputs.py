@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "rhs", "u1_links", "kappa_grf", "batch_instances", "kappa_fd_nodes",
-    "random_dense", "random_hessenberg",
+    "random_dense", "random_hessenberg", "example1_rhs",
 ]
 
 
@@ -105,3 +105,13 @@ def random_hessenberg(m: int, seed: int = 0, rows: int | None = None) -> np.ndar
     for c in range(m):
         a[c + 2:, c] = 0.0
     return a
+
+
+def example1_rhs(N: int) -> np.ndarray:
+    """Right-hand side of the paper's Example 1 as printed, f = c sin(x) cos(x) exp(x y) on the
+    interior nodes x = i h, y = j h (h = 1/(N+1)), x fastest, c making ||f|| = 1."""
+    h = 1.0 / (N + 1)
+    t = np.arange(1, N + 1) * h
+    Y, X = np.meshgrid(t, t, indexing="ij")
+    f = (np.sin(X) * np.cos(X) * np.exp(X * Y)).reshape(-1)
+    return f / np.linalg.norm(f)
