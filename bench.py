@@ -324,6 +324,28 @@ def run_tg(args, wl, rank, world):
         setup_ir, fine_ir = (max_over_ranks(v) for v in split["f32_ir"])
         ir_ok = all(s == tg.TG_OK and st["relres"] <= wl["rtol"] for s, st, _ in infos_ir)
 
+    # GMRES(m3)-Proj on the same workload (the 3D configuration compares it with BiCGStab-Proj)
+    gmres = None
+    if wl["kind"] == "cd3d" and not args.no_gmres:
+        wg = dict(wl, method="gmres")
+        wl_saved = dict(wl)
+        wl.update(wg)
+        step(b, wl["precision"])
+        barrier()
+        ms_g, infos_g, _, _ = timed_steps(min(k_side, 2), wl["precision"])
+        barrier()
+        ms_g = max_over_ranks(ms_g)
+        setup_g, fine_g = (max_over_ranks(v) for v in split[wl["precision"]])
+        wl.clear()
+        wl.update(wl_saved)
+        sg = infos_g[-1][1]
+        gmres = {"method": f"GMRES({wl['m3']})-Proj({wl['k']})", "value": round(world * 1000.0 / ms_g, 5),
+                 "unit": "solves/s", "ms_per_step": round(ms_g, 3),
+                 "converged": all(s_ == tg.TG_OK and st_["relres"] <= wl["rtol"] for s_, st_, _ in infos_g),
+                 "fine_solve_ms": round(fine_g, 3), "fine_mvps": sg["mvps"], "fine_cycles": sg["cycles"],
+                 "fine_solve_only": round(world * 1000.0 / fine_g, 5),
+                 "bicgstab_fine_solve_ms": round(fine_ms, 3)}
+
     # per-kernel-class profile: one more step with a CUDA event pair around every launch
     # (eager launches, no graph replay), outside the timed regions above
     _, _, _, prof = timed_steps(1, wl["precision"], profile=True)
@@ -380,6 +402,7 @@ def run_tg(args, wl, rank, world):
                             "note": "set-up excluded (amortised over right-hand sides)"},
         "e2e": {"value": round(world * 1000.0 / ms_e2e, 5), "unit": "solves/s",
                 "h2d_bytes_per_step": n * b_host.element_size(), "d2h_bytes_per_step": n * b_host.element_size()},
+        "gmres_proj": gmres,
         "fp32_ir": None if ms_ir is None else {"value": round(world * 1000.0 / ms_ir, 5), "unit": "solves/s",
                                                "ms_per_step": round(ms_ir, 3), "converged": ir_ok,
                                                "speedup_vs_f64": round(ms / ms_ir, 3),
@@ -711,6 +734,7 @@ def run_batch(args, wl, rank, world, fp64_instances=0):
                               "speedup_of_batched": round((world * nsolves * 1000.0 / ms) /
                                                           (world * nsolves64 * 1000.0 / ms64), 3)},
         "gpu_launches": int(launches),
+        "autotuner": batch.tuning(),
         "clocks": clocks.summary(),
     }
     return line
@@ -833,6 +857,7 @@ def main():
     p.add_argument("--side-steps", type=int, default=5,
                    help="timed steps of the e2e and float32 side measurements (at most --steps)")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form key of the default run")
+    p.add_argument("--no-gmres", action="store_true", help="skip the GMRES(m3)-Proj key of the 3D workload")
     args = p.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -899,7 +924,8 @@ def main():
                        rank, world, fp64_instances=16)
         line["batch128"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "solves_converged",
                                                "not_converged", "relres_max", "mvps_mean", "step_phases_ms",
-                                               "solve_only", "e2e", "fp64_per_instance", "gpu_launches", "clocks")}
+                                               "solve_only", "e2e", "fp64_per_instance", "gpu_launches", "autotuner",
+                                               "clocks")}
         line["batch128"]["config"] = bl["config"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ("cd2d", "cd3d"):
         v, info = cpu_sample(wl, counts)

@@ -270,10 +270,17 @@ int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *
  *   prolongation, A Y and CholQR2 with float32 copies (1 <= k <= 32); stats: count entries.
  * tg_batch_solve: per instance, float32-inner / float64-refinement BiCGStab(ncyc)-Proj(k)
  *   on the 8 columns together (one read of the basis serves all 8), each column with its
- *   own cycle tolerance and stopping test; the iteration batch is a CUDA graph replayed
- *   until every column of the cycle has finished.  x holds the initial guesses.
- *   Instances run concurrently on `threads` host threads, one stream each; both calls
- *   wait for `stream` first and return when all work is done.  stats: count * 8 entries.
+ *   own cycle tolerance and stopping test.  x holds the initial guesses.
+ * Both phases advance all instances together in lock-step cycles, one kernel launch per
+ *   phase for all of them (blocks of instance i take its points): tg_batch_setup runs the
+ *   instances' coarse GMRES-DR cycles with one batched restart launch per cycle (m <= 62;
+ *   larger m falls back to one instance per host thread), then prolongs and factors each
+ *   basis on `threads` host threads; tg_batch_solve replays the 8-iteration BiCGStab
+ *   sequence of all instances as one CUDA graph until every column of the cycle has
+ *   finished.  The graph's blocks per instance are chosen on the first solve of a handle
+ *   by timing the candidates 8, 16, 32, 64, 128 on the first cycle (tg_batch_tuning).
+ *   Both calls wait for `stream` first and return when all work is done (they run on a
+ *   private stream).  stats: count (setup) / count * 8 (solve) entries.
  * Returns TG_OK when every column converged, else the first failing status.           */
 int tg_batch_create(tg_batch **out, int count, const int64_t *Ns, const double *betas, int nrhs,
                     void *stream);
@@ -283,6 +290,12 @@ int tg_batch_setup(tg_batch *b, const void *rhs, int m, int k, int nev, double r
 int tg_batch_solve(tg_batch *b, const void *rhs, void *x, double rtol, int ncyc, int restart_mvps,
                    int64_t max_mvps, int threads, tg_stats *stats, void *stream);
 int tg_destroy_batch(tg_batch *b);
+/* The autotuner's choice for the batched iteration graph: blocks per instance and its
+ * time per iteration (microseconds, all instances and columns), and every candidate's
+ * (ncand entries of cand_blocks / cand_us, at most 8; any pointer may be NULL).  Zero
+ * blocks before the first tg_batch_solve of the handle.                               */
+int tg_batch_tuning(const tg_batch *b, int *blocks_per_instance, double *us_per_iteration, int *ncand,
+                    int *cand_blocks, double *cand_us);
 
 /* ------------------------------------------------------------------ small dense step
  * The single-CTA float64 kernel of GMRES-DR's restart (Section 2.1), exposed for tests:

@@ -19,6 +19,7 @@
 #include "tg_idr.cuh"
 #include "tg_kernels.cuh"
 #include "tg_mrhs.cuh"
+#include "tg_batch.cuh"
 #include "tg_setup.cuh"
 #include "tg_small.cuh"
 
@@ -348,13 +349,6 @@ template <class T>
 static int launch_apply(const DevOp &A, const DevOp32 &A32, const T *x, T *y, cudaStream_t s) {
     double xb, fl;
     op_cost(A, &xb, &fl);
-    if constexpr (std::is_same<T, float>::value) {
-        if (f4_ok(A, {x, y})) {
-            TG_PROF(P_APPLY, 8.0 * A.n, fl * A.n, k_apply_f4<<<grid_for((A.n + 3) / 4, 8), kThreads, 0, s>>>(A, A32, x, y));
-            TG_LAUNCH_CHECK();
-            return TG_OK;
-        }
-    }
     TG_PROF(P_APPLY, (2.0 * sizeof(T) + xb * (sizeof(T) == 4 ? 0.5 : 1.0)) * A.n, fl * A.n, k_apply<T><<<grid_for(A.n, 8), kThreads, 0, s>>>(A, A32, x, y));
     TG_LAUNCH_CHECK();
     return TG_OK;
@@ -985,10 +979,6 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL) + SmallArea::bistate);
     TG_PROF(P_BI_INIT, 3.0 * n * sizeof(T), 2.0 * n, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
     TG_LAUNCH_CHECK();
-    // float32 constant-coefficient grids: the 4-points-per-thread stencil kernels
-    bool use_f4 = false;
-    if constexpr (std::is_same<T, float>::value) use_f4 = f4_ok(A, {w.p, w.rh, w.v, w.s, w.t});
-    const int g4 = grid_for((n + 3) / 4, 8);
     int chunk = 2;
     int launched = 0;
     BiState<D> h{};
@@ -1000,19 +990,9 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     int iters_prev = 0;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
-            if (use_f4) {
-                if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v_f4<<<g4, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
-            } else {
-                TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
-            }
+            TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
             TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
-            if (use_f4) {
-                if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t_f4<<<g4, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
-            } else {
-                TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
-            }
+            TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
             TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
         }
         TG_LAUNCH_CHECK();
@@ -2223,27 +2203,58 @@ extern "C" int64_t tg_launch_count(void) { return g_prof.launches; }
 // ============================================================================= batched solver
 // Many independent instances (each its own operator, coarse grid and deflation basis),
 // each with R right-hand sides stored point-major (element (j, q) of instance i at
-// offset_i + j * R + q).  Set-up runs coarse GMRES-DR per instance; the solve runs the
-// float32-inner / float64-refinement BiCGStab(ncyc)-Proj(k) on the R columns of an
-// instance together (one read of the basis and of the stencil neighbourhood serves all R),
-// with the iteration batch captured once as a CUDA graph and replayed; instances are
-// processed concurrently by a pool of host threads, one CUDA stream per instance.
+// offset_i + j * R + q).  Both phases advance all instances together in lock-step cycles,
+// one launch per phase for all of them (tg_batch.cuh): the set-up runs the instances'
+// coarse GMRES-DR cycles (float32 basis, one batched restart launch per cycle), then
+// prolongs and factors each basis; the solve runs the float32-inner / float64-refinement
+// BiCGStab(ncyc)-Proj(k) on the R columns of every instance (one read of the basis and of
+// the stencil neighbourhood serves all R), the iteration sequence captured once as a CUDA
+// graph and replayed, its blocks-per-instance shape chosen by timing (the autotuner).
 namespace tg {
 
 constexpr int kBatchR = 8;
 constexpr int kGraphIters = 8;
 
 struct BatchInst {
-    DBuf rh, p, v, s, t, r32, e32, r64, part, small, tmp;
+    DBuf tmp;
+    // batched coarse phase: basis pair, restart scratch, coarse right-hand side
+    DBuf cV, cV2, cbc, cc, cd, cres, cz, ctheta, cwr, cwi, cord, ceres, cP, ccn, cwork, cyw, cgw, cYc;
     PinBuf pin;
     cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
     ~BatchInst() {
-        if (graph) cudaGraphExecDestroy(graph);
         if (stream) cudaStreamDestroy(stream);
     }
 };
 
+}  // namespace tg
+
+// Device state of the batched coarse phase shared by all instances.
+namespace tg {
+struct BatchCoarse {
+    DBuf H, H2, small, part, ticket, seg, args, active, info;
+    int m = 0;
+};
+}  // namespace tg
+
+// Device state of the batched solve: the work vectors of every instance concatenated (the
+// instances' offsets are those of the right-hand sides), per-instance column states and
+// reduction slices, the instance table, and the captured iteration graph.
+namespace tg {
+struct BatchAll {
+    DBuf rh, p, v, s, t, r32, e32, r64, rsave, part, st, ctl, ticket, small, seg;
+    PinBuf pin;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_gx = 0;
+    int gx = 0;                    // tuned blocks per instance (0: not tuned yet)
+    double tune_us[8] = {0};       // us per iteration of each candidate
+    int tune_gx[8] = {0};
+    int ntune = 0;
+    ~BatchAll() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
 }  // namespace tg
 
 struct tg_batch {
@@ -2255,6 +2266,8 @@ struct tg_batch {
     int64_t total = 0;
     int device = 0;
     std::vector<std::unique_ptr<tg::BatchInst>> inst;
+    tg::BatchAll all;
+    tg::BatchCoarse coarse;
     ~tg_batch() {
         for (auto *d : defls) delete d;
         for (auto *o : ops) delete o;
@@ -2294,224 +2307,627 @@ static int parallel_for(int count, int threads, int device, F f) {
     return first_err.load();
 }
 
-// small-area layout of one instance (bytes)
-struct MrSmall {
-    static constexpr size_t st = 0;              // BiState<double>[R]
-    static constexpr size_t ctl = 2048;          // MrCtl
-    static constexpr size_t ticket = 2304;       // unsigned
-    static constexpr size_t target2 = 2560;      // double[R]
-    static constexpr size_t inv = 2816;          // double[R]
-    static constexpr size_t scale = 3072;        // double[R]
-    static constexpr size_t norms = 3328;        // double[2R] (residual) / [R] (projection)
-    static constexpr size_t cvec = 4096;         // double[k R]
-    static constexpr size_t dvec = 8192;         // double[k R]
-    static constexpr size_t bytes = 12288;
-};
 
 static int batch_inst_ready(tg_batch *b, int i) {
     BatchInst &I = *b->inst[i];
-    const int n = b->ops[i]->n;
-    const size_t fb = (size_t)n * kBatchR * 4, db = (size_t)n * kBatchR * 8;
-    TG_CHECK(I.rh.ensure(fb));
-    TG_CHECK(I.p.ensure(fb));
-    TG_CHECK(I.v.ensure(fb));
-    TG_CHECK(I.s.ensure(fb));
-    TG_CHECK(I.t.ensure(fb));
-    TG_CHECK(I.r32.ensure(fb));
-    TG_CHECK(I.e32.ensure(fb));
-    TG_CHECK(I.r64.ensure(db));
-    TG_CHECK(I.part.ensure((size_t)4 << 20));
     if (!I.stream) TG_CHECK_CUDA(cudaStreamCreateWithFlags(&I.stream, cudaStreamNonBlocking));
-    if (!I.small.p) {
-        TG_CHECK(I.small.ensure(MrSmall::bytes));
-        TG_CHECK_CUDA(cudaMemsetAsync(I.small.p, 0, MrSmall::bytes, I.stream));
-    }
     TG_CHECK(I.pin.ensure(4096));
     return TG_OK;
 }
 
-static void batch_iters(const DevOp &A, const DevOp32 &A32, BatchInst &I, int n, int g, int iters) {
-    char *sm = I.small.as<char>();
-    BiState<double> *st = reinterpret_cast<BiState<double> *>(sm + MrSmall::st);
-    MrCtl *ctl = reinterpret_cast<MrCtl *>(sm + MrSmall::ctl);
-    unsigned *tk = reinterpret_cast<unsigned *>(sm + MrSmall::ticket);
-    double *part = I.part.as<double>();
-    float *rh = I.rh.as<float>(), *p = I.p.as<float>(), *v = I.v.as<float>(), *s = I.s.as<float>(),
-          *t = I.t.as<float>(), *r = I.r32.as<float>(), *x = I.e32.as<float>();
+}  // namespace tg
+
+namespace tg {
+
+// Batched float32-inner / float64-refinement BiCGStab(ncyc)-Proj(k) over every instance at
+// once: all instances advance their cycles in lock-step, one launch per phase for all of
+// them (grid (gx, count)), the 8-iteration sequence of the four BiCGStab phases is one CUDA
+// graph replayed until every column of the cycle has finished.  Per column: the schedule,
+// safeguards and statistics of the single-instance float32 refinement.  gx (blocks per
+// instance) is chosen once
+// per handle by timing the iteration graph for each candidate (the autotuner).
+constexpr int kMrPartW = 4 * kBatchR > 32 * kBatchR ? 4 * kBatchR : 32 * kBatchR;
+
+static int batch_all_ready(tg_batch *b) {
+    constexpr int R = kBatchR;
+    BatchAll &A = b->all;
+    const size_t tot = (size_t)b->total;
+    TG_CHECK(A.rh.ensure(tot * 4));
+    TG_CHECK(A.p.ensure(tot * 4));
+    TG_CHECK(A.v.ensure(tot * 4));
+    TG_CHECK(A.s.ensure(tot * 4));
+    TG_CHECK(A.t.ensure(tot * 4));
+    TG_CHECK(A.r32.ensure(tot * 4));
+    TG_CHECK(A.e32.ensure(tot * 4));
+    TG_CHECK(A.rsave.ensure(tot * 4));
+    TG_CHECK(A.r64.ensure(tot * 8));
+    TG_CHECK(A.part.ensure((size_t)b->count * 128 * kMrPartW * 8));   // up to 128 blocks per instance
+    TG_CHECK(A.st.ensure((size_t)b->count * R * sizeof(BiState<double>)));
+    TG_CHECK(A.ctl.ensure((size_t)b->count * sizeof(MrCtl)));
+    TG_CHECK(A.small.ensure((size_t)b->count * (2 * R + 2 * R + 2 * R + 2 * 32 * R) * 8));
+    TG_CHECK(A.seg.ensure((size_t)b->count * sizeof(MrSeg)));
+    TG_CHECK(A.pin.ensure((size_t)b->count * (R * sizeof(BiState<double>) + 4 * R * 8 + sizeof(GdrInfo)) + 4096));
+    if (!A.stream) TG_CHECK_CUDA(cudaStreamCreateWithFlags(&A.stream, cudaStreamNonBlocking));
+    if (!A.ticket.p) {
+        TG_CHECK(A.ticket.ensure((size_t)b->count * sizeof(unsigned)));
+        TG_CHECK_CUDA(cudaMemsetAsync(A.ticket.p, 0, (size_t)b->count * sizeof(unsigned), A.stream));
+    }
+    return TG_OK;
+}
+
+static MrBatchPtrs batch_ptrs(tg_batch *b, int cap) {
+    constexpr int R = kBatchR;
+    BatchAll &A = b->all;
+    MrBatchPtrs P;
+    double *sm = A.small.as<double>();
+    const size_t B = b->count;
+    P.seg = A.seg.as<MrSeg>();
+    P.st = A.st.as<BiState<double>>();
+    P.ctl = A.ctl.as<MrCtl>();
+    P.ticket = A.ticket.as<unsigned>();
+    P.part = A.part.as<double>();
+    P.partw = kMrPartW;
+    P.target2 = sm;
+    P.inv = sm + B * R;
+    P.scale = sm + 2 * B * R;
+    P.norms = sm + 3 * B * R;
+    P.cvec = sm + 5 * B * R;
+    P.dvec = sm + 5 * B * R + B * 32 * R;
+    P.cap = cap;
+    return P;
+}
+
+static void batch_iters_all(tg_batch *b, const MrBatchPtrs &P, int gx, int iters, cudaStream_t s) {
+    constexpr int R = kBatchR;
+    BatchAll &A = b->all;
+    const dim3 grid(gx, b->count);
+    float *rh = A.rh.as<float>(), *p = A.p.as<float>(), *v = A.v.as<float>(), *sv = A.s.as<float>(),
+          *t = A.t.as<float>(), *r = A.r32.as<float>(), *x = A.e32.as<float>();
     for (int it = 0; it < iters; ++it) {
-        k_mr_bi_v<kBatchR><<<g, kThreads, 0, I.stream>>>(A, A32, p, rh, v, part, tk, st, ctl);
-        k_mr_bi_s<kBatchR><<<g, kThreads, 0, I.stream>>>(r, v, s, n, part, tk, st, ctl);
-        k_mr_bi_t<kBatchR><<<g, kThreads, 0, I.stream>>>(A, A32, s, rh, t, part, tk, st, ctl);
-        k_mr_bi_x<kBatchR><<<g, kThreads, 0, I.stream>>>(x, r, p, s, t, v, n, part, tk, st, ctl);
+        k_mrb_bi_v<R><<<grid, kThreads, 0, s>>>(p, rh, v, P);
+        k_mrb_bi_s<R><<<grid, kThreads, 0, s>>>(r, v, sv, P);
+        k_mrb_bi_t<R><<<grid, kThreads, 0, s>>>(sv, rh, t, P);
+        k_mrb_bi_x<R><<<grid, kThreads, 0, s>>>(x, r, p, sv, t, v, P);
     }
 }
 
-static int batch_solve_one(tg_batch *b, int i, const double *B, double *X, const SolveCfg &cfg, tg_stats *stats) {
+// the iteration graph for gx blocks per instance (captured once per gx)
+static int batch_graph(tg_batch *b, int gx) {
+    BatchAll &A = b->all;
+    if (A.graph && A.graph_gx == gx) return TG_OK;
+    if (A.graph) {
+        cudaGraphExecDestroy(A.graph);
+        A.graph = nullptr;
+    }
+    const MrBatchPtrs P = batch_ptrs(b, 0);
+    cudaGraph_t graph;
+    TG_CHECK_CUDA(cudaStreamBeginCapture(A.stream, cudaStreamCaptureModeThreadLocal));
+    batch_iters_all(b, P, gx, kGraphIters, A.stream);
+    TG_CHECK_CUDA(cudaStreamEndCapture(A.stream, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&A.graph, graph, 0);
+    cudaGraphDestroy(graph);
+    TG_CHECK_CUDA(e);
+    A.graph_gx = gx;
+    return TG_OK;
+}
+
+static int batch_readback(tg_batch *b, const void *dev, size_t bytes) {
+    TG_CHECK_CUDA(cudaMemcpyAsync(b->all.pin.p, dev, bytes, cudaMemcpyDeviceToHost, b->all.stream));
+    TG_CHECK_CUDA(cudaStreamSynchronize(b->all.stream));
+    return TG_OK;
+}
+
+// The autotuner: with r32 of the first cycle in place, each candidate gx runs the iteration
+// graph on all columns (no column may finish: targets 0) and the fastest per iteration is
+// kept; r32 is restored and e32 cleared afterwards.
+static int batch_tune(tg_batch *b) {
     constexpr int R = kBatchR;
-    tg_op *op = b->ops[i];
-    const tg_defl *df = b->defls.empty() ? nullptr : b->defls[i];
-    TG_CHECK(batch_inst_ready(b, i));
-    BatchInst &I = *b->inst[i];
-    cudaStream_t s = I.stream;
-    const DevOp &A = op->fine.A;
-    const DevOp32 &A32 = op->fine.A32;
-    const int n = op->n;
-    const int g = grid_for(n, 8);
-    char *sm = I.small.as<char>();
-    double *part = I.part.as<double>();
-    unsigned *tk = reinterpret_cast<unsigned *>(sm + MrSmall::ticket);
-    double *d_norms = reinterpret_cast<double *>(sm + MrSmall::norms);
-    double *d_t2 = reinterpret_cast<double *>(sm + MrSmall::target2);
-    double *d_inv = reinterpret_cast<double *>(sm + MrSmall::inv);
-    double *d_scale = reinterpret_cast<double *>(sm + MrSmall::scale);
-    double *cvec = reinterpret_cast<double *>(sm + MrSmall::cvec);
-    double *dvec = reinterpret_cast<double *>(sm + MrSmall::dvec);
-    BiState<double> *st = reinterpret_cast<BiState<double> *>(sm + MrSmall::st);
-    MrCtl *ctl = reinterpret_cast<MrCtl *>(sm + MrSmall::ctl);
-    double *hp = reinterpret_cast<double *>(I.pin.p);
-    const int kk = df ? df->kk : 0;
-    if (kk > 32) {
-        set_error("batched projection supports k <= 32 (got %d)", kk);
-        return TG_BAD_ARG;
-    }
-    if (!I.graph) {
-        // the iteration batch as one CUDA graph (captured once per instance)
-        cudaGraph_t graph;
-        TG_CHECK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        batch_iters(A, A32, I, n, g, kGraphIters);
-        TG_CHECK_CUDA(cudaStreamEndCapture(s, &graph));
-        cudaError_t e = cudaGraphInstantiate(&I.graph, graph, 0);
-        cudaGraphDestroy(graph);
-        TG_CHECK_CUDA(e);
-    }
-    auto residual = [&](double *nr, double *nb) -> int {
-        TG_PROF(P_RESIDUAL, (3.0 * 8 * R) * n, 12.0 * R * n,
-                k_mr_residual<R><<<g, kThreads, 0, s>>>(A, B, X, I.r64.as<double>(), part, tk, d_norms));
-        TG_CHECK_CUDA(cudaMemcpyAsync(hp, d_norms, 2 * R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BatchAll &A = b->all;
+    const size_t tot = (size_t)b->total;
+    cudaStream_t s = A.stream;
+    TG_CHECK_CUDA(cudaMemcpyAsync(A.rsave.p, A.r32.p, tot * 4, cudaMemcpyDeviceToDevice, s));
+    const int cands[] = {8, 16, 32, 64, 128};
+    std::vector<double> zeros((size_t)b->count * R, 0.0);
+    const MrBatchPtrs P0 = batch_ptrs(b, INT_MAX / 2);
+    cudaEvent_t e0, e1;
+    TG_CHECK_CUDA(cudaEventCreate(&e0));
+    TG_CHECK_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_gx = 16;
+    A.ntune = 0;
+    for (int gx : cands) {
+        TG_CHECK_CUDA(cudaMemcpyAsync(P0.target2, zeros.data(), zeros.size() * 8, cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(A.r32.p, A.rsave.p, tot * 4, cudaMemcpyDeviceToDevice, s));
+        TG_CHECK_CUDA(cudaMemsetAsync(A.e32.p, 0, tot * 4, s));
+        k_mrb_bi_init<R><<<dim3(gx, b->count), kThreads, 0, s>>>(A.r32.as<float>(), A.rh.as<float>(), A.p.as<float>(), P0);
+        TG_LAUNCH_CHECK();
+        TG_CHECK(batch_graph(b, gx));
+        TG_CHECK_CUDA(cudaGraphLaunch(A.graph, s));          // warm
+        TG_CHECK_CUDA(cudaEventRecord(e0, s));
+        TG_CHECK_CUDA(cudaGraphLaunch(A.graph, s));
+        TG_CHECK_CUDA(cudaEventRecord(e1, s));
         TG_CHECK_CUDA(cudaStreamSynchronize(s));
-        for (int q = 0; q < R; ++q) {
-            nr[q] = sqrt(hp[q]);
-            nb[q] = sqrt(hp[R + q]);
+        float ms = 0.f;
+        TG_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double us = 1e3 * ms / kGraphIters;
+        A.tune_gx[A.ntune] = gx;
+        A.tune_us[A.ntune] = us;
+        ++A.ntune;
+        if (us < best) { best = us; best_gx = gx; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TG_CHECK_CUDA(cudaMemcpyAsync(A.r32.p, A.rsave.p, tot * 4, cudaMemcpyDeviceToDevice, s));
+    TG_CHECK_CUDA(cudaMemsetAsync(A.e32.p, 0, tot * 4, s));
+    A.gx = best_gx;
+    __atomic_add_fetch(&g_prof.launches, (int64_t)A.ntune * (2 * 4 * kGraphIters + 1), __ATOMIC_RELAXED);
+    return TG_OK;
+}
+
+static int batch_solve_all(tg_batch *b, const double *Bv, double *X, const SolveCfg &cfg, tg_stats *stats) {
+    constexpr int R = kBatchR;
+    const int count = b->count;
+    TG_CHECK(batch_all_ready(b));
+    BatchAll &A = b->all;
+    cudaStream_t s = A.stream;
+    // the instance table
+    std::vector<MrSeg> seg(count);
+    for (int i = 0; i < count; ++i) {
+        const tg_op *op = b->ops[i];
+        const tg_defl *df = b->defls.empty() ? nullptr : b->defls[i];
+        MrSeg &g = seg[i];
+        g.op = op->fine.A;
+        g.o32 = op->fine.A32;
+        g.off = (size_t)b->off[i];
+        g.kk = df ? df->kk : 0;
+        if (g.kk > 32) {
+            set_error("batched projection supports k <= 32 (got %d)", g.kk);
+            return TG_BAD_ARG;
         }
+        g.proj = df ? df->proj : TG_PROJ_MINRES;
+        g.W = df ? df->W32.as<float>() : nullptr;
+        g.B1 = df ? df->B1_32.as<float>() : nullptr;
+        g.B2 = df ? df->B2_32.as<float>() : nullptr;
+        g.M = df ? df->M.as<double>() : nullptr;
+    }
+    TG_CHECK_CUDA(cudaMemcpyAsync(A.seg.p, seg.data(), seg.size() * sizeof(MrSeg), cudaMemcpyHostToDevice, s));
+    bool any_defl = false;
+    for (const MrSeg &g : seg) any_defl |= g.kk > 0;
+    const int gres = 16;                                          // blocks per instance, refinement kernels
+    MrBatchPtrs P = batch_ptrs(b, 0);
+    double *hp = reinterpret_cast<double *>(A.pin.p);
+    const size_t BR = (size_t)count * R;
+    std::vector<double> nr(BR), nb(BR), nrel(BR), hv(BR);
+    std::vector<int64_t> mv(BR, 0);
+    std::vector<int> status(BR);
+    auto residual = [&]() -> int {
+        TG_PROF(P_RESIDUAL, (3.0 * 8) * b->total, 12.0 * b->total,
+                k_mrb_residual<R><<<dim3(gres, count), kThreads, 0, s>>>(Bv, X, A.r64.as<double>(), P));
+        TG_LAUNCH_CHECK();
+        TG_CHECK(batch_readback(b, P.norms, (size_t)count * 2 * R * 8));
+        for (int i = 0; i < count; ++i)
+            for (int q = 0; q < R; ++q) {
+                nr[i * R + q] = sqrt(hp[(size_t)i * 2 * R + q]);
+                nb[i * R + q] = sqrt(hp[(size_t)i * 2 * R + R + q]);
+            }
         return TG_OK;
     };
-    double nr[R], nb[R];
-    int64_t mv[R] = {0};
-    int status[R];
-    TG_CHECK(residual(nr, nb));
-    for (int q = 0; q < R; ++q) status[q] = (nb[q] == 0.0 || nr[q] <= cfg.rtol * nb[q]) ? TG_OK : TG_NOT_CONVERGED;
+    TG_CHECK(residual());
+    for (size_t c = 0; c < BR; ++c) status[c] = (nb[c] == 0.0 || nr[c] <= cfg.rtol * nb[c]) ? TG_OK : TG_NOT_CONVERGED;
     int cyc = 0;
+    std::vector<int> cycles(count, 0);
     while (true) {
         bool any = false;
-        for (int q = 0; q < R; ++q) any |= status[q] == TG_NOT_CONVERGED;
+        for (size_t c = 0; c < BR; ++c) any |= status[c] == TG_NOT_CONVERGED;
         if (!any) break;
         ++cyc;
         const bool sched = cfg.ncyc && cyc <= cfg.ncyc;   // beyond ncyc: finish with rtol ||b|| / ||r||
-        // correction equations A e_q = r_q / ||r_q|| in float32
-        for (int q = 0; q < R; ++q) {
-            const bool on = status[q] == TG_NOT_CONVERGED;
-            hp[q] = on ? 1.0 / nr[q] : 0.0;
-            hp[R + q] = on ? nr[q] : 0.0;
+        for (int i = 0; i < count; ++i) {
+            bool on_i = false;
+            for (int q = 0; q < R; ++q) on_i |= status[i * R + q] == TG_NOT_CONVERGED;
+            if (on_i) cycles[i] = cyc;
         }
-        TG_CHECK_CUDA(cudaMemcpyAsync(d_inv, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
-        TG_CHECK_CUDA(cudaMemcpyAsync(d_scale, hp + R, R * sizeof(double), cudaMemcpyHostToDevice, s));
-        TG_PROF(P_CONVERT, 16.0 * R * n, R * n,
-                k_mr_scale<R><<<grid_for((int64_t)n * R, 8), kThreads, 0, s>>>(I.r64.as<double>(), I.r32.as<float>(),
-                                                                                 I.e32.as<float>(), n, d_inv));
-        double nrel[R];
-        for (int q = 0; q < R; ++q) nrel[q] = 1.0;
-        if (kk > 0) {
-            const float *W = df->W32.as<float>(), *B1 = df->B1_32.as<float>(), *B2 = df->B2_32.as<float>();
-            const int gp = std::max(1, std::min((n + 127) / 128, num_sms() * 8));
-            const size_t smem = ((size_t)kk * 128 + 128 * R) * sizeof(float);
-            TG_PROF(P_GEMV_T, (double)(kk + R) * n * 4, 2.0 * kk * R * n,
-                    k_mr_proj_dots<R><<<gp, kThreads, smem, s>>>(W, kk, I.r32.as<float>(), n, part));
-            TG_PROF(P_SUM_PART, (double)gp * kk * R * 8, (double)gp * kk * R,
-                    k_sum_part<double><<<(kk * R + 7) / 8, 256, 0, s>>>(part, gp, kk * R, cvec, 0));
-            TG_PROF(P_SMALL, 0, 2.0 * kk * kk * R, k_mr_small<R><<<1, 256, 0, s>>>(df->M.as<double>(), kk, cvec, dvec));
-            const double *ee = df->proj == TG_PROJ_MINRES ? cvec : dvec;
-            TG_PROF(P_PROJ, (2.0 * kk + 4.0 * R) * n * 4, 4.0 * kk * R * n,
-                    k_mr_proj_update<R><<<g, kThreads, 0, s>>>(B1, B2, kk, dvec, ee, I.e32.as<float>(),
-                                                              I.r32.as<float>(), n, part, tk, d_norms));
-            TG_CHECK_CUDA(cudaMemcpyAsync(hp, d_norms, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-            TG_CHECK_CUDA(cudaStreamSynchronize(s));
-            for (int q = 0; q < R; ++q) nrel[q] = sqrt(hp[q]);
+        // correction equations A e = r / ||r|| in float32
+        for (size_t c = 0; c < BR; ++c) hv[c] = status[c] == TG_NOT_CONVERGED ? 1.0 / nr[c] : 0.0;
+        TG_CHECK_CUDA(cudaMemcpyAsync(P.inv, hv.data(), BR * 8, cudaMemcpyHostToDevice, s));
+        TG_PROF(P_CONVERT, 16.0 * b->total, b->total,
+                k_mrb_scale<R><<<dim3(gres, count), kThreads, 0, s>>>(A.r64.as<double>(), A.r32.as<float>(),
+                                                                         A.e32.as<float>(), P));
+        TG_LAUNCH_CHECK();
+        for (size_t c = 0; c < BR; ++c) nrel[c] = 1.0;
+        if (any_defl) {
+            const size_t smem = ((size_t)32 * 128 + 128 * R) * sizeof(float);
+            TG_CHECK(set_smem<float>((const void *)k_mrb_proj_dots<R>, smem));
+            TG_PROF(P_GEMV_T, 0, 0, k_mrb_proj_dots<R><<<dim3(gres, count), kThreads, smem, s>>>(A.r32.as<float>(), P));
+            TG_PROF(P_SMALL, 0, 0, k_mrb_small<R><<<count, 256, 0, s>>>(P));
+            TG_PROF(P_PROJ, 0, 0, k_mrb_proj_update<R><<<dim3(gres, count), kThreads, 0, s>>>(A.e32.as<float>(),
+                                                                                            A.r32.as<float>(), P));
+            TG_LAUNCH_CHECK();
+            TG_CHECK(batch_readback(b, P.norms, (size_t)count * 2 * R * 8));
+            for (int i = 0; i < count; ++i)
+                if (seg[i].kk > 0)
+                    for (int q = 0; q < R; ++q) nrel[i * R + q] = sqrt(hp[(size_t)i * 2 * R + q]);
         }
         int64_t cap64 = cfg.max_mvps;
-        for (int q = 0; q < R; ++q) {
-            const bool on = status[q] == TG_NOT_CONVERGED;
+        for (size_t c = 0; c < BR; ++c) {
             double t2 = -1.0;
-            if (on) {
-                const double nrp = nrel[q] * nr[q];
-                double rt = sched ? cycle_tol(cfg.rtol, nb[q], nrp, cyc, cfg.ncyc) : cfg.rtol * nb[q] / nrp;
+            if (status[c] == TG_NOT_CONVERGED) {
+                const double nrp = nrel[c] * nr[c];
+                const int i = (int)(c / R);
+                (void)i;
+                double rt = sched ? cycle_tol(cfg.rtol, nb[c], nrp, cyc, cfg.ncyc) : cfg.rtol * nb[c] / nrp;
                 if (rt < 1e-6) rt = 1e-6;
-                t2 = (rt * nrel[q]) * (rt * nrel[q]);
-                cap64 = std::min<int64_t>(cap64, cfg.max_mvps - mv[q]);
+                t2 = (rt * nrel[c]) * (rt * nrel[c]);
+                cap64 = std::min<int64_t>(cap64, cfg.max_mvps - mv[c]);
             }
-            hp[q] = t2;
+            hv[c] = t2;
         }
         cap64 = std::min<int64_t>(cap64, cfg.restart_mvps > 0 ? cfg.restart_mvps : kIrCycleCap);
         cap64 = std::max<int64_t>(1, std::min<int64_t>(cap64, INT_MAX / 2));
-        TG_CHECK_CUDA(cudaMemcpyAsync(d_t2, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
-        TG_PROF(P_BI_INIT, 12.0 * R * n, 2.0 * R * n,
-                k_mr_bi_init<R><<<g, kThreads, 0, s>>>(I.r32.as<float>(), I.rh.as<float>(), I.p.as<float>(), n, d_t2,
-                                                       (int)cap64, part, tk, st, ctl));
+        if (A.gx == 0) TG_CHECK(batch_tune(b));           // once per handle, on the first cycle's r32
+        const int gx = A.gx;
+        TG_CHECK_CUDA(cudaMemcpyAsync(P.target2, hv.data(), BR * 8, cudaMemcpyHostToDevice, s));
+        const MrBatchPtrs Pc = batch_ptrs(b, (int)cap64);
+        TG_PROF(P_BI_INIT, 12.0 * b->total, 2.0 * b->total,
+                k_mrb_bi_init<R><<<dim3(gx, count), kThreads, 0, s>>>(A.r32.as<float>(), A.rh.as<float>(),
+                                                                        A.p.as<float>(), Pc));
+        TG_LAUNCH_CHECK();
+        TG_CHECK(batch_graph(b, gx));
         int graphs = 0;
         while (true) {
-            TG_CHECK_CUDA(cudaGraphLaunch(I.graph, s));
+            TG_CHECK_CUDA(cudaGraphLaunch(A.graph, s));
             __atomic_add_fetch(&g_prof.launches, 4 * kGraphIters, __ATOMIC_RELAXED);
             ++graphs;
-            MrCtl hc;
-            TG_CHECK_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(MrCtl), cudaMemcpyDeviceToHost, s));
-            TG_CHECK_CUDA(cudaStreamSynchronize(s));
-            if (hc.active == 0) break;
+            TG_CHECK(batch_readback(b, P.ctl, (size_t)count * sizeof(MrCtl)));
+            const MrCtl *hc = reinterpret_cast<const MrCtl *>(A.pin.p);
+            int active = 0;
+            for (int i = 0; i < count; ++i) active += hc[i].active;
+            if (active == 0) break;
             if ((int64_t)graphs * kGraphIters > cap64 + 8) {
                 set_error("batched BiCGStab cycle exceeded its product cap");
                 return TG_SYNC_TIMEOUT;
             }
         }
-        BiState<double> hs[R];
-        TG_CHECK_CUDA(cudaMemcpyAsync(hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
-        TG_CHECK_CUDA(cudaStreamSynchronize(s));
-        bool reject = false;
-        for (int q = 0; q < R; ++q) {   // a diverged or NaN float32 correction is not added
-            const bool bad = status[q] == TG_NOT_CONVERGED && (hs[q].status == 4 || hs[q].status == 5);
-            hp[q] = (status[q] == TG_NOT_CONVERGED && !bad) ? nr[q] : 0.0;
-            reject |= bad;
+        TG_CHECK(batch_readback(b, P.st, BR * sizeof(BiState<double>)));
+        std::vector<BiState<double>> hs(BR);
+        memcpy(hs.data(), A.pin.p, BR * sizeof(BiState<double>));
+        for (size_t c = 0; c < BR; ++c) {     // a diverged or NaN float32 correction is not added
+            const bool bad = status[c] == TG_NOT_CONVERGED && (hs[c].status == 4 || hs[c].status == 5);
+            hv[c] = (status[c] == TG_NOT_CONVERGED && !bad) ? nr[c] : 0.0;
         }
-        if (reject) TG_CHECK_CUDA(cudaMemcpyAsync(d_scale, hp, R * sizeof(double), cudaMemcpyHostToDevice, s));
-        TG_PROF(P_CONVERT, 12.0 * R * n, 2.0 * R * n,
-                k_mr_add<R><<<grid_for((int64_t)n * R, 8), kThreads, 0, s>>>(X, I.e32.as<float>(), n, d_scale));
-        TG_CHECK_CUDA(cudaStreamSynchronize(s));
-        TG_CHECK(residual(nr, nb));
+        TG_CHECK_CUDA(cudaMemcpyAsync(P.scale, hv.data(), BR * 8, cudaMemcpyHostToDevice, s));
+        TG_PROF(P_CONVERT, 12.0 * b->total, 2.0 * b->total,
+                k_mrb_add<R><<<dim3(gres, count), kThreads, 0, s>>>(X, A.e32.as<float>(), P));
+        TG_LAUNCH_CHECK();
+        TG_CHECK(residual());
         bool stuck = true;
-        for (int q = 0; q < R; ++q) {
-            if (status[q] != TG_NOT_CONVERGED) continue;
-            mv[q] += hs[q].mvps;
-            if (hs[q].mvps > 0) stuck = false;
-            if (!std::isfinite(nr[q]) || hs[q].status == 4 || hs[q].status == 5) status[q] = TG_NAN;
-            else if (nr[q] <= cfg.rtol * nb[q]) status[q] = TG_OK;
-            else if (mv[q] >= cfg.max_mvps) status[q] = TG_NOT_CONVERGED + 100;   // out of budget
+        for (size_t c = 0; c < BR; ++c) {
+            if (status[c] != TG_NOT_CONVERGED) continue;
+            mv[c] += hs[c].mvps;
+            if (hs[c].mvps > 0) stuck = false;
+            if (!std::isfinite(nr[c]) || hs[c].status == 4 || hs[c].status == 5) status[c] = TG_NAN;
+            else if (nr[c] <= cfg.rtol * nb[c]) status[c] = TG_OK;
+            else if (mv[c] >= cfg.max_mvps) status[c] = TG_NOT_CONVERGED + 100;   // out of budget
         }
         if (stuck) break;
     }
-    for (int q = 0; q < R; ++q) {
-        if (status[q] == TG_NOT_CONVERGED + 100) status[q] = TG_NOT_CONVERGED;
+    int worst = TG_OK;
+    for (size_t c = 0; c < BR; ++c) {
+        if (status[c] == TG_NOT_CONVERGED + 100) status[c] = TG_NOT_CONVERGED;
         if (stats) {
-            tg_stats &o = stats[(size_t)i * R + q];
-            o.mvps = mv[q];
-            o.cycles = cyc;
-            o.relres = nb[q] > 0 ? nr[q] / nb[q] : 0.0;
-            o.status = status[q];
-            o.vops = mv[q] * 7;
+            tg_stats &o = stats[c];
+            o.mvps = mv[c];
+            o.cycles = cycles[c / R];
+            o.relres = nb[c] > 0 ? nr[c] / nb[c] : 0.0;
+            o.status = status[c];
+            o.vops = mv[c] * 7;
         }
+        if (status[c] != TG_OK && worst == TG_OK) worst = status[c];
     }
-    for (int q = 0; q < R; ++q)
-        if (status[q] != TG_OK) return status[q] == TG_NOT_CONVERGED ? TG_NOT_CONVERGED : status[q];
-    return TG_OK;
+    return worst;
 }
 
 }  // namespace tg
+
+namespace tg {
+
+// The coarse GMRES-DR(m,k) of every instance in lock-step cycles (float32 basis, float64
+// Hessenberg and restart step, as gmresdr_impl<float, double>): one launch per Arnoldi
+// sub-step for all instances, one batched restart launch (one block per instance), then
+// the recombination V <- V P_{k+1} and the re-orthogonalisation of v_{kk} for all.  An
+// instance leaves the loop when its least-squares residual is below rtol ||b_c|| and nev
+// pairs have converged, or after max_cycles.  Afterwards each instance's basis V_m P_k is
+// prolonged and factored (A Y, CholQR2, float32 copies) as in tg_coarse_gmresdr.
+constexpr int kGbBlocks = 64;             // blocks per instance of the coarse kernels
+constexpr int kGbPartW = 64;              // >= m + 2 columns of partial sums
+
+static int batch_setup_all(tg_batch *b, const double *R0, int m, int k, int nev, double rtolev, double rtol,
+                           int max_cycles, int proj, int threads, tg_stats *stats) {
+    const int count = b->count;
+    TG_CHECK(batch_all_ready(b));
+    BatchAll &A = b->all;
+    BatchCoarse &C = b->coarse;
+    cudaStream_t s = A.stream;
+    const int ldh = m + 1;
+    TG_ARG(m + 2 <= kGbPartW && m + 1 <= kSmallCols, "the batched coarse phase takes m <= %d", kGbPartW - 2);
+    // shared coarse state
+    TG_CHECK(C.H.ensure((size_t)count * ldh * m * 8));
+    TG_CHECK(C.H2.ensure((size_t)count * ldh * m * 8));
+    TG_CHECK(C.small.ensure((size_t)count * 3 * 256 * 8));      // h1, h2, nrm per instance
+    TG_CHECK(C.part.ensure((size_t)count * kGbBlocks * kGbPartW * 8));
+    TG_CHECK(C.seg.ensure((size_t)count * sizeof(GdrSeg)));
+    TG_CHECK(C.args.ensure((size_t)count * sizeof(GdrArgs<double>)));
+    TG_CHECK(C.active.ensure((size_t)count * sizeof(int)));
+    TG_CHECK(C.info.ensure((size_t)count * sizeof(GdrInfo)));
+    if (!C.ticket.p) {
+        TG_CHECK(C.ticket.ensure((size_t)count * sizeof(unsigned)));
+        TG_CHECK_CUDA(cudaMemsetAsync(C.ticket.p, 0, (size_t)count * sizeof(unsigned), s));
+    }
+    int parts = 0;
+    gmresdr_restart_smem<double>(m, &parts);
+    std::vector<GdrSeg> seg(count);
+    std::vector<GdrArgs<double>> args(count);
+    std::vector<double *> Hc(count), H2c(count);
+    std::vector<float *> V2(count);
+    std::vector<double> nbc(count);
+    std::vector<int> active(count, 1), cycles(count, 0);
+    std::vector<int64_t> cmvps(count, 0);
+    std::vector<GdrInfo> info(count);
+    double *small = C.small.as<double>();
+    for (int i = 0; i < count; ++i) {
+        tg_op *op = b->ops[i];
+        BatchInst &I = *b->inst[i];
+        const int nc = op->nc;
+        TG_ARG(m < nc && k < m - 1 && nev >= 0 && nev <= k, "bad GMRES-DR sizes for instance %d", i);
+        const size_t ldv = ((size_t)nc + 127) / 128 * 128;
+        TG_CHECK(I.cV.ensure(ldv * (m + 1) * 4));
+        TG_CHECK(I.cV2.ensure(ldv * (m + 1) * 4));
+        TG_CHECK(I.cbc.ensure((size_t)nc * 8));
+        TG_CHECK(I.tmp.ensure((size_t)op->n * 8));
+        TG_CHECK(I.cd.ensure((size_t)(m + 1) * 8));
+        TG_CHECK(I.cc.ensure((size_t)(m + 1) * 8));
+        TG_CHECK(I.cres.ensure((size_t)(m + 1) * 8));
+        TG_CHECK(I.cz.ensure((size_t)(m + 1) * 8));
+        TG_CHECK(I.ctheta.ensure((size_t)2 * m * 8));
+        TG_CHECK(I.cwr.ensure((size_t)m * 8));
+        TG_CHECK(I.cwi.ensure((size_t)m * 8));
+        TG_CHECK(I.cord.ensure((size_t)m * 4));
+        TG_CHECK(I.ceres.ensure((size_t)m * 8));
+        TG_CHECK(I.cP.ensure((size_t)(m + 1) * (m + 2) * 8));
+        TG_CHECK(I.ccn.ensure((size_t)(m + 2) * 8));
+        TG_CHECK(I.cwork.ensure(((size_t)(m + 1) * m + 2 * (size_t)m * m + 3 * (size_t)m + 4) * 8));
+        TG_CHECK(I.cyw.ensure((size_t)m * m * 16));
+        TG_CHECK(I.cgw.ensure((size_t)m * m * 16));
+        TG_CHECK(I.cYc.ensure((size_t)nc * (k + 2) * 8));
+        // b_c = restrict(column 0), ||b_c||, v_0 = b_c / ||b_c|| (float32)
+        k_mr_extract<kBatchR><<<grid_for(op->n, 8), kThreads, 0, s>>>(R0 + b->off[i], 0, op->n, I.tmp.as<double>());
+        TG_LAUNCH_CHECK();
+        TG_CHECK(restrict_impl(op, I.tmp.p, I.cbc.p, 1, s));
+        double nb2 = 0.0;
+        TG_CHECK(red_ready(op, 0, s));
+        TG_CHECK(dot_host<double>(op, I.cbc.as<double>(), nullptr, nc, &nb2, nullptr, s));
+        nbc[i] = sqrt(nb2);
+        TG_ARG(nbc[i] > 0 && std::isfinite(nbc[i]), "restricted right-hand side of instance %d is zero or not finite", i);
+        launch_d2f_scaled(grid_for(nc, 8), s, I.cbc.as<double>(), I.cV.as<float>(), nc, 1.0 / nbc[i]);
+        TG_LAUNCH_CHECK();
+        Hc[i] = C.H.as<double>() + (size_t)i * ldh * m;
+        H2c[i] = C.H2.as<double>() + (size_t)i * ldh * m;
+        V2[i] = I.cV2.as<float>();
+        GdrSeg &g = seg[i];
+        g.op = op->coarse.A;
+        g.o32 = op->coarse.A32;
+        g.V = I.cV.as<float>();
+        g.xc = nullptr;
+        g.H = Hc[i];
+        g.h1 = small + (size_t)i * 3 * 256;
+        g.h2 = g.h1 + 256;
+        g.nrm = g.h2 + 256;
+        g.d = I.cd.as<double>();
+        g.ldv = ldv;
+        g.nc = nc;
+        g.j0 = 0;
+        g.kk = 0;
+        g.active = 1;
+        // c = ||b_c|| e_1 in the least-squares right-hand side (the restart kernel reads it from a.c)
+        GdrArgs<double> &a = args[i];
+        a.ldh = ldh; a.m = m; a.k = k; a.nev = nev; a.rtolev = rtolev;
+        a.d = I.cd.as<double>(); a.res = I.cres.as<double>(); a.z = I.cz.as<double>();
+        a.theta = I.ctheta.as<double>(); a.wr = I.cwr.as<double>(); a.wi = I.cwi.as<double>();
+        a.order = I.cord.as<int>(); a.eres = I.ceres.as<double>(); a.P = I.cP.as<double>();
+        a.cnew = I.ccn.as<double>(); a.work = I.cwork.as<double>(); a.ywork = I.cyw.as<cplx>();
+        a.gwork = I.cgw.as<cplx>(); a.info = C.info.as<GdrInfo>() + i;
+        a.smem = parts;
+        a.mode = 0;
+    }
+    TG_CHECK_CUDA(cudaMemsetAsync(C.H.p, 0, (size_t)count * ldh * m * 8, s));
+    // least-squares right-hand sides c = ||b_c|| e_1
+    std::vector<double> c0(m + 1, 0.0);
+    for (int i = 0; i < count; ++i) {
+        BatchInst &I = *b->inst[i];
+        c0[0] = nbc[i];
+        TG_CHECK_CUDA(cudaMemcpyAsync(I.cc.p, c0.data(), (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, s));
+        args[i].c = I.cc.as<double>();
+    }
+    GdrBatchPtrs P{C.seg.as<GdrSeg>(), C.part.as<double>(), kGbPartW, C.ticket.as<unsigned>()};
+    const dim3 grid(kGbBlocks, count);
+    int any = count;
+    int cyc = 0;
+    while (any) {
+        ++cyc;
+        // table and restart arguments of this cycle
+        int jmin = m;
+        for (int i = 0; i < count; ++i) {
+            seg[i].active = active[i];
+            args[i].H = Hc[i];
+            args[i].Hnew = H2c[i];
+            if (active[i]) jmin = std::min(jmin, seg[i].j0);
+        }
+        TG_CHECK_CUDA(cudaMemcpyAsync(C.seg.p, seg.data(), seg.size() * sizeof(GdrSeg), cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(C.args.p, args.data(), args.size() * sizeof(GdrArgs<double>),
+                                      cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(C.active.p, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        // Arnoldi from each instance's j0 to m
+        for (int j = jmin; j < m; ++j) {
+            TG_PROF(P_APPLY, 0, 0, k_gb_apply<<<grid, kThreads, 0, s>>>(P, j));
+            TG_PROF(P_GEMV_T, 0, 0, k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, j, j + 2, 0, 0));
+            TG_PROF(P_GEMV_N, 0, 0, k_gb_gemv_n_norm<<<grid, kThreads, 0, s>>>(P, j, j + 1, 0, 0));
+            TG_PROF(P_GEMV_T, 0, 0, k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, j, j + 1, 0, 1));
+            TG_PROF(P_GEMV_N, 0, 0, k_gb_gemv_n_norm<<<grid, kThreads, 0, s>>>(P, j, j + 1, 0, 1));
+            TG_PROF(P_SMALL, 0, 0, k_gb_finish<<<(count + 127) / 128, 128, 0, s>>>(P, count, j, ldh, 0));
+            TG_PROF(P_SCALE, 0, 0, k_gb_scale<<<grid, kThreads, 0, s>>>(P, j, 0));
+        }
+        TG_LAUNCH_CHECK();
+        // the restart matrices are written into each instance's other Hbar buffer (which of
+        // the two pools holds it alternates with the instance's restarts)
+        for (int i = 0; i < count; ++i)
+            if (active[i]) TG_CHECK_CUDA(cudaMemsetAsync(H2c[i], 0, (size_t)ldh * m * 8, s));
+        cudaError_t le = cudaSuccess;
+        TG_PROF(P_GDR_RESTART, 0, 30.0 * m * m * m * count,
+                le = launch_gmresdr_restart_batch<double>(C.args.as<GdrArgs<double>>(), C.active.as<int>(), count, m, s));
+        if (le != cudaSuccess) return cuda_status(le, "launching the batched restart step");
+        // the instances' restart results
+        TG_CHECK(batch_readback(b, C.info.p, (size_t)count * sizeof(GdrInfo)));
+        {
+            const GdrInfo *hi = reinterpret_cast<const GdrInfo *>(A.pin.p);
+            for (int i = 0; i < count; ++i)
+                if (active[i]) info[i] = hi[i];
+        }
+        std::vector<int> cont(count, 0);
+        for (int i = 0; i < count; ++i) {
+            if (!active[i]) continue;
+            cmvps[i] += m - seg[i].j0;
+            cycles[i] = cyc;
+            if (info[i].status != 0) {
+                set_error("harmonic Ritz QR iteration did not converge (instance %d)", i);
+                return TG_NOT_CONVERGED;
+            }
+            const int kk = info[i].kk;
+            const bool conv = info[i].rnorm <= rtol * nbc[i] && info[i].nconv >= (nev < kk ? nev : kk);
+            seg[i].kk = kk;
+            if (conv || cyc >= max_cycles || !std::isfinite(info[i].rnorm)) {
+                active[i] = 0;            // done: its V, Hbar and P stay for the final basis
+            } else {
+                cont[i] = 1;
+            }
+        }
+        any = 0;
+        for (int i = 0; i < count; ++i) any += cont[i];
+        if (!any) break;
+        // restart of the continuing instances: V2 = V P_{k+1}, Hbar <- Hnew, c <- cnew, then
+        // re-orthogonalise v_kk and normalise it
+        for (int i = 0; i < count; ++i) seg[i].active = cont[i];
+        TG_CHECK_CUDA(cudaMemcpyAsync(C.seg.p, seg.data(), seg.size() * sizeof(GdrSeg), cudaMemcpyHostToDevice, s));
+        {
+            std::vector<const double *> Pp(count);
+            std::vector<float *> Op(count);
+            std::vector<size_t> ldo(count);
+            for (int i = 0; i < count; ++i) {
+                Pp[i] = args[i].P;
+                Op[i] = V2[i];
+                ldo[i] = seg[i].ldv;
+            }
+            TG_CHECK(A.rsave.ensure(std::max<size_t>(A.rsave.bytes, (size_t)count * 24)));
+            char *tb = A.rsave.as<char>();
+            TG_CHECK_CUDA(cudaMemcpyAsync(tb, Pp.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+            TG_CHECK_CUDA(cudaMemcpyAsync(tb + (size_t)count * 8, Op.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+            TG_CHECK_CUDA(cudaMemcpyAsync(tb + (size_t)count * 16, ldo.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+            TG_PROF(P_TSM, 0, 0, k_gb_tsm<float><<<grid, kThreads, 0, s>>>(
+                P, reinterpret_cast<const double *const *>(tb), m + 1, m + 1, 1,
+                reinterpret_cast<float *const *>(tb + (size_t)count * 8), reinterpret_cast<const size_t *>(tb + (size_t)count * 16)));
+            TG_LAUNCH_CHECK();
+            TG_CHECK_CUDA(cudaStreamSynchronize(s));     // the tables are reused below
+        }
+        for (int i = 0; i < count; ++i) {
+            if (!cont[i]) continue;
+            std::swap(seg[i].V, V2[i]);
+            std::swap(Hc[i], H2c[i]);
+            seg[i].H = Hc[i];
+            BatchInst &I = *b->inst[i];
+            // c = cnew (kk + 1 entries), zero beyond
+            TG_CHECK_CUDA(cudaMemsetAsync(I.cc.p, 0, (size_t)(m + 1) * 8, s));
+            TG_CHECK_CUDA(cudaMemcpyAsync(I.cc.p, I.ccn.p, (size_t)(seg[i].kk + 1) * 8, cudaMemcpyDeviceToDevice, s));
+            seg[i].j0 = seg[i].kk;
+        }
+        TG_CHECK_CUDA(cudaMemcpyAsync(C.seg.p, seg.data(), seg.size() * sizeof(GdrSeg), cudaMemcpyHostToDevice, s));
+        TG_PROF(P_REORTH, 0, 0, k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, 0, 0, 1, 0));
+        TG_PROF(P_REORTH, 0, 0, k_gb_gemv_n_norm<<<grid, kThreads, 0, s>>>(P, 0, 0, 1, 0));
+        TG_PROF(P_SMALL, 0, 0, k_gb_finish<<<(count + 127) / 128, 128, 0, s>>>(P, count, 0, ldh, 1));
+        TG_PROF(P_SCALE, 0, 0, k_gb_scale<<<grid, kThreads, 0, s>>>(P, 0, 1));
+        TG_LAUNCH_CHECK();
+        for (int i = 0; i < count; ++i) active[i] = cont[i];
+    }
+    // final bases Yc = V_m P_k (float64), for every instance
+    for (int i = 0; i < count; ++i) seg[i].active = 1;
+    TG_CHECK_CUDA(cudaMemcpyAsync(C.seg.p, seg.data(), seg.size() * sizeof(GdrSeg), cudaMemcpyHostToDevice, s));
+    {
+        std::vector<const double *> Pp(count);
+        std::vector<double *> Op(count);
+        std::vector<size_t> ldo(count);
+        for (int i = 0; i < count; ++i) {
+            Pp[i] = args[i].P;
+            Op[i] = b->inst[i]->cYc.as<double>();
+            ldo[i] = (size_t)seg[i].nc;
+        }
+        char *tb = A.rsave.as<char>();
+        TG_CHECK_CUDA(cudaMemcpyAsync(tb, Pp.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(tb + (size_t)count * 8, Op.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpyAsync(tb + (size_t)count * 16, ldo.data(), (size_t)count * 8, cudaMemcpyHostToDevice, s));
+        TG_PROF(P_TSM, 0, 0, k_gb_tsm<double><<<grid, kThreads, 0, s>>>(
+            P, reinterpret_cast<const double *const *>(tb), m + 1, m, 0,
+            reinterpret_cast<double *const *>(tb + (size_t)count * 8), reinterpret_cast<const size_t *>(tb + (size_t)count * 16)));
+        TG_LAUNCH_CHECK();
+    }
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
+    // per instance: prolong the basis, A Y and its factorisation (float64 and float32 copies)
+    if ((int)b->defls.size() != count) b->defls.assign(count, nullptr);
+    return parallel_for(count, threads, b->device, [&](int i) -> int {
+        TG_CHECK(batch_inst_ready(b, i));
+        BatchInst &I = *b->inst[i];
+        tg_op *op = b->ops[i];
+        const int kk = seg[i].kk;
+        tg_defl *d = b->defls[i];
+        if (d) {
+            d->kk = kk; d->n = op->n; d->proj = proj; d->precision = TG_F32_IR; d->cplx_ = false; d->transposed = false;
+            TG_CHECK(d->Y.ensure((size_t)op->n * kk * 8));
+        } else {
+            TG_CHECK(defl_create(op, 0, kk, proj, TG_F32_IR, &d));
+            b->defls[i] = d;
+        }
+        TG_CHECK(prolong_impl(op, I.cYc.p, d->Y.p, kk, I.stream));
+        TG_CHECK(build_defl<double>(op, 0, d, I.stream));
+        if (stats) {
+            tg_stats &o = stats[i];
+            o = tg_stats{};
+            o.coarse_mvps = cmvps[i];
+            o.cycles = cycles[i];
+            o.coarse_relres = info[i].rnorm / nbc[i];
+            o.kk = kk;
+            o.eig_converged = info[i].nconv;
+            o.status = (info[i].rnorm <= rtol * nbc[i] && info[i].nconv >= (nev < kk ? nev : kk)) ? TG_OK
+                                                                                                 : TG_NOT_CONVERGED;
+        }
+        return TG_OK;
+    });
+}
+
+}  // namespace tg
+
+extern "C" int tg_batch_tuning(const tg_batch *b, int *blocks_per_instance, double *us_per_iteration, int *ncand,
+                               int *cand_blocks, double *cand_us) {
+    TG_ARG(b, "NULL batch");
+    const BatchAll &A = b->all;
+    if (blocks_per_instance) *blocks_per_instance = A.gx;
+    double best = 0.0;
+    for (int q = 0; q < A.ntune; ++q)
+        if (A.tune_gx[q] == A.gx) best = A.tune_us[q];
+    if (us_per_iteration) *us_per_iteration = best;
+    if (ncand) *ncand = A.ntune;
+    for (int q = 0; q < A.ntune; ++q) {
+        if (cand_blocks) cand_blocks[q] = A.tune_gx[q];
+        if (cand_us) cand_us[q] = A.tune_us[q];
+    }
+    return TG_OK;
+}
 
 extern "C" int tg_batch_create(tg_batch **out, int count, const int64_t *Ns, const double *betas, int nrhs,
                                void *stream) {
@@ -2557,6 +2973,8 @@ extern "C" int tg_batch_setup(tg_batch *b, const void *rhs, int m, int k, int ne
     TG_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     if ((int)b->defls.size() != b->count) b->defls.assign(b->count, nullptr);   // handles are rebuilt in place
     const double *R0 = static_cast<const double *>(rhs);
+    if (m + 2 <= kGbPartW)
+        return batch_setup_all(b, R0, m, k, nev, rtolev, rtol, max_cycles, proj, threads, stats);
     return parallel_for(b->count, threads, b->device, [&](int i) -> int {
         TG_CHECK(batch_inst_ready(b, i));
         BatchInst &I = *b->inst[i];
@@ -2585,14 +3003,6 @@ extern "C" int tg_batch_solve(tg_batch *b, const void *rhs, void *x, double rtol
     SolveCfg cfg{rtol, ncyc, restart_mvps, 0, max_mvps};
     const double *B = static_cast<const double *>(rhs);
     double *X = static_cast<double *>(x);
-    std::vector<int> rcs(b->count, TG_OK);
-    int rc = parallel_for(b->count, threads, b->device, [&](int i) -> int {
-        int r = batch_solve_one(b, i, B + b->off[i], X + b->off[i], cfg, stats);
-        rcs[i] = r;
-        return (r == TG_NOT_CONVERGED || r == TG_BREAKDOWN) ? TG_OK : r;   // keep going on numerical failures
-    });
-    if (rc != TG_OK) return rc;
-    for (int r : rcs)
-        if (r != TG_OK) return r;
-    return TG_OK;
+    (void)threads;     // one batched launch per phase for all instances: no host threads
+    return batch_solve_all(b, B, X, cfg, stats);
 }

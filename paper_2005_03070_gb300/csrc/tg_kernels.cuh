@@ -5,7 +5,6 @@
 // per thread in float and across threads and blocks in double.
 #pragma once
 
-#include <initializer_list>
 #include <type_traits>
 
 #include "tg_common.cuh"
@@ -341,211 +340,6 @@ __global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restr
             else if (dabs(st->omega) < kTiny) st->status = 2;
             else if (dabs(st->rho_next) < kTiny) st->status = 2;
             else if (st->mvps >= st->cap) st->status = 3;
-        }
-    }
-}
-
-// ----------------------------------------------------------------------------- float32 stencil, 4 points per thread
-// The constant-coefficient float32 stencils (cd2d / cd3d) as used by the inner BiCGStab of the
-// float32 + refinement form: thread g takes the 4 consecutive points 4g .. 4g + 3 of the flat
-// index.  The centre values are one aligned float4; a neighbour at flat offset d is the 4-wide
-// window starting at 4g + d, assembled from the two aligned float4 covering it (the window
-// offset d mod 4 is the same for every thread, so the selection does not diverge); the x
-// neighbours 4g - 1 and 4g + 4 are single loads.  About 10 vector loads per 4 points replace
-// 28 scalar ones: more bytes in flight per instruction for a kernel bound by load latency.
-// Points of the first and last plane (3D) / row (2D), whose windows would leave the array,
-// and a partial last group take the scalar stencil.  Summation order per point is that of
-// the scalar float32 stencil (centre, -x, +x, -y, +y, -z, +z).
-__device__ __forceinline__ float4 ld4(const float *__restrict__ p, int a) {
-    return *reinterpret_cast<const float4 *>(p + a);
-}
-__device__ __forceinline__ float f4e(const float4 &v, int e) {
-    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-}
-// the 4 values p[start .. start + 3], start = 4g + d >= 0, from two aligned float4 loads
-__device__ __forceinline__ void window4(const float *__restrict__ p, int start, float (&w)[4]) {
-    const int a = start & ~3, o = start & 3;
-    const float4 L0 = ld4(p, a);
-    if (o == 0) {
-        w[0] = L0.x; w[1] = L0.y; w[2] = L0.z; w[3] = L0.w;
-        return;
-    }
-    const float4 L1 = ld4(p, a + 4);
-    if (o == 1) { w[0] = L0.y; w[1] = L0.z; w[2] = L0.w; w[3] = L1.x; }
-    else if (o == 2) { w[0] = L0.z; w[1] = L0.w; w[2] = L1.x; w[3] = L1.y; }
-    else { w[0] = L0.w; w[1] = L1.x; w[2] = L1.y; w[3] = L1.z; }
-}
-
-// y[e] = (A p)(4g + e) for e < 4, c[e] = p(4g + e); returns false when the group is not
-// eligible for the vector path (the caller then takes the scalar stencil per point).
-__device__ __forceinline__ bool stencil4(const DevOp &op, const DevOp32 &o, const float *__restrict__ p, int idx0,
-                                         float (&c)[4], float (&y)[4]) {
-    const int N = op.N, n = op.n;
-    const bool three = op.kind == DK_CD3D;
-    const int far = three ? N * N : N;                // the farthest neighbour offset
-    if (idx0 < far || idx0 + far + 8 > n) return false;
-    const float4 C = ld4(p, idx0);
-    c[0] = C.x; c[1] = C.y; c[2] = C.z; c[3] = C.w;
-    const float xl = p[idx0 - 1], xr = p[idx0 + 4];
-    float ym[4], yp[4], zm[4], zp[4];
-    window4(p, idx0 - N, ym);
-    window4(p, idx0 + N, yp);
-    if (three) {
-        window4(p, idx0 - far, zm);
-        window4(p, idx0 + far, zp);
-    }
-    // coordinates of the first point, then carried along x
-    int i, j, k = 0;
-    if (three) {
-        const int q = (int)op.fN.div((unsigned)idx0);
-        k = (int)op.fNN.div((unsigned)idx0);
-        i = idx0 - q * N;
-        j = q - k * N;
-    } else {
-        j = (int)op.fN.div((unsigned)idx0);
-        i = idx0 - j * N;
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const float xw = e == 0 ? xl : c[e - 1];
-        const float xe = e == 3 ? xr : c[e + 1];
-        float v = o.c0 * c[e];
-        v = i > 0 ? fmaf(o.cxm, xw, v) : v;
-        v = i < N - 1 ? fmaf(o.cxp, xe, v) : v;
-        v = j > 0 ? fmaf(o.cym, ym[e], v) : v;
-        v = j < N - 1 ? fmaf(o.cyp, yp[e], v) : v;
-        if (three) {
-            v = k > 0 ? fmaf(o.czm, zm[e], v) : v;
-            v = k < N - 1 ? fmaf(o.czp, zp[e], v) : v;
-        }
-        y[e] = v;
-        if (++i == N) {            // the next point starts a new row (and maybe a new plane)
-            i = 0;
-            if (++j == N) { j = 0; ++k; }
-        }
-    }
-    return true;
-}
-
-// y = A x for float32 constant-coefficient grids (4 points per thread).
-__global__ void __launch_bounds__(kThreads) k_apply_f4(DevOp op, DevOp32 o32, const float *__restrict__ x,
-                                                        float *__restrict__ y) {
-    const int n = op.n, ng = (n + 3) >> 2;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const int idx0 = 4 * g;
-        float c[4], v[4];
-        if (stencil4(op, o32, x, idx0, c, v)) {
-            *reinterpret_cast<float4 *>(y + idx0) = make_float4(v[0], v[1], v[2], v[3]);
-        } else {
-            for (int e = 0; e < 4 && idx0 + e < n; ++e)
-                y[idx0 + e] = Apply<float>::at(op, o32, idx0 + e, [&](int jj) { return x[jj]; });
-        }
-    }
-}
-
-// whether the 4-point float32 kernels apply: constant-coefficient grid, 16-byte aligned vectors
-__host__ __forceinline__ bool f4_ok(const DevOp &A, std::initializer_list<const void *> ptrs) {
-    if (A.kind != DK_CD2D && A.kind != DK_CD3D) return false;
-    for (const void *q : ptrs)
-        if (reinterpret_cast<uintptr_t>(q) & 15) return false;
-    return true;
-}
-
-// k_bi_v for float32 constant-coefficient grids: v = A p, sigma = <r_hat, v>, alpha = rho / sigma.
-__global__ void __launch_bounds__(kThreads) k_bi_v_f4(DevOp op, DevOp32 o32, const float *__restrict__ p,
-                                                       const float *__restrict__ rh, float *__restrict__ v,
-                                                       double *part, unsigned *ticket, BiState<double> *st) {
-    if (st->status != 0) return;
-    __shared__ double red[(kThreads / 32)];
-    __shared__ double tot[1];
-    float acc[1] = {0.0f};
-    const int n = op.n, ng = (n + 3) >> 2;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const int idx0 = 4 * g;
-        float c[4], y[4];
-        if (stencil4(op, o32, p, idx0, c, y)) {
-            const float4 r = ld4(rh, idx0);
-            *reinterpret_cast<float4 *>(v + idx0) = make_float4(y[0], y[1], y[2], y[3]);
-            acc[0] = fmaf(r.x, y[0], acc[0]);
-            acc[0] = fmaf(r.y, y[1], acc[0]);
-            acc[0] = fmaf(r.z, y[2], acc[0]);
-            acc[0] = fmaf(r.w, y[3], acc[0]);
-        } else {
-            for (int e = 0; e < 4 && idx0 + e < n; ++e) {
-                const float yy = Apply<float>::at(op, o32, idx0 + e, [&](int jj) { return p[jj]; });
-                v[idx0 + e] = yy;
-                acc[0] = fmaf(rh[idx0 + e], yy, acc[0]);
-            }
-        }
-    }
-    block_reduce_store<float, double, 1>(acc, part, red);
-    if (last_block(ticket)) {
-        final_sum<double, 1>(part, tot, ticket);
-        if (threadIdx.x == 0) {
-            const double sigma = tot[0];
-            st->mvps += 1;
-            if (!isfinite(sigma)) st->status = 4;
-            else if (fabs(sigma) < kTiny) st->status = 2;
-            else st->alpha = st->rho / sigma;
-        }
-    }
-}
-
-// k_bi_t for float32 constant-coefficient grids: t = A s; <t,s>, <t,t>, <r_hat,s>, <r_hat,t>;
-// omega, rho_next and beta as in k_bi_t.
-__global__ void __launch_bounds__(kThreads) k_bi_t_f4(DevOp op, DevOp32 o32, const float *__restrict__ s,
-                                                       const float *__restrict__ rh, float *__restrict__ t,
-                                                       double *part, unsigned *ticket, BiState<double> *st) {
-    if (st->status != 0 || st->half) return;
-    __shared__ double red[(kThreads / 32) * 4];
-    __shared__ double tot[4];
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const int n = op.n, ng = (n + 3) >> 2;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const int idx0 = 4 * g;
-        float c[4], y[4];
-        if (stencil4(op, o32, s, idx0, c, y)) {
-            const float4 r = ld4(rh, idx0);
-            *reinterpret_cast<float4 *>(t + idx0) = make_float4(y[0], y[1], y[2], y[3]);
-            const float rr[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                acc[0] = fmaf(y[e], c[e], acc[0]);
-                acc[1] = fmaf(y[e], y[e], acc[1]);
-                acc[2] = fmaf(rr[e], c[e], acc[2]);
-                acc[3] = fmaf(rr[e], y[e], acc[3]);
-            }
-        } else {
-            for (int e = 0; e < 4 && idx0 + e < n; ++e) {
-                const int i = idx0 + e;
-                const float ti = Apply<float>::at(op, o32, i, [&](int jj) { return s[jj]; });
-                t[i] = ti;
-                const float si = s[i], ri = rh[i];
-                acc[0] = fmaf(ti, si, acc[0]);
-                acc[1] = fmaf(ti, ti, acc[1]);
-                acc[2] = fmaf(ri, si, acc[2]);
-                acc[3] = fmaf(ri, ti, acc[3]);
-            }
-        }
-    }
-    block_reduce_store<float, double, 4>(acc, part, red);
-    if (last_block(ticket)) {
-        final_sum<double, 4>(part, tot, ticket);
-        if (threadIdx.x == 0) {
-            st->mvps += 1;
-            const double tt = tot[1];
-            if (!isfinite(tt) || !isfinite(tot[0])) {
-                st->status = 4;
-            } else if (tt < kTiny) {
-                st->half = 1;
-                st->pending = 2;
-            } else {
-                const double omega = tot[0] / tt;
-                st->omega = omega;
-                const double rn = tot[2] - omega * tot[3];
-                st->rho_next = rn;
-                if (fabs(omega) >= kTiny) st->beta = (rn / st->rho) * (st->alpha / omega);
-            }
         }
     }
 }

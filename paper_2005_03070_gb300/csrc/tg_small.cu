@@ -916,7 +916,7 @@ __global__ void k_small_gemv(const D *M, int k, const D *c, D *out) {
 // ----------------------------------------------------------------------------- GMRES-DR restart
 // See tg_small.cuh for the argument layout.
 template <class T>
-__global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
+__device__ __forceinline__ void gmresdr_restart_body(const GdrArgs<T> &a) {
     const int m = a.m;
     const int rows = m + 1;
     const int ldh = a.ldh;
@@ -1288,6 +1288,20 @@ __global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
     if (threadIdx.x == 0) a.info->phase[7] = clock64() - t_mark;
 }
 
+template <class T>
+__global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart(GdrArgs<T> a) {
+    gmresdr_restart_body<T>(a);
+}
+
+// many independent restart steps, one block each (the batched coarse phase): block b runs
+// args[b] when active[b] is set
+template <class T>
+__global__ void __launch_bounds__(kGdrThreads) k_gmresdr_restart_batch(const GdrArgs<T> *args, const int *active) {
+    if (!active[blockIdx.x]) return;
+    const GdrArgs<T> a = args[blockIdx.x];
+    gmresdr_restart_body<T>(a);
+}
+
 // ----------------------------------------------------------------------------- GMRES(m) Givens step
 // Column j of the Arnoldi Hessenberg (h[0..j+1], ld = m+1) is rotated by the previous
 // rotations, a new rotation zeroes h[j+1]; g (the least-squares right-hand side) is
@@ -1368,6 +1382,29 @@ cudaError_t launch_gmresdr_restart(const GdrArgs<T> &a_in, cudaStream_t s) {
     k_gmresdr_restart<T><<<1, kGdrThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
+template <class T>
+size_t gmresdr_restart_smem(int m, int *parts) {
+    const size_t mm = m;
+    const size_t sizes[4] = {(mm + 1) * mm * sizeof(T), mm * mm * sizeof(T), mm * mm * sizeof(T), mm * mm * sizeof(cplx)};
+    size_t smem = 0;
+    *parts = 0;
+    for (int q = 0; q < 4 && smem + sizes[q] <= kGdrSmemMax; ++q) {
+        smem += sizes[q];
+        *parts = q + 1;
+    }
+    return smem;
+}
+template <class T>
+cudaError_t launch_gmresdr_restart_batch(const GdrArgs<T> *args, const int *active, int count, int m, cudaStream_t s) {
+    int parts = 0;
+    const size_t smem = gmresdr_restart_smem<T>(m, &parts);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = smem_attr_once((const void *)k_gmresdr_restart_batch<T>, (int)kGdrSmemMax);
+        if (e != cudaSuccess) return e;
+    }
+    k_gmresdr_restart_batch<T><<<count, kGdrThreads, smem, s>>>(args, active);
+    return cudaGetLastError();
+}
 template <class D>
 void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s) {
     k_givens_step<D><<<1, 1, 0, s>>>(H, ldh, j, cs, sn, g, state);
@@ -1382,6 +1419,8 @@ void launch_givens_solve(const D *H, int ldh, const D *g, D *y, const GivensStat
     template void launch_inverse<D>(const D *, int, D *, D *, int *, cudaStream_t);                  \
     template void launch_small_gemv<D>(const D *, int, const D *, D *, cudaStream_t);                \
     template cudaError_t launch_gmresdr_restart<D>(const GdrArgs<D> &, cudaStream_t);                \
+    template size_t gmresdr_restart_smem<D>(int, int *);                                              \
+    template cudaError_t launch_gmresdr_restart_batch<D>(const GdrArgs<D> *, const int *, int, int, cudaStream_t); \
     template void launch_givens_step<D>(D *, int, int, D *, D *, D *, GivensState *, cudaStream_t);  \
     template void launch_givens_solve<D>(const D *, int, const D *, D *, const GivensState *, cudaStream_t);
 TG_INST(double)

@@ -67,6 +67,14 @@ template <class D> void launch_small_gemv(const D *M, int k, const D *c, D *out,
 // Returns the error of raising the kernel's shared-memory limit (nothing is launched then)
 // or of the launch itself.
 template <class T> cudaError_t launch_gmresdr_restart(const GdrArgs<T> &a, cudaStream_t s);
+// The dynamic shared memory of the restart kernel for subspace size m, and how many of its
+// work matrices it holds (the rest live in the global scratch); a.smem must be set to that
+// count in every entry of a batched launch.
+template <class T> size_t gmresdr_restart_smem(int m, int *parts);
+// count independent restart steps of size m in one launch (one block each; args and active
+// in device memory).
+template <class T>
+cudaError_t launch_gmresdr_restart_batch(const GdrArgs<T> *args, const int *active, int count, int m, cudaStream_t s);
 template <class D>
 void launch_givens_step(D *H, int ldh, int j, D *cs, D *sn, D *g, GivensState *state, cudaStream_t s);
 template <class D>

@@ -37,6 +37,7 @@ EXPORTS = [
     "tg_kappa_gradient",
     "tg_harmonic_ritz", "tg_harmonic_ritz_noalloc", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
     "tg_batch_create", "tg_batch_layout", "tg_batch_setup", "tg_batch_solve", "tg_destroy_batch",
+    "tg_batch_tuning",
 ]
 
 
@@ -99,6 +100,8 @@ def load() -> C.CDLL:
         "tg_batch_setup": (i32, [vp, vp, i32, i32, i32, dbl, dbl, i32, i32, i32, C.POINTER(TgStats), vp]),
         "tg_batch_solve": (i32, [vp, vp, vp, dbl, i32, i32, i64, i32, C.POINTER(TgStats), vp]),
         "tg_destroy_batch": (i32, [vp]),
+        "tg_batch_tuning": (i32, [vp, C.POINTER(i32), C.POINTER(dbl), C.POINTER(i32), C.POINTER(i32),
+                                  C.POINTER(dbl)]),
         "tg_profile_enable": (i32, [i32]),
         "tg_profile_read": (i32, [C.c_char_p, i32]),
         "tg_launch_count": (i64, []),
@@ -390,6 +393,15 @@ class Batch:
                                  _stream(stream))
         _check(st, "tg_batch_setup")
         return [s.as_dict() for s in stats]
+
+    def tuning(self):
+        """tg_batch_tuning: {"blocks_per_instance", "us_per_iteration", "candidates": {blocks: us}}."""
+        g, us, nc = C.c_int(), C.c_double(), C.c_int()
+        cb = (C.c_int * 8)()
+        cu = (C.c_double * 8)()
+        _check(_lib.tg_batch_tuning(self._h, C.byref(g), C.byref(us), C.byref(nc), cb, cu), "tg_batch_tuning")
+        return {"blocks_per_instance": g.value, "us_per_iteration": round(us.value, 2),
+                "candidates": {str(cb[i]): round(cu[i], 2) for i in range(nc.value)}}
 
     def solve(self, rhs, x, rtol=1e-8, ncyc=20, restart_mvps=0, max_mvps=10 ** 6, threads=16, stream=None):
         stats = (TgStats * (self.count * self.R))()

@@ -79,3 +79,20 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
                                       C.c_void_p(basis.data_ptr()), None, C.byref(kk), None)
     assert st == 4
     assert b"m <= 128" in lib.tg_last_error()
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_noalloc_at_its_size_limit(lib, cplx):
+    """m = 128, the largest size the fixed array is carved for (complex arithmetic needs the
+    most of it), against the allocating entry point, twice in a row."""
+    m, k = 128, 40
+    for seed in (4, 5):
+        H = _hessenberg(m, seed, cplx)
+        th_a, b_a, e_a = _call(lib, "tg_harmonic_ritz", H, m, k, cplx)
+        th_b, b_b, e_b = _call(lib, "tg_harmonic_ritz_noalloc", H, m, k, cplx)
+        z_a = th_a[:, 0] + 1j * th_a[:, 1]
+        z_b = th_b[:, 0] + 1j * th_b[:, 1]
+        assert np.max(np.abs(z_a - z_b) / np.abs(z_a)) <= 1e-10
+        assert b_a.shape == b_b.shape
+        assert _span_gap(b_a, b_b) <= 1e-8
+        assert np.allclose(e_a, e_b, rtol=1e-10, atol=1e-14)
