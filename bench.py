@@ -49,6 +49,10 @@ WORKLOADS = {
     "batch128": dict(kind="batch", count=128, m=40, k=20, nev=20, rtolev=1e-2, rtol_c=1e-8, max_cycles=300,
                      method="bicgstab", proj="minres", precision="f32_ir", rtol=1e-8, ncyc=20, restart_mvps=0,
                      threads=32),
+    # a 16-instance cut of the batched workload (same size range) for profiler captures
+    "batch16": dict(kind="batch", count=16, m=40, k=20, nev=20, rtolev=1e-2, rtol_c=1e-8, max_cycles=300,
+                    method="bicgstab", proj="minres", precision="f32_ir", rtol=1e-8, ncyc=20, restart_mvps=0,
+                    threads=16),
     "cd2d_127": dict(kind="cd2d", N=127, beta=(1.0,), m=30, k=15, nev=15, rtolev=1e-4, rtol_c=1e-8,
                      max_cycles=300, method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=0,
                      restart_mvps=60, m3=20),
