@@ -3,8 +3,10 @@
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Section 3, phase 1: the coarse solution and the approximate eigenvectors are moved to
-the fine grid.  The paper uses spline interpolation; this build uses bilinear (2D),
-trilinear (3D) and 2^4 block transport (lattice) instead.  Readings taken:
+the fine grid.  The paper generally uses spline interpolation; this build uses bilinear
+(2D), trilinear (3D) and 2^4 block transport (lattice) by default, and offers a
+fourth-order cubic interpolation on the grids (below) as the stand-in for the splines.
+Readings taken:
 
   * Nested vertex-centred grids: N = 2 N_c + 1; coarse node I sits on fine node 2I;
     coarse values beyond the grid (I = 0, N_c + 1) are the Dirichlet zero.
@@ -86,6 +88,55 @@ def prolong3d(uc: np.ndarray, Nc: int) -> np.ndarray:
                 w = 0.5 ** (px + py + pz)
                 F[fz, fy, fx] = w * tot
     return F.reshape(-1).copy()
+
+
+# ----------------------------------------------------------------------------- cubic
+# Fourth-order interpolation standing in for the paper's spline interpolation (Section 3,
+# phase 1: the paper generally uses splines to move the eigenvectors).  Readings taken:
+#
+#  * a new fine point halfway between coarse nodes a and a + 1 takes the cubic through the
+#    four coarse nodes a - 1 .. a + 2: weights (-1, 9, 9, -1) / 16 (exact for cubics);
+#    fine points on coarse nodes copy them;
+#  * beyond the Dirichlet boundary the grid function is continued oddly: node 0 and node
+#    N_c + 1 are the boundary zeros, node -1 is -u(1) and node N_c + 2 is -u(N_c), so
+#    every mode sin(p pi x) is continued exactly;
+#  * tensor product, axes in the order x, y, z; each 4-term sum is evaluated as
+#    ((w0 v0 + w1 v1) + w2 v2) + w3 v3 with separate rounded products (the weights are
+#    exact binary fractions), so the result is reproducible bit for bit.
+
+CUBIC_W = (-0.0625, 0.5625, 0.5625, -0.0625)
+
+
+def _cubic_axis(U: np.ndarray) -> np.ndarray:
+    """Interpolate along the last axis: (..., Nc) -> (..., 2 Nc + 1)."""
+    Nc = U.shape[-1]
+    z = np.zeros_like(U[..., :1])
+    # padded nodes -1, 0, 1..Nc, Nc+1, Nc+2 at positions 0..Nc+3
+    P = np.concatenate([-U[..., :1], z, U, z, -U[..., -1:]], axis=-1)
+    out = np.empty(U.shape[:-1] + (2 * Nc + 1,))
+    out[..., 1::2] = U                           # fine index 2I (1-based) = coarse node I
+    a = np.arange(0, Nc + 1)                     # fine index 2a + 1 lies between nodes a, a + 1
+    v = [P[..., a + q] for q in range(4)]        # nodes a - 1 .. a + 2 sit at positions a .. a + 3
+    w = CUBIC_W
+    out[..., 0::2] = ((w[0] * v[0] + w[1] * v[1]) + w[2] * v[2]) + w[3] * v[3]
+    return out
+
+
+def prolong2d_cubic(uc: np.ndarray, Nc: int) -> np.ndarray:
+    """Cubic prolongation, coarse Nc^2 -> fine (2Nc+1)^2, x fastest (x first, then y)."""
+    U = uc.reshape(Nc, Nc)                       # [J, I]
+    T = _cubic_axis(U)                           # [J, i]
+    F = _cubic_axis(T.T).T                       # [j, i]
+    return np.ascontiguousarray(F).reshape(-1)
+
+
+def prolong3d_cubic(uc: np.ndarray, Nc: int) -> np.ndarray:
+    """Cubic prolongation, coarse Nc^3 -> fine (2Nc+1)^3, x fastest (x, then y, then z)."""
+    U = uc.reshape(Nc, Nc, Nc)                   # [K, J, I]
+    T = _cubic_axis(U)                           # [K, J, i]
+    T = np.swapaxes(_cubic_axis(np.swapaxes(T, 1, 2)), 1, 2)       # [K, j, i]
+    F = np.swapaxes(_cubic_axis(np.swapaxes(T, 0, 2)), 0, 2)       # [k, j, i]
+    return np.ascontiguousarray(F).reshape(-1)
 
 
 def prolongation_matrix(Nc: int, dim: int):

@@ -113,6 +113,80 @@ def test_prolong2d_reproduces_linear_and_matches_sparse():
     assert np.max(np.abs(transfer.prolong2d(w, Nc) - transfer.prolongation_matrix(Nc, 2) @ w)) < 1e-15
 
 
+def _cubic_matrix_1d(Nc):
+    """The 1D cubic interpolation written entry by entry from its rule: fine node 2I copies
+    coarse node I; fine node 2a + 1 takes (-1, 9, 9, -1)/16 of nodes a-1 .. a+2, where
+    nodes 0 and Nc+1 are zero and nodes -1, Nc+2 are -u(1), -u(Nc) (odd continuation)."""
+    N = 2 * Nc + 1
+    P = np.zeros((N, Nc))
+    for i in range(1, N + 1):
+        if i % 2 == 0:
+            P[i - 1, i // 2 - 1] = 1.0
+            continue
+        a = (i - 1) // 2
+        for node, w in zip(range(a - 1, a + 3), (-1 / 16, 9 / 16, 9 / 16, -1 / 16)):
+            if node == -1:
+                P[i - 1, 0] -= w
+            elif node == Nc + 2:
+                P[i - 1, Nc - 1] -= w
+            elif 1 <= node <= Nc:
+                P[i - 1, node - 1] += w
+    return P
+
+
+def test_cubic_prolongation_pins():
+    """Cubic prolongation (the stand-in for the paper's splines): (1) fine nodes on coarse
+    nodes copy them bit for bit; (2) it reproduces cubic polynomials wherever its stencil
+    stays inside the grid; (3) it equals the entry-by-entry Kronecker product of the 1D
+    rule; (4) on the Dirichlet modes sin(p pi x) sin(q pi y) the error is fourth order (the
+    odd continuation is exact for them, boundary rows included) and within the Lagrange
+    remainder bound of the 4-point cubic at a midpoint, 9/16 h^4 |f''''| / 24 per axis."""
+    rng = np.random.default_rng(11)
+    Nc = 9
+    N = 2 * Nc + 1
+    uc = rng.standard_normal(Nc * Nc)
+    uf = transfer.prolong2d_cubic(uc, Nc).reshape(N, N)
+    assert np.array_equal(uf[1::2, 1::2], uc.reshape(Nc, Nc))
+    P1 = _cubic_matrix_1d(Nc)
+    assert np.max(np.abs(uf.reshape(-1) - np.kron(P1, P1) @ uc)) < 1e-14
+    uc3 = rng.standard_normal(5 ** 3)
+    P5 = _cubic_matrix_1d(5)
+    assert np.max(np.abs(transfer.prolong3d_cubic(uc3, 5) - np.kron(P5, np.kron(P5, P5)) @ uc3)) < 1e-14
+    # cubic polynomials
+    hc, h = 1.0 / (Nc + 1), 1.0 / (N + 1)
+
+    def cub(x, y):
+        return 0.2 - x + 2.0 * x ** 3 - 0.5 * x ** 2 * y + 1.5 * y ** 3 + 0.7 * x * y ** 2
+
+    J, I = np.meshgrid(np.arange(1, Nc + 1), np.arange(1, Nc + 1), indexing="ij")
+    ufc = transfer.prolong2d_cubic(cub(I * hc, J * hc).reshape(-1), Nc).reshape(N, N)
+    j, i = np.meshgrid(np.arange(1, N + 1), np.arange(1, N + 1), indexing="ij")
+    inner = (i >= 4) & (i <= N - 3) & (j >= 4) & (j <= N - 3)   # every stencil node in 1..Nc
+    assert inner.sum() > 0
+    assert np.max(np.abs(ufc - cub(i * h, j * h))[inner]) < 1e-13
+    # fourth order on a Dirichlet mode, boundary rows included
+    p, q = 3, 2
+    errs = []
+    for Ncs in (15, 31, 63):
+        Ns = 2 * Ncs + 1
+        xc = np.arange(1, Ncs + 1) / (Ncs + 1)
+        xf = np.arange(1, Ns + 1) / (Ns + 1)
+        mode_c = np.outer(np.sin(q * np.pi * xc), np.sin(p * np.pi * xc)).reshape(-1)
+        mode_f = np.outer(np.sin(q * np.pi * xf), np.sin(p * np.pi * xf))
+        e = np.max(np.abs(transfer.prolong2d_cubic(mode_c, Ncs).reshape(Ns, Ns) - mode_f))
+        bound = (9 / 16) / 24 * (1.0 / (Ncs + 1)) ** 4 * ((p * np.pi) ** 4 + (q * np.pi) ** 4) * (1 + 1 / 8)
+        assert e <= bound
+        errs.append(e)
+    assert 12.0 < errs[0] / errs[1] < 20.0 and 12.0 < errs[1] / errs[2] < 20.0
+    # bilinear is only second order on the same mode
+    Ncs = 31
+    xc = np.arange(1, Ncs + 1) / (Ncs + 1)
+    xf = np.arange(1, 2 * Ncs + 2) / (2 * Ncs + 2)
+    mode_c = np.outer(np.sin(q * np.pi * xc), np.sin(p * np.pi * xc)).reshape(-1)
+    mode_f = np.outer(np.sin(q * np.pi * xf), np.sin(p * np.pi * xf)).reshape(-1)
+    assert np.max(np.abs(transfer.prolong2d(mode_c, Ncs) - mode_f)) > 20 * errs[1]
+
+
 def test_prolong3d_reproduces_linear_and_matches_sparse():
     Nc = 4
     N = 2 * Nc + 1
