@@ -74,12 +74,16 @@ PAPER_RUNS = {
                                                               "7": 177, "none": 1255},
                            "table_3_1_coarse_cycles": {"255": 1023, "127": 270, "63": 107, "31": 43, "15": 12}}),
     "helm_511": dict(kind="cd2d", beta=(0.0,), mass=-1e4, N=511, coarse_N=127, m=200, k=150, nev=120, rtolev=1e-8,
-                     rtol_c=1e-10, max_cycles=400, rtol=1e-10, rhs="random", proj="galerkin",
+                     rtol_c=1e-10, max_cycles=400, rtol=1e-10, rhs="random", proj="galerkin", interp="cubic",
                      bicg_ncyc=[20], gmres_m3=[100], idr_ncyc=[20], coarse_sweep=[],
                      paper={"coarse_cycles_eig": 285, "note": "GMRES(100)-Proj(150) and IDR(20)-Proj(150) converge; "
                                                               "IDR(20)-Proj(150) is the fastest; plain IDR does not "
                                                               "converge (Figure 5.1, counts not printed)"}),
 }
+# the same experiments with the other interpolation (the paper generally uses splines; the
+# cubic interpolation stands in for them, bilinear is the default of the library)
+PAPER_RUNS["helm_511_linear"] = dict(PAPER_RUNS["helm_511"], interp="linear")
+PAPER_RUNS["ex1_511_cubic"] = dict(PAPER_RUNS["ex1_511"], interp="cubic", coarse_sweep=[])
 L2_BYTES = 129 * 1024 * 1024
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12     # 152 SMs x 2 FP64 FMA/clk x 2 flops per FMA x 2070 MHz
 NOMINAL_HBM_GBS = 8000.0                         # the ~8 TB/s nominal HBM3e figure the 70% target refers to
@@ -89,6 +93,29 @@ NOMINAL_HBM_GBS = 8000.0                         # the ~8 TB/s nominal HBM3e fig
 # the traffic of a full-size launch is this ratio times its algorithmic bytes (the traffic
 # grows in proportion to rows x columns).  Remove an entry when its kernel changes.
 NCU_TRAFFIC_RATIO = {"gemv_t": 1.024}
+
+
+def dgemm_tflops(dev, n=4096, reps=5):
+    """cuBLAS float64 GEMM rate on this GPU (torch.matmul), measured with CUDA events: the
+    attainable float64 rate beside the derived FP64 peak (context for the ALU-bound kernels)."""
+    import torch
+    try:
+        a = torch.randn(n, n, dtype=torch.float64, device=dev)
+        b = torch.randn(n, n, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            torch.matmul(a, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        del a, b
+        return round(reps * 2.0 * n ** 3 / t / 1e12, 4)
+    except Exception:
+        return None
 
 
 def measured_peaks():
@@ -369,9 +396,12 @@ def run_tg(args, wl, rank, world):
     tflops = dom["flops"] / (dom["ms"] * 1e-3) / 1e12
     ratio = NCU_TRAFFIC_RATIO.get(dom_name)
     traffic = None if ratio is None else ratio * dom["bytes"] / dom["launches"]
+    dgemm = dgemm_tflops(dev)
     roofline = {"kernel": dom_name, "bound": "alu", "achieved": round(tflops, 4),
                 "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops per FMA x 2070 MHz",
+                "fp64_dgemm_tflops_measured": dgemm,
+                "frac_of_dgemm": round(tflops / dgemm, 4) if dgemm else None,
                 "traffic": traffic, "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
                 "algorithmic_flops_per_launch": dom["flops"] / dom["launches"],
                 "ms_per_launch": round(per_launch_ms, 5), "hbm_gbs": round(gbs, 1),
@@ -423,7 +453,7 @@ def run_tg(args, wl, rank, world):
         "profile_note": "kernels / roofline from one extra step per precision with CUDA events around every "
                         "launch (eager launches), outside the timed regions",
         "gmresdr_restart_phase_us": None if not phases else
-            [round(p / max(1, cst["cycles"] * args.steps) / 2070.0, 1) for p in phases],
+            [round(p / max(1, cst["cycles"]) / 2070.0, 1) for p in phases],
         "clocks": clocks.summary(),
     }
     return line, {"coarse_cycles": cst["cycles"], "fine_mvps": st["mvps"], "fine_cycles": st["cycles"],
@@ -706,6 +736,10 @@ def run_batch(args, wl, rank, world, fp64_instances=0):
     split64["solve"] = max_over_ranks_of(split64["solve"], world, dev)
     value = weak_scaling_rate(nsolves, ms, world)
     n_tot = int(sum(batch.sizes))
+    tune = batch.tuning()
+    peaks, peak_src = measured_peaks()
+    iter_bytes = n_tot * 8 * 17 * 4
+    iter_gbs = iter_bytes / (tune["us_per_iteration"] * 1e-6) / 1e9 if tune["us_per_iteration"] > 0 else 0.0
     line = {
         "metric": "fine-grid solves/sec to rel. residual 1e-8 (FP64 vs batched FP32+IR) and HBM GB/s",
         "value": round(value, 3), "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -738,7 +772,16 @@ def run_batch(args, wl, rank, world, fp64_instances=0):
                               "speedup_of_batched": round((world * nsolves * 1000.0 / ms) /
                                                           (world * nsolves64 * 1000.0 / ms64), 3)},
         "gpu_launches": int(launches),
-        "autotuner": batch.tuning(),
+        "autotuner": tune,
+        # the batched BiCGStab iteration (the four phase kernels over all instances and columns):
+        # algorithmic bytes 17 float32 words per point and right-hand side, over the iteration
+        # time the autotuner measured with CUDA events on the batch's stream (all columns active)
+        "roofline": {"kernel": "batched BiCGStab iteration (k_mrb_bi_v/s/t/x, all instances)", "bound": "hbm",
+                     "achieved": round(iter_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(iter_gbs / peaks["hbm_gbs"], 4),
+                     "frac_nominal": round(iter_gbs / NOMINAL_HBM_GBS, 4), "peak_source": peak_src,
+                     "algorithmic_bytes_per_iteration": iter_bytes, "us_per_iteration": tune["us_per_iteration"],
+                     "traffic": None},
         "clocks": clocks.summary(),
     }
     return line
@@ -771,7 +814,7 @@ def run_paper(args, name, rank, world):
 
     def op_of(Nl):
         if Nl not in ops:
-            ops[Nl] = tg.Operator(cfg["kind"], Nl, cfg["beta"], mass=cfg["mass"])
+            ops[Nl] = tg.Operator(cfg["kind"], Nl, cfg["beta"], mass=cfg["mass"], interp=cfg.get("interp", "linear"))
         return ops[Nl]
 
     if cfg["rhs"] == "example1":
@@ -929,7 +972,7 @@ def main():
         line["batch128"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "solves_converged",
                                                "not_converged", "relres_max", "mvps_mean", "step_phases_ms",
                                                "solve_only", "e2e", "fp64_per_instance", "gpu_launches", "autotuner",
-                                               "clocks")}
+                                               "roofline", "clocks")}
         line["batch128"]["config"] = bl["config"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ("cd2d", "cd3d"):
         v, info = cpu_sample(wl, counts)

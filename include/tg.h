@@ -129,6 +129,19 @@ int tg_apply(const tg_op *op, int level, int transpose, int precision,
 int tg_prolong(const tg_op *op, const void *coarse, void *fine, int ncols, void *stream);
 int tg_restrict(const tg_op *op, const void *fine, void *coarse, int ncols, void *stream);
 
+/* Interpolation used by every prolongation of this operator (tg_prolong, the moved
+ * eigenvectors and x0 of tg_coarse_gmresdr, the batched set-up).  TG_INTERP_LINEAR (the
+ * default): bilinear / trilinear as above.  TG_INTERP_CUBIC: fourth-order interpolation in
+ * place of the paper's splines (Section 3, phase 1 "we generally use spline
+ * interpolation"): a fine point halfway between coarse nodes a, a+1 takes (-1, 9, 9, -1)/16
+ * of nodes a-1..a+2, with the grid function continued oddly beyond the Dirichlet boundary
+ * (node -1 = -u(1), node Nc+2 = -u(Nc)); tensor product in x, then y, then z, each sum
+ * rounded in a fixed order, so results are reproducible bit for bit.  Grid kinds only
+ * (TG_BAD_ARG for the lattice or an unknown value).  The restriction is unchanged.     */
+#define TG_INTERP_LINEAR 0
+#define TG_INTERP_CUBIC  1
+int tg_op_set_interp(tg_op *op, int interp);
+
 /* ------------------------------------------------------------------ phase 1: coarse solve
  * GMRES-DR(m,k) (Section 2.1) on the coarse operator (transpose = 1: on A_c^T, giving
  * left eigenvectors for the adjoint solve), right-hand side b_c = restrict(b_fine)
@@ -279,6 +292,10 @@ int tg_kappa_gradient(const tg_op *op, const void *x, const void *lambda, void *
  *   sequence of all instances as one CUDA graph until every column of the cycle has
  *   finished.  The graph's blocks per instance are chosen on the first solve of a handle
  *   by timing the candidates 8, 16, 32, 64, 128 on the first cycle (tg_batch_tuning).
+ *   A float32 correction that raises a column's float64 residual more than 4-fold is undone
+ *   and that column's cycle cap halved; a column that no float32 cycle can advance finishes
+ *   with float64 BiCGStab(-Proj) cycles on its instance's operator and basis
+ *   (stats.fp64_cycles, per instance).
  *   Both calls wait for `stream` first and return when all work is done (they run on a
  *   private stream).  stats: count (setup) / count * 8 (solve) entries.
  * Returns TG_OK when every column converged, else the first failing status.           */

@@ -238,6 +238,7 @@ struct tg_op {
     bool cplx_ = false;
     double beta[3] = {0, 0, 0};
     double mass = 0;
+    int interp = TG_INTERP_LINEAR;
     Level fine, coarse;
     DBuf kappa, kappa_c, coef, coef32, coefT, coefT32, ccoef, ccoef32, ccoefT, ccoefT32;
     DBuf links, pw, cst;
@@ -739,8 +740,14 @@ static int prolong_impl(const tg_op *op, const void *coarse, void *fine, int nco
         } else {
             const double *uc = (const double *)coarse + (size_t)c * op->nc;
             double *uf = (double *)fine + (size_t)c * op->n;
-            if (op->dim == 3) TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), 0, launch_prolong3d(grid_for(op->n, 8), s, uc, op->Nc, uf));
-            else TG_PROF(P_TRANSFER, (double)(op->n + op->nc) * elem_size(op), 0, launch_prolong2d(grid_for(op->n, 8), s, uc, op->Nc, uf));
+            const double bytes = (double)(op->n + op->nc) * elem_size(op);
+            if (op->interp == TG_INTERP_CUBIC) {
+                if (op->dim == 3) TG_PROF(P_TRANSFER, bytes, 0, launch_prolong3d_cubic(grid_for(op->n, 8), s, uc, op->Nc, uf));
+                else TG_PROF(P_TRANSFER, bytes, 0, launch_prolong2d_cubic(grid_for(op->n, 8), s, uc, op->Nc, uf));
+            } else {
+                if (op->dim == 3) TG_PROF(P_TRANSFER, bytes, 0, launch_prolong3d(grid_for(op->n, 8), s, uc, op->Nc, uf));
+                else TG_PROF(P_TRANSFER, bytes, 0, launch_prolong2d(grid_for(op->n, 8), s, uc, op->Nc, uf));
+            }
         }
         TG_LAUNCH_CHECK();
     }
@@ -767,6 +774,14 @@ static int restrict_impl(const tg_op *op, const void *fine, void *coarse, int nc
 extern "C" int tg_prolong(const tg_op *op, const void *coarse, void *fine, int ncols, void *stream) {
     TG_ARG(op && coarse && fine && ncols >= 0, "bad argument");
     return prolong_impl(op, coarse, fine, ncols, (cudaStream_t)stream);
+}
+
+extern "C" int tg_op_set_interp(tg_op *op, int interp) {
+    TG_ARG(op, "NULL operator");
+    TG_ARG(interp == TG_INTERP_LINEAR || interp == TG_INTERP_CUBIC, "unknown interpolation %d", interp);
+    TG_ARG(!op->cplx_ || interp == TG_INTERP_LINEAR, "the lattice transfer is block transport only");
+    op->interp = interp;
+    return TG_OK;
 }
 
 extern "C" int tg_restrict(const tg_op *op, const void *fine, void *coarse, int ncols, void *stream) {
@@ -973,12 +988,33 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     BiVecs<T> w;
     TG_CHECK(bicg_vecs<T>(op, n, &w));
     const int g = grid_for(n, 8);
-    TG_CHECK(red_ready(op, (size_t)g * 4 * sizeof(D), s));
+    // float32 constant-coefficient 3D grids: the plane-marching stencil kernels, each block
+    // marching zlen planes; zlen is chosen so that one wave of resident blocks (8 per SM)
+    // covers the grid
+    const bool use_plane = std::is_same<T, float>::value && A.kind == DK_CD3D;
+    int zlen_v = 0, zlen_t = 0, gp_v = 0, gp_t = 0;
+    if (use_plane) {
+        const int tiles = plane_tiles_xy(A.N);
+        auto pick_z = [&](int per_sm, int *zl, int *blocks) {
+            const int nz = std::max(1, std::min(A.N, num_sms() * per_sm / tiles));
+            *zl = (A.N + nz - 1) / nz;
+            *blocks = tiles * ((A.N + *zl - 1) / *zl);
+        };
+        pick_z(8, &zlen_v, &gp_v);
+        pick_z(8, &zlen_t, &gp_t);
+    }
+    const int gp = std::max(gp_v, gp_t);
+    TG_CHECK(red_ready(op, (size_t)(g > gp ? g : gp) * 4 * sizeof(D), s));
     D *part = wsp<D>(op, S_PART);
     unsigned *tk = wsp<unsigned>(op, S_TICKET);
     BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL) + SmallArea::bistate);
     TG_PROF(P_BI_INIT, 3.0 * n * sizeof(T), 2.0 * n, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
     TG_LAUNCH_CHECK();
+    // float32 streaming updates with 16-byte aligned vectors: 4 points per thread
+    bool use_v4 = false;
+    if constexpr (std::is_same<T, float>::value)
+        use_v4 = !(((uintptr_t)x | (uintptr_t)r | (uintptr_t)w.p | (uintptr_t)w.v | (uintptr_t)w.s | (uintptr_t)w.t) & 15);
+    const int g4 = grid_for((n + 3) / 4, 8);
     int chunk = 2;
     int launched = 0;
     BiState<D> h{};
@@ -990,10 +1026,30 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     int iters_prev = 0;
     while (true) {
         for (int c = 0; c < chunk; ++c) {
-            TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
-            TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
-            TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
-            TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
+            if (use_plane) {
+                if constexpr (std::is_same<T, float>::value)
+                    TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_plane<0><<<gp_v, 256, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st, zlen_v));
+            } else {
+                TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
+            }
+            if (use_v4) {
+                if constexpr (std::is_same<T, float>::value)
+                    TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s_f4<<<g4, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
+            } else {
+                TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
+            }
+            if (use_plane) {
+                if constexpr (std::is_same<T, float>::value)
+                    TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_plane<1><<<gp_t, 256, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st, zlen_t));
+            } else {
+                TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
+            }
+            if (use_v4) {
+                if constexpr (std::is_same<T, float>::value)
+                    TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x_f4<<<g4, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
+            } else {
+                TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
+            }
         }
         TG_LAUNCH_CHECK();
         launched += chunk;
@@ -1136,6 +1192,7 @@ static int solve_bicg64(tg_op *op, int transpose, const tg_defl *df, const T *b,
 
 // float32 inner cycles with float64 refinement (real operators only).
 constexpr int64_t kIrCycleCap = 2000;
+constexpr double kIrGrowth = 4.0;        // batched form: a correction raising ||r|| more than this is undone
 static int solve_bicg_ir(tg_op *op, int transpose, const tg_defl *df, const double *b, double *x, const SolveCfg &cfg,
                          tg_stats *st, cudaStream_t s) {
     const DevOp &A = pick(op, TG_FINE, transpose);
@@ -2241,7 +2298,7 @@ struct BatchCoarse {
 // reduction slices, the instance table, and the captured iteration graph.
 namespace tg {
 struct BatchAll {
-    DBuf rh, p, v, s, t, r32, e32, r64, rsave, part, st, ctl, ticket, small, seg;
+    DBuf rh, p, v, s, t, r32, e32, r64, rsave, part, st, ctl, ticket, small, seg, colb, colx;
     PinBuf pin;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -2344,6 +2401,7 @@ static int batch_all_ready(tg_batch *b) {
     TG_CHECK(A.part.ensure((size_t)b->count * 128 * kMrPartW * 8));   // up to 128 blocks per instance
     TG_CHECK(A.st.ensure((size_t)b->count * R * sizeof(BiState<double>)));
     TG_CHECK(A.ctl.ensure((size_t)b->count * sizeof(MrCtl)));
+    // target2, inv, scale (R each), norms (2 R), cvec, dvec (32 R each), capv (R) per instance
     TG_CHECK(A.small.ensure((size_t)b->count * (2 * R + 2 * R + 2 * R + 2 * 32 * R) * 8));
     TG_CHECK(A.seg.ensure((size_t)b->count * sizeof(MrSeg)));
     TG_CHECK(A.pin.ensure((size_t)b->count * (R * sizeof(BiState<double>) + 4 * R * 8 + sizeof(GdrInfo)) + 4096));
@@ -2374,6 +2432,7 @@ static MrBatchPtrs batch_ptrs(tg_batch *b, int cap) {
     P.cvec = sm + 5 * B * R;
     P.dvec = sm + 5 * B * R + B * 32 * R;
     P.cap = cap;
+    P.capv = sm + 69 * B * R;
     return P;
 }
 
@@ -2428,7 +2487,8 @@ static int batch_tune(tg_batch *b) {
     TG_CHECK_CUDA(cudaMemcpyAsync(A.rsave.p, A.r32.p, tot * 4, cudaMemcpyDeviceToDevice, s));
     const int cands[] = {8, 16, 32, 64, 128};
     std::vector<double> zeros((size_t)b->count * R, 0.0);
-    const MrBatchPtrs P0 = batch_ptrs(b, INT_MAX / 2);
+    MrBatchPtrs P0 = batch_ptrs(b, INT_MAX / 2);
+    P0.capv = nullptr;
     cudaEvent_t e0, e1;
     TG_CHECK_CUDA(cudaEventCreate(&e0));
     TG_CHECK_CUDA(cudaEventCreate(&e1));
@@ -2497,8 +2557,13 @@ static int batch_solve_all(tg_batch *b, const double *Bv, double *X, const Solve
     MrBatchPtrs P = batch_ptrs(b, 0);
     double *hp = reinterpret_cast<double *>(A.pin.p);
     const size_t BR = (size_t)count * R;
-    std::vector<double> nr(BR), nb(BR), nrel(BR), hv(BR);
+    std::vector<double> nr(BR), nb(BR), nrel(BR), hv(BR), nr_before(BR), hcap(BR);
     std::vector<int64_t> mv(BR, 0);
+    // per-column cycle cap: halved after a cycle whose correction raised the float64 residual
+    // more than kIrGrowth-fold (the correction is then undone), so that the next cycle keeps
+    // only the early, still contracting part of a float32 BiCGStab that diverges later;
+    // smaller rises are kept (restarted BiCGStab is not monotone, later cycles recover them)
+    std::vector<int64_t> capc(BR, cfg.restart_mvps > 0 ? cfg.restart_mvps : kIrCycleCap);
     std::vector<int> status(BR);
     auto residual = [&]() -> int {
         TG_PROF(P_RESIDUAL, (3.0 * 8) * b->total, 12.0 * b->total,
@@ -2562,8 +2627,16 @@ static int batch_solve_all(tg_batch *b, const double *Bv, double *X, const Solve
             }
             hv[c] = t2;
         }
-        cap64 = std::min<int64_t>(cap64, cfg.restart_mvps > 0 ? cfg.restart_mvps : kIrCycleCap);
-        cap64 = std::max<int64_t>(1, std::min<int64_t>(cap64, INT_MAX / 2));
+        // per-column caps (a column whose cap was halved does not shorten the others' cycles);
+        // cap64, the largest, bounds the host loop
+        int64_t capmax = 1;
+        for (size_t c = 0; c < BR; ++c) {
+            const int64_t cc = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(cap64, capc[c]), INT_MAX / 2));
+            hcap[c] = (double)cc;
+            if (status[c] == TG_NOT_CONVERGED) capmax = std::max(capmax, cc);
+        }
+        TG_CHECK_CUDA(cudaMemcpyAsync(const_cast<double *>(P.capv), hcap.data(), BR * 8, cudaMemcpyHostToDevice, s));
+        cap64 = capmax;
         if (A.gx == 0) TG_CHECK(batch_tune(b));           // once per handle, on the first cycle's r32
         const int gx = A.gx;
         TG_CHECK_CUDA(cudaMemcpyAsync(P.target2, hv.data(), BR * 8, cudaMemcpyHostToDevice, s));
@@ -2591,26 +2664,77 @@ static int batch_solve_all(tg_batch *b, const double *Bv, double *X, const Solve
         TG_CHECK(batch_readback(b, P.st, BR * sizeof(BiState<double>)));
         std::vector<BiState<double>> hs(BR);
         memcpy(hs.data(), A.pin.p, BR * sizeof(BiState<double>));
+        std::vector<char> bad(BR, 0);
         for (size_t c = 0; c < BR; ++c) {     // a diverged or NaN float32 correction is not added
-            const bool bad = status[c] == TG_NOT_CONVERGED && (hs[c].status == 4 || hs[c].status == 5);
-            hv[c] = (status[c] == TG_NOT_CONVERGED && !bad) ? nr[c] : 0.0;
+            bad[c] = status[c] == TG_NOT_CONVERGED && (hs[c].status == 4 || hs[c].status == 5);
+            hv[c] = (status[c] == TG_NOT_CONVERGED && !bad[c]) ? nr[c] : 0.0;
+            nr_before[c] = nr[c];
         }
         TG_CHECK_CUDA(cudaMemcpyAsync(P.scale, hv.data(), BR * 8, cudaMemcpyHostToDevice, s));
         TG_PROF(P_CONVERT, 12.0 * b->total, 2.0 * b->total,
                 k_mrb_add<R><<<dim3(gres, count), kThreads, 0, s>>>(X, A.e32.as<float>(), P));
         TG_LAUNCH_CHECK();
         TG_CHECK(residual());
+        // a correction that raised the float64 residual kIrGrowth-fold is undone (x -= ||r|| e)
+        bool undo = false;
+        for (size_t c = 0; c < BR; ++c) {
+            const bool worse = status[c] == TG_NOT_CONVERGED && !bad[c] && !(nr[c] <= kIrGrowth * nr_before[c]);
+            hv[c] = worse ? -nr_before[c] : 0.0;
+            if (worse || bad[c]) {
+                capc[c] = std::max<int64_t>(1, std::min<int64_t>(capc[c], hs[c].mvps) / 2);
+                undo |= worse;
+            }
+        }
+        if (undo) {
+            TG_CHECK_CUDA(cudaMemcpyAsync(P.scale, hv.data(), BR * 8, cudaMemcpyHostToDevice, s));
+            TG_PROF(P_CONVERT, 12.0 * b->total, 2.0 * b->total,
+                    k_mrb_add<R><<<dim3(gres, count), kThreads, 0, s>>>(X, A.e32.as<float>(), P));
+            TG_LAUNCH_CHECK();
+            TG_CHECK(residual());
+        }
         bool stuck = true;
         for (size_t c = 0; c < BR; ++c) {
             if (status[c] != TG_NOT_CONVERGED) continue;
             mv[c] += hs[c].mvps;
             if (hs[c].mvps > 0) stuck = false;
-            if (!std::isfinite(nr[c]) || hs[c].status == 4 || hs[c].status == 5) status[c] = TG_NAN;
+            if (!std::isfinite(nr[c])) status[c] = TG_NAN;
             else if (nr[c] <= cfg.rtol * nb[c]) status[c] = TG_OK;
             else if (mv[c] >= cfg.max_mvps) status[c] = TG_NOT_CONVERGED + 100;   // out of budget
+            else if (capc[c] < 4) status[c] = TG_BREAKDOWN;      // no float32 cycle lowers its residual
         }
         if (stuck) break;
     }
+    // columns no float32 cycle can advance finish with float64 BiCGStab(-Proj) cycles on the
+    // instance's own operator and basis, as the single-system float32 form does: the column is
+    // gathered from the point-major block, solved, and scattered back
+    std::vector<int> fp64_cyc(count, 0);
+    for (size_t c = 0; c < BR; ++c) {
+        if (status[c] != TG_BREAKDOWN && status[c] != TG_NAN) continue;
+        const int i = (int)(c / R), q = (int)(c % R);
+        tg_op *op = b->ops[i];
+        const tg_defl *df = b->defls.empty() ? nullptr : b->defls[i];
+        const size_t n = (size_t)op->n;
+        TG_CHECK(A.colb.ensure(n * 8));
+        TG_CHECK(A.colx.ensure(n * 8));
+        double *cb = A.colb.as<double>(), *cx = A.colx.as<double>();
+        const size_t off = (size_t)b->off[i] + q;
+        TG_CHECK_CUDA(cudaMemcpy2DAsync(cb, 8, Bv + off, R * 8, 8, n, cudaMemcpyDeviceToDevice, s));
+        TG_CHECK_CUDA(cudaMemcpy2DAsync(cx, 8, X + off, R * 8, 8, n, cudaMemcpyDeviceToDevice, s));
+        SolveCfg c64 = cfg;
+        c64.ncyc = 0;
+        c64.max_mvps = std::max<int64_t>(1, cfg.max_mvps - mv[c]);
+        if (c64.restart_mvps <= 0) c64.restart_mvps = 1000;
+        tg_stats s64{};
+        s64.history = nullptr;
+        const int rc64 = solve_bicg64<double>(op, 0, df, cb, cx, c64, &s64, s);
+        if (rc64 == TG_BAD_ARG || rc64 == TG_OOM || rc64 == TG_CUDA_ERROR) return rc64;
+        TG_CHECK_CUDA(cudaMemcpy2DAsync(X + off, R * 8, cx, 8, 8, n, cudaMemcpyDeviceToDevice, s));
+        mv[c] += s64.mvps;
+        nr[c] = s64.relres * nb[c];
+        status[c] = rc64;
+        fp64_cyc[i] += s64.cycles;
+    }
+    TG_CHECK_CUDA(cudaStreamSynchronize(s));
     int worst = TG_OK;
     for (size_t c = 0; c < BR; ++c) {
         if (status[c] == TG_NOT_CONVERGED + 100) status[c] = TG_NOT_CONVERGED;
@@ -2621,6 +2745,7 @@ static int batch_solve_all(tg_batch *b, const double *Bv, double *X, const Solve
             o.relres = nb[c] > 0 ? nr[c] / nb[c] : 0.0;
             o.status = status[c];
             o.vops = mv[c] * 7;
+            o.fp64_cycles = fp64_cyc[c / R];
         }
         if (status[c] != TG_OK && worst == TG_OK) worst = status[c];
     }

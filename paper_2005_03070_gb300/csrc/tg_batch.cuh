@@ -41,6 +41,7 @@ struct MrBatchPtrs {
     double *norms;              // [B][2 R]
     double *cvec, *dvec;        // [B][32 R]
     int cap;                    // product cap of the cycle (all instances)
+    const double *capv = nullptr;   // [B][R] per-column product caps (nullptr: cap for all)
 };
 
 template <int R>
@@ -113,7 +114,8 @@ __global__ void __launch_bounds__(kThreads) k_mrb_bi_init(const float *__restric
                 BiState<double> &s = st[q];
                 const double rho = tot[q];
                 s.rho = rho; s.rr = rho; s.ss = 0.0; s.target2 = t2[q]; s.div2 = 1e16 * rho;   // 1e8-fold growth
-                s.mvps = 0; s.cap = P.cap; s.iters = 0; s.half = 0; s.pending = 0;
+                s.mvps = 0; s.cap = P.capv ? (int)P.capv[(size_t)b * R + q] : P.cap;
+                s.iters = 0; s.half = 0; s.pending = 0;
                 s.alpha = s.omega = s.beta = s.rho_next = 1.0;
                 if (t2[q] < 0.0) s.status = 1;                 // not in this cycle
                 else if (!isfinite(rho)) s.status = 4;

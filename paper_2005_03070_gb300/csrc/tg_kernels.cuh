@@ -344,6 +344,127 @@ __global__ void __launch_bounds__(kThreads) k_bi_x(T *__restrict__ x, T *__restr
     }
 }
 
+// ----------------------------------------------------------------------------- float32 streaming updates, 4 points per thread
+// The float32 BiCGStab updates touch only their own points: thread g takes the 4 consecutive
+// points 4g .. 4g + 3 as aligned float4, 16 bytes per request, so each thread keeps four
+// times the DRAM bytes of the one-point kernels in flight.  A partial last group runs the
+// one-point code.
+__device__ __forceinline__ float4 ld4(const float *__restrict__ p, int a) {
+    return *reinterpret_cast<const float4 *>(p + a);
+}
+
+// k_bi_s for float32 with 16-byte aligned vectors, 4 points per thread: s = r - alpha v, <s,s>.
+__global__ void __launch_bounds__(kThreads) k_bi_s_f4(const float *__restrict__ r, const float *__restrict__ v,
+                                                       float *__restrict__ s, int n, double *part,
+                                                       unsigned *ticket, BiState<double> *st) {
+    if (st->status != 0) return;
+    __shared__ double red[(kThreads / 32)];
+    __shared__ double tot[1];
+    const float malpha = -(float)st->alpha;
+    float acc[1] = {0.0f};
+    const int ng = n >> 2;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const float4 rv = ld4(r, 4 * g), vv = ld4(v, 4 * g);
+        const float4 sv = make_float4(fmaf(malpha, vv.x, rv.x), fmaf(malpha, vv.y, rv.y),
+                                      fmaf(malpha, vv.z, rv.z), fmaf(malpha, vv.w, rv.w));
+        *reinterpret_cast<float4 *>(s + 4 * g) = sv;
+        acc[0] = fmaf(sv.x, sv.x, acc[0]);
+        acc[0] = fmaf(sv.y, sv.y, acc[0]);
+        acc[0] = fmaf(sv.z, sv.z, acc[0]);
+        acc[0] = fmaf(sv.w, sv.w, acc[0]);
+    }
+    for (int i = 4 * ng + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float si = fmaf(malpha, v[i], r[i]);
+        s[i] = si;
+        acc[0] = fmaf(si, si, acc[0]);
+    }
+    block_reduce_store<float, double, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<double, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            const double ss = tot[0];
+            st->ss = ss;
+            if (!isfinite(ss)) st->status = 4;
+            else if (ss <= st->target2) { st->half = 1; st->pending = 1; }
+            else if (ss > st->div2) st->status = 5;
+            else if (st->mvps >= st->cap) { st->half = 1; st->pending = 3; }
+        }
+    }
+}
+
+// k_bi_x for float32 with 16-byte aligned vectors, 4 points per thread: x += alpha p + omega s,
+// r = s - omega t, p = r + beta (p - omega v), <r,r> (or the half step x += alpha p, r = s).
+__device__ __forceinline__ float4 f4_axpy(float a, const float4 &x, const float4 &y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__global__ void __launch_bounds__(kThreads) k_bi_x_f4(float *__restrict__ x, float *__restrict__ r,
+                                                       float *__restrict__ p, const float *__restrict__ s,
+                                                       const float *__restrict__ t, const float *__restrict__ v,
+                                                       int n, double *part, unsigned *ticket, BiState<double> *st) {
+    if (st->status != 0) return;
+    __shared__ double red[(kThreads / 32)];
+    __shared__ double tot[1];
+    const float alpha = (float)st->alpha;
+    const int ng = n >> 2;
+    const int g0 = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    if (st->half) {
+        for (int g = g0; g < ng; g += gs) {
+            *reinterpret_cast<float4 *>(x + 4 * g) = f4_axpy(alpha, ld4(p, 4 * g), ld4(x, 4 * g));
+            *reinterpret_cast<float4 *>(r + 4 * g) = ld4(s, 4 * g);
+        }
+        for (int i = 4 * ng + g0; i < n; i += gs) {
+            x[i] = fmaf(alpha, p[i], x[i]);
+            r[i] = s[i];
+        }
+        if (last_block(ticket)) {
+            if (threadIdx.x == 0) {
+                *ticket = 0u;
+                st->rr = st->ss;
+                st->status = st->pending;
+                st->iters += 1;
+            }
+        }
+        return;
+    }
+    const float omega = (float)st->omega, momega = -omega, beta = (float)st->beta;
+    float acc[1] = {0.0f};
+    for (int g = g0; g < ng; g += gs) {
+        const float4 sv = ld4(s, 4 * g), pv = ld4(p, 4 * g);
+        *reinterpret_cast<float4 *>(x + 4 * g) = f4_axpy(omega, sv, f4_axpy(alpha, pv, ld4(x, 4 * g)));
+        const float4 rv = f4_axpy(momega, ld4(t, 4 * g), sv);
+        *reinterpret_cast<float4 *>(r + 4 * g) = rv;
+        *reinterpret_cast<float4 *>(p + 4 * g) = f4_axpy(beta, f4_axpy(momega, ld4(v, 4 * g), pv), rv);
+        acc[0] = fmaf(rv.x, rv.x, acc[0]);
+        acc[0] = fmaf(rv.y, rv.y, acc[0]);
+        acc[0] = fmaf(rv.z, rv.z, acc[0]);
+        acc[0] = fmaf(rv.w, rv.w, acc[0]);
+    }
+    for (int i = 4 * ng + g0; i < n; i += gs) {
+        const float si = s[i], pi = p[i];
+        x[i] = fmaf(omega, si, fmaf(alpha, pi, x[i]));
+        const float ri = fmaf(momega, t[i], si);
+        r[i] = ri;
+        p[i] = fmaf(beta, fmaf(momega, v[i], pi), ri);
+        acc[0] = fmaf(ri, ri, acc[0]);
+    }
+    block_reduce_store<float, double, 1>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<double, 1>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            const double rr = tot[0];
+            st->rr = rr;
+            st->iters += 1;
+            st->rho = st->rho_next;
+            if (!isfinite(rr)) st->status = 4;
+            else if (rr <= st->target2) st->status = 1;
+            else if (rr > st->div2) st->status = 5;
+            else if (fabs(st->omega) < kTiny) st->status = 2;
+            else if (fabs(st->rho_next) < kTiny) st->status = 2;
+            else if (st->mvps >= st->cap) st->status = 3;
+        }
+    }
+}
+
 // ----------------------------------------------------------------------------- tall-skinny
 // Partial products of h = V^H w over row tiles: part[block][c] = sum over the block's rows
 // of conj(V[row, c]) w[row], c < ncol.  Columns come in groups of kGemvTCols (blockIdx.y);
@@ -868,5 +989,124 @@ __global__ void k_arnoldi_finish(const typename ST<T>::D *h1, const typename ST<
 
 
 
+
+// ----------------------------------------------------------------------------- float32 7-point stencil, plane marching
+// The constant-coefficient 3D stencil products of the float32 inner BiCGStab (v = A p with
+// <r_hat, v>; t = A s with <t,s>, <t,t>, <r_hat,s>, <r_hat,t>).  A block owns a 32 x 8 column
+// of points (warp w takes row y0 + w, lane l takes x0 + l) and marches through zlen
+// consecutive planes of it.  Each thread keeps its own values of p at planes k-1, k, k+1 (and
+// the next two planes, loaded ahead) in registers, so p and r_hat come from DRAM once per
+// point with the loads two planes ahead of their use; the x neighbours come from the
+// neighbouring lanes by shuffle (the block-edge lanes load one value), the y neighbours are
+// loads of the rows the neighbouring warps of the block fetched as their own (L1 hits inside
+// the block), issued one plane ahead.  No shared memory or barrier in the loop.  Summation
+// order per point is that of the one-point float32 stencil (centre, -x, +x, -y, +y, -z, +z);
+// terms outside the grid are exact zeros.
+constexpr int kPlX = 32, kPlY = 8;
+
+// tiles in x and y of the plane-marching stencil for an N^3 grid
+__host__ __device__ __forceinline__ int plane_tiles_xy(int N) { return ((N + kPlX - 1) / kPlX) * ((N + kPlY - 1) / kPlY); }
+
+// MODE 0: out = A p, <r_hat, out> -> alpha;  MODE 1: out = A p (p = s), the four dots -> omega,
+// rho_next, beta (or the half-step exit), exactly as k_bi_v / k_bi_t.  Block b takes xy tile
+// b % tiles and planes (b / tiles) * zlen .. + zlen - 1.  Indices are 32-bit (n < 2^31).
+template <int MODE>
+__global__ void __launch_bounds__(256, 8) k_bi_plane(DevOp op, DevOp32 o, const float *__restrict__ p,
+                                                  const float *__restrict__ rh, float *__restrict__ out,
+                                                  double *part, unsigned *ticket, BiState<double> *st, int zlen) {
+    if (st->status != 0) return;
+    if (MODE == 1 && st->half) return;
+    constexpr int ND = MODE == 0 ? 1 : 4;
+    __shared__ double red[(256 / 32) * ND];
+    __shared__ double tot[ND];
+    const int N = op.N;
+    const unsigned NN = (unsigned)N * (unsigned)N;
+    const int ntx = (N + kPlX - 1) / kPlX, tiles = plane_tiles_xy(N);
+    const int b = blockIdx.x;
+    const int xy = b % tiles;
+    const int x0 = (xy % ntx) * kPlX, y0 = (xy / ntx) * kPlY, z0 = (b / tiles) * zlen;
+    const int z1 = min(z0 + zlen, N);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = x0 + lane, y = y0 + w;
+    const bool inside = x < N && y < N;
+    const bool hs = inside && y > 0, hn = inside && y < N - 1;
+    const bool hw = inside && lane == 0 && x > 0, he = inside && (lane == 31 || x == N - 1) && x < N - 1;
+    const unsigned col = inside ? (unsigned)y * (unsigned)N + (unsigned)x : 0u;   // offset within a plane
+    auto at = [&](int z) { return (unsigned)z * NN + col; };
+    // registers: planes k-1, k, k+1 of p; k+2 loaded ahead; r_hat of planes k, k+1; the y
+    // neighbours of plane k
+    float pm = (inside && z0 > 0) ? p[at(z0 - 1)] : 0.0f;
+    float pc = inside ? p[at(z0)] : 0.0f;
+    float pn = (inside && z0 + 1 < N) ? p[at(z0 + 1)] : 0.0f;
+    float pnn = (inside && z0 + 2 < N) ? p[at(z0 + 2)] : 0.0f;
+    float rc = inside ? rh[at(z0)] : 0.0f;
+    float rn = (inside && z0 + 1 < z1) ? rh[at(z0 + 1)] : 0.0f;
+    float ys = hs ? p[at(z0) - N] : 0.0f, yn = hn ? p[at(z0) + N] : 0.0f;
+    float acc[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc[d] = 0.0f;
+    for (int k = z0; k < z1; ++k) {
+        // loads for later planes first (independent of this plane's arithmetic)
+        const float pload = (inside && k + 3 < N) ? p[at(k + 3)] : 0.0f;
+        const float rload = (inside && k + 2 < z1) ? rh[at(k + 2)] : 0.0f;
+        const bool nxt = k + 1 < z1;
+        const float ysn = (hs && nxt) ? p[at(k + 1) - N] : 0.0f;
+        const float ynn = (hn && nxt) ? p[at(k + 1) + N] : 0.0f;
+        // x neighbours: the neighbouring lanes' centre values (0 outside the grid)
+        float xw = __shfl_up_sync(0xffffffffu, pc, 1);
+        float xe = __shfl_down_sync(0xffffffffu, pc, 1);
+        if (lane == 0) xw = hw ? p[at(k) - 1] : 0.0f;
+        if (he && lane == 31) xe = p[at(k) + 1];
+        if (x == N - 1) xe = 0.0f;
+        float v = o.c0 * pc;
+        v = fmaf(o.cxm, xw, v);
+        v = fmaf(o.cxp, xe, v);
+        v = fmaf(o.cym, ys, v);
+        v = fmaf(o.cyp, yn, v);
+        v = fmaf(o.czm, pm, v);
+        v = fmaf(o.czp, pn, v);
+        if (inside) {
+            out[at(k)] = v;
+            if (MODE == 0) {
+                acc[0] = fmaf(rc, v, acc[0]);
+            } else {
+                acc[0] = fmaf(v, pc, acc[0]);
+                acc[ND > 1 ? 1 : 0] = fmaf(v, v, acc[ND > 1 ? 1 : 0]);
+                acc[ND > 2 ? 2 : 0] = fmaf(rc, pc, acc[ND > 2 ? 2 : 0]);
+                acc[ND > 3 ? 3 : 0] = fmaf(rc, v, acc[ND > 3 ? 3 : 0]);
+            }
+        }
+        pm = pc; pc = pn; pn = pnn; pnn = pload;
+        rc = rn; rn = rload;
+        ys = ysn; yn = ynn;
+    }
+    block_reduce_store<float, double, ND>(acc, part, red);
+    if (last_block(ticket)) {
+        final_sum<double, ND>(part, tot, ticket);
+        if (threadIdx.x == 0) {
+            st->mvps += 1;
+            if (MODE == 0) {
+                const double sigma = tot[0];
+                if (!isfinite(sigma)) st->status = 4;
+                else if (fabs(sigma) < kTiny) st->status = 2;
+                else st->alpha = st->rho / sigma;
+            } else {
+                const double tt = tot[ND > 1 ? 1 : 0];
+                if (!isfinite(tt) || !isfinite(tot[0])) {
+                    st->status = 4;
+                } else if (tt < kTiny) {
+                    st->half = 1;
+                    st->pending = 2;
+                } else {
+                    const double omega = tot[0] / tt;
+                    st->omega = omega;
+                    const double rn2 = tot[ND > 2 ? 2 : 0] - omega * tot[ND > 3 ? 3 : 0];
+                    st->rho_next = rn2;
+                    if (fabs(omega) >= kTiny) st->beta = (rn2 / st->rho) * (st->alpha / omega);
+                }
+            }
+        }
+    }
+}
 
 }  // namespace tg

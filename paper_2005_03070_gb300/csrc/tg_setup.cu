@@ -5,7 +5,7 @@
 //  - lattice block-transport weights P[x, X] = (1/4) conj(W(x)) and the Galerkin coarse
 //    operator P^H A P as a 9-point stencil (Section 5.4's lattice problem; the paper's
 //    Schwinger-model coarse operator is not specified, this build uses 2^4 blocking);
-//  - bilinear / trilinear prolongation with a fixed summation order, full-weighting
+//  - bilinear / trilinear and cubic prolongation with a fixed summation order, full-weighting
 //    restriction, lattice prolongation / restriction (Section 3, phase 1: moving the
 //    coarse eigenvectors and solution to the fine grid);
 //  - the kappa-gradient contraction of the adjoint form and precision conversions.
@@ -197,6 +197,111 @@ __global__ void k_prolong3d(const double *__restrict__ uc, int Nc, double *__res
     }
 }
 
+// ----------------------------------------------------------------------------- cubic prolongation
+// Fourth-order interpolation in place of the paper's splines (Section 3, phase 1): a fine
+// point halfway between coarse nodes a and a + 1 takes (-1, 9, 9, -1)/16 of nodes a-1..a+2,
+// a fine point on a coarse node copies it; beyond the Dirichlet boundary the function is
+// continued oddly (nodes 0 and Nc+1 are zero, node -1 is -u(1), node Nc+2 is -u(Nc)).
+// Tensor product over x, then y, then z; each sum ((w0 v0 + w1 v1) + w2 v2) + w3 v3 uses
+// separately rounded products and sums (no contraction), so the result is reproducible.
+struct CubAxis {
+    int cnt;         // 1 (on a coarse node) or 4
+    int node[4];     // coarse nodes, 1..Nc after folding (0 when the term is a boundary zero)
+    double sgn[4];   // +1, or -1 for a reflected node
+};
+
+__device__ __forceinline__ CubAxis cub_axis(int i, int Nc) {
+    CubAxis c;
+    if (!(i & 1)) {
+        c.cnt = 1;
+        c.node[0] = i >> 1;
+        c.sgn[0] = 1.0;
+        return c;
+    }
+    c.cnt = 4;
+    const int a = (i - 1) >> 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int nd = a - 1 + q;
+        if (nd == -1) { c.node[q] = 1; c.sgn[q] = -1.0; }
+        else if (nd == Nc + 2) { c.node[q] = Nc; c.sgn[q] = -1.0; }
+        else if (nd < 1 || nd > Nc) { c.node[q] = 0; c.sgn[q] = 0.0; }
+        else { c.node[q] = nd; c.sgn[q] = 1.0; }
+    }
+    return c;
+}
+
+__device__ __forceinline__ double cub_sum(const double (&v)[4]) {
+    constexpr double w0 = -0.0625, w1 = 0.5625;
+    return __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(w0, v[0]), __dmul_rn(w1, v[1])), __dmul_rn(w1, v[2])),
+                     __dmul_rn(w0, v[3]));
+}
+
+// value of a reflected term: sgn * u (exact), or the boundary zero
+__device__ __forceinline__ double cub_term(double sgn, double u) { return sgn == 0.0 ? 0.0 : (sgn < 0.0 ? -u : u); }
+
+__global__ void k_prolong2d_cubic(const double *__restrict__ uc, int Nc, double *__restrict__ uf) {
+    const int N = 2 * Nc + 1;
+    const int n = N * N;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int i = idx % N + 1, j = idx / N + 1;
+        const CubAxis ax = cub_axis(i, Nc), ay = cub_axis(j, Nc);
+        double t[4];
+        for (int b = 0; b < ay.cnt; ++b) {
+            // the x-interpolated row ay.node[b] (a zero row at the boundary)
+            double xv;
+            if (ay.sgn[b] == 0.0) {
+                xv = 0.0;
+            } else {
+                const double *row = uc + (size_t)(ay.node[b] - 1) * Nc;
+                if (ax.cnt == 1) {
+                    xv = row[ax.node[0] - 1];
+                } else {
+                    double v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v[q] = ax.sgn[q] == 0.0 ? 0.0 : cub_term(ax.sgn[q], row[ax.node[q] - 1]);
+                    xv = cub_sum(v);
+                }
+            }
+            t[b] = cub_term(ay.sgn[b], xv);
+        }
+        uf[idx] = ay.cnt == 1 ? t[0] : cub_sum(t);
+    }
+}
+
+__global__ void k_prolong3d_cubic(const double *__restrict__ uc, int Nc, double *__restrict__ uf) {
+    const int N = 2 * Nc + 1;
+    const int64_t n = (int64_t)N * N * N;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % N) + 1, j = (int)((idx / N) % N) + 1, k = (int)(idx / ((int64_t)N * N)) + 1;
+        const CubAxis ax = cub_axis(i, Nc), ay = cub_axis(j, Nc), az = cub_axis(k, Nc);
+        double tz[4];
+        for (int c = 0; c < az.cnt; ++c) {
+            double ty[4];
+            for (int b = 0; b < ay.cnt; ++b) {
+                double xv;
+                if (az.sgn[c] == 0.0 || ay.sgn[b] == 0.0) {
+                    xv = 0.0;
+                } else {
+                    const double *row = uc + (size_t)Nc * ((ay.node[b] - 1) + (size_t)Nc * (az.node[c] - 1));
+                    if (ax.cnt == 1) {
+                        xv = row[ax.node[0] - 1];
+                    } else {
+                        double v[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[q] = ax.sgn[q] == 0.0 ? 0.0 : cub_term(ax.sgn[q], row[ax.node[q] - 1]);
+                        xv = cub_sum(v);
+                    }
+                }
+                ty[b] = cub_term(ay.sgn[b], xv);
+            }
+            const double yv = ay.cnt == 1 ? ty[0] : cub_sum(ty);
+            tz[c] = cub_term(az.sgn[c], yv);
+        }
+        uf[idx] = az.cnt == 1 ? tz[0] : cub_sum(tz);
+    }
+}
+
 // Full weighting: uc(I, J) = (1/4) sum_f P[f, (I,J)] uf(f) (weights 1, 1/2, 1/4).
 __global__ void k_restrict2d(const double *__restrict__ uf, int N, double *__restrict__ uc) {
     const int Nc = (N - 1) / 2;
@@ -310,6 +415,8 @@ TG_L(lattice_coarse, (int grid, cudaStream_t s, const cplx *links, const cplx *p
      (links, pw, L, mdiag, cst))
 TG_L(prolong2d, (int grid, cudaStream_t s, const double *uc, int Nc, double *uf), (uc, Nc, uf))
 TG_L(prolong3d, (int grid, cudaStream_t s, const double *uc, int Nc, double *uf), (uc, Nc, uf))
+TG_L(prolong2d_cubic, (int grid, cudaStream_t s, const double *uc, int Nc, double *uf), (uc, Nc, uf))
+TG_L(prolong3d_cubic, (int grid, cudaStream_t s, const double *uc, int Nc, double *uf), (uc, Nc, uf))
 TG_L(restrict2d, (int grid, cudaStream_t s, const double *uf, int N, double *uc), (uf, N, uc))
 TG_L(restrict3d, (int grid, cudaStream_t s, const double *uf, int N, double *uc), (uf, N, uc))
 TG_L(prolong_lattice, (int grid, cudaStream_t s, const cplx *uc, const cplx *pw, int L, cplx *uf), (uc, pw, L, uf))

@@ -15,6 +15,8 @@ void launch_lattice_weights(int grid, cudaStream_t s, const cplx *links, int L, 
 void launch_lattice_coarse(int grid, cudaStream_t s, const cplx *links, const cplx *pw, int L, double mdiag, cplx *cst);
 void launch_prolong2d(int grid, cudaStream_t s, const double *uc, int Nc, double *uf);
 void launch_prolong3d(int grid, cudaStream_t s, const double *uc, int Nc, double *uf);
+void launch_prolong2d_cubic(int grid, cudaStream_t s, const double *uc, int Nc, double *uf);
+void launch_prolong3d_cubic(int grid, cudaStream_t s, const double *uc, int Nc, double *uf);
 void launch_restrict2d(int grid, cudaStream_t s, const double *uf, int N, double *uc);
 void launch_restrict3d(int grid, cudaStream_t s, const double *uf, int N, double *uc);
 void launch_prolong_lattice(int grid, cudaStream_t s, const cplx *uc, const cplx *pw, int L, cplx *uf);

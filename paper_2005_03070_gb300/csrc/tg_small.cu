@@ -1028,18 +1028,27 @@ __device__ __forceinline__ void gmresdr_restart_body(const GdrArgs<T> &a) {
     __shared__ int kk_s;
     int *ord = a.order;
     __shared__ double mod_s[kMaxM];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) mod_s[i] = hypot(wr[i], wi[i]);
+    __shared__ double wr_s[kMaxM], wi_s[kMaxM];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        mod_s[i] = hypot(wr[i], wi[i]);
+        wr_s[i] = wr[i];
+        wi_s[i] = wi[i];
+    }
+    __syncthreads();
+    // stable rank sort, one thread per value: the rank of i is the number of values before it
+    // in the order plus the equal values of smaller index (the order a stable sort gives)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        int r = 0;
+        for (int j = 0; j < m; ++j) {
+            if (j == i) continue;
+            const bool jl = ritz_less_m(mod_s[j], wr_s[j], wi_s[j], mod_s[i], wr_s[i], wi_s[i]);
+            const bool il = ritz_less_m(mod_s[i], wr_s[i], wi_s[i], mod_s[j], wr_s[j], wi_s[j]);
+            if (jl || (j < i && !il)) ++r;
+        }
+        ord[r] = i;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < m; ++i) ord[i] = i;
-        for (int i = 1; i < m; ++i) {
-            int v = ord[i], j = i - 1;
-            while (j >= 0 && ritz_less_m(mod_s[v], wr[v], wi[v], mod_s[ord[j]], wr[ord[j]], wi[ord[j]])) {
-                ord[j + 1] = ord[j];
-                --j;
-            }
-            ord[j + 1] = v;
-        }
         int kk = a.k;
         if (sizeof(T) == sizeof(double) && kk < m) {
             int t = ord[kk - 1];
@@ -1047,10 +1056,10 @@ __device__ __forceinline__ void gmresdr_restart_body(const GdrArgs<T> &a) {
         }
         kk_s = kk;
         a.info->status = st;
-        for (int i = 0; i < m; ++i) {
-            a.theta[2 * i] = wr[ord[i]];
-            a.theta[2 * i + 1] = wi[ord[i]];
-        }
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        a.theta[2 * i] = wr_s[ord[i]];
+        a.theta[2 * i + 1] = wi_s[ord[i]];
     }
     __syncthreads();
     const int kk = kk_s;
@@ -1074,12 +1083,16 @@ __device__ __forceinline__ void gmresdr_restart_body(const GdrArgs<T> &a) {
         const int i = e % m, q = e / m;
         const cplx *y = Y + (size_t)q * m;
         cplx s = {0.0, 0.0};
-        for (int l = 0; l < m; ++l) {
-            T zl = Z[i + (size_t)l * m];
-            cplx zc;
-            if constexpr (sizeof(T) == sizeof(double)) zc = mkc(*reinterpret_cast<const double *>(&zl), 0.0);
-            else zc = *reinterpret_cast<const cplx *>(&zl);
-            s = s + zc * y[l];
+        if constexpr (sizeof(T) == sizeof(double)) {
+            // real Schur vectors: two real products per term
+            const double *Zd = reinterpret_cast<const double *>(Z);
+            for (int l = 0; l < m; ++l) {
+                const double zl = Zd[i + (size_t)l * m];
+                s.re = fma(zl, y[l].re, s.re);
+                s.im = fma(zl, y[l].im, s.im);
+            }
+        } else {
+            for (int l = 0; l < m; ++l) s = s + *reinterpret_cast<const cplx *>(&Z[i + (size_t)l * m]) * y[l];
         }
         G[i + (size_t)q * m] = s;
     }

@@ -29,10 +29,11 @@ KIND = {"cd2d": TG_CD2D, "cd3d": TG_CD3D, "u1_4d": TG_U1_4D, "vark2d": TG_VARK2D
 METHOD = {"bicgstab": TG_BICGSTAB, "gmres": TG_GMRES}
 PROJ = {"minres": TG_PROJ_MINRES, "galerkin": TG_PROJ_GALERKIN}
 PREC = {"f64": TG_F64, "f32_ir": TG_F32_IR}
+INTERP = {"linear": 0, "cubic": 1}
 
 EXPORTS = [
     "tg_status_string", "tg_last_error", "tg_setup_operator", "tg_destroy_op", "tg_op_size", "tg_apply",
-    "tg_prolong", "tg_restrict", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
+    "tg_prolong", "tg_restrict", "tg_op_set_interp", "tg_coarse_gmresdr", "tg_defl_from_basis", "tg_destroy_defl",
     "tg_defl_copy", "tg_project", "tg_solve_proj", "tg_solve_idr", "tg_improve_defl", "tg_adjoint_solve",
     "tg_kappa_gradient",
     "tg_harmonic_ritz", "tg_harmonic_ritz_noalloc", "tg_profile_enable", "tg_profile_read", "tg_launch_count",
@@ -82,6 +83,7 @@ def load() -> C.CDLL:
         "tg_apply": (i32, [vp, i32, i32, i32, vp, vp, vp]),
         "tg_prolong": (i32, [vp, vp, vp, i32, vp]),
         "tg_restrict": (i32, [vp, vp, vp, i32, vp]),
+        "tg_op_set_interp": (i32, [vp, i32]),
         "tg_coarse_gmresdr": (i32, [vp, i32, vp, i32, i32, i32, dbl, dbl, i32, vp, C.POINTER(vp), i32, i32,
                                     C.POINTER(TgStats), vp]),
         "tg_defl_from_basis": (i32, [vp, i32, vp, i32, i32, i32, C.POINTER(vp), vp]),
@@ -140,9 +142,11 @@ class Operator:
     kind: "cd2d" | "cd3d" | "vark2d" | "exp2d" | "u1_4d"; N: points per axis (odd) or lattice L;
     beta: convection speeds (exp2d: (beta_x, beta_y, gamma) of -exp(gamma x y) Lap u + beta . grad u);
     kappa: (N+2)^2 float64 CUDA tensor (vark2d); links: (4, L^4) complex128 CUDA tensor and mass
-    (u1_4d); mass on the grid kinds: the reaction coefficient c of + c u (Helmholtz: -k^2)."""
+    (u1_4d); mass on the grid kinds: the reaction coefficient c of + c u (Helmholtz: -k^2);
+    interp: "linear" (bilinear / trilinear) or "cubic" (fourth order, the stand-in for the
+    paper's splines) for every prolongation of this operator (tg_op_set_interp)."""
 
-    def __init__(self, kind, N, beta=(0.0,), kappa=None, links=None, mass=None, stream=None):
+    def __init__(self, kind, N, beta=(0.0,), kappa=None, links=None, mass=None, interp="linear", stream=None):
         lib = load()
         self.kind = KIND[kind] if isinstance(kind, str) else int(kind)
         self.N = int(N)
@@ -155,6 +159,9 @@ class Operator:
                                    _ptr(coeffs), 2, _stream(stream))
         _check(st, "tg_setup_operator")
         self._h = h
+        if interp != "linear":
+            _check(lib.tg_op_set_interp(h, INTERP[interp]), "tg_op_set_interp")
+        self.interp = interp
         self.n = lib.tg_op_size(h, TG_FINE)
         self.nc = lib.tg_op_size(h, TG_COARSE)
         self.complex = self.kind == TG_U1_4D

@@ -76,3 +76,31 @@ def test_batch_per_instance_fp64_path(tg):
             assert st == tg.TG_OK
             xs = exact_solution(OOp(CD2D, N, (betas[i],)), B[q])
             assert np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs) <= 1e-6
+
+
+def test_batch_float64_fallback_on_a_poor_basis(tg):
+    """With the coarse phase cut off early (GMRES-DR(40,20), 100 cycles: as few as 5 of the 20
+    pairs converged) some float32 cycles raise the float64 residual.  Such a correction is
+    undone and the column's cycle cap halved; a column no float32 cycle can advance
+    finishes with float64 BiCGStab-Proj cycles on its instance's operator and basis.  Every
+    column must still reach rtol (recomputed by the oracle's operator), and the fallback
+    must have run on this case (fp64_cycles > 0)."""
+    Ns, betas = gi.batch_instances(16, seed=0)
+    batch = tg.Batch(Ns, betas)
+    host = np.empty(batch.total)
+    for i, N in enumerate(Ns):
+        o, n = batch.offsets[i], batch.sizes[i]
+        host[o:o + n * 8] = np.ascontiguousarray(gi.rhs(n, seed=i, nrhs=8).T).reshape(-1)
+    rhs = torch.from_numpy(host).cuda()
+    batch.setup(rhs, m=40, k=20, nev=20, rtolev=1e-2, rtol=1e-8, max_cycles=100, threads=16)
+    x = torch.zeros_like(rhs)
+    status, stats = batch.solve(rhs, x, rtol=1e-8, ncyc=20, restart_mvps=0, threads=16)
+    assert status == tg.TG_OK, [s["status"] for s in stats]
+    assert sum(s["fp64_cycles"] for s in stats) > 0
+    xh = x.cpu().numpy()
+    for i, N in enumerate(Ns):
+        op = OOp(CD2D, N, (betas[i],))
+        o, n = batch.offsets[i], batch.sizes[i]
+        B, X = host[o:o + n * 8].reshape(n, 8), xh[o:o + n * 8].reshape(n, 8)
+        for q in range(8):
+            assert np.linalg.norm(B[:, q] - op.apply(X[:, q])) / np.linalg.norm(B[:, q]) <= 1e-8

@@ -126,6 +126,33 @@ def test_prolongation_bit_exact(tg, kind, N):
     assert rel(r, transfer.restrict(uf, N, dim)) <= 1e-14
 
 
+@pytest.mark.parametrize("kind,N", [("cd2d", 127), ("cd2d", 7), ("cd2d", 3), ("cd3d", 31), ("cd3d", 7), ("cd3d", 3)])
+def test_cubic_prolongation_bit_exact(tg, kind, N):
+    """The cubic interpolation (stand-in for the paper's splines) against the oracle, bit for
+    bit: same fixed summation order; N = 3 (Nc = 1) has every stencil folded at the boundary."""
+    dim = 2 if kind == "cd2d" else 3
+    top = tg.Operator(kind, N, (1.0,) if dim == 2 else (2.0, 1.0, 0.5), interp="cubic")
+    Nc = (N - 1) // 2
+    rng = np.random.default_rng(17)
+    uc = rng.standard_normal((3, Nc ** dim))
+    f = host(top.prolong(cu(uc.reshape(-1)))).reshape(3, -1)
+    for c in range(3):
+        ref = transfer.prolong2d_cubic(uc[c], Nc) if dim == 2 else transfer.prolong3d_cubic(uc[c], Nc)
+        assert np.array_equal(f[c], ref)
+    # the restriction is unchanged (full weighting)
+    uf = rng.standard_normal(N ** dim)
+    assert rel(host(top.restrict(cu(uf))), transfer.restrict(uf, N, dim)) <= 1e-14
+
+
+def test_interp_setter_rejects_the_lattice_and_unknown_values(tg):
+    top, _ = make_pair(tg, "u1_4d", 8)
+    lib = tg.load()
+    assert lib.tg_op_set_interp(top.handle, 1) == tg.TG_BAD_ARG
+    g = tg.Operator("cd2d", 15, (1.0,))
+    assert lib.tg_op_set_interp(g.handle, 7) == tg.TG_BAD_ARG
+    assert lib.tg_op_set_interp(g.handle, 1) == 0
+
+
 @pytest.mark.parametrize("proj", ["minres", "galerkin"])
 @pytest.mark.parametrize("kind,N,beta", [("cd2d", 63, (1.0,)), ("cd3d", 15, (2.0, 1.0, 0.5))])
 def test_projection_parity(tg, proj, kind, N, beta):

@@ -92,10 +92,12 @@ def test_example1_two_grid(tg, method):
     assert rel(x, xs) <= 1e-6
 
 
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
 @pytest.mark.parametrize("method", ["gmres", "idr"])
-def test_helmholtz_two_grid(tg, method):
-    """-Lap u - 30^2 u on 63^2 (several negative eigenvalues): the indefinite case."""
-    top = tg.Operator("cd2d", 63, (0.0,), mass=-900.0)
+def test_helmholtz_two_grid(tg, method, interp):
+    """-Lap u - 30^2 u on 63^2 (several negative eigenvalues): the indefinite case, with the
+    moved vectors interpolated bilinearly and by the cubic stand-in for the paper's splines."""
+    top = tg.Operator("cd2d", 63, (0.0,), mass=-900.0, interp=interp)
     oop = OOp(CD2D, 63, (0.0,), mass=-900.0)
     b = gi.rhs(oop.n, 44)
     xs = twogrid.exact_solution(oop, b)
@@ -236,3 +238,22 @@ def test_arnoldi_e_improves_moved_vectors(tg):
     status, s2 = top.solve(bt, x, defl, rtol=1e-10, ncyc=20, restart_mvps=0)
     assert status == tg.TG_OK
     assert rel(host(x), twogrid.exact_solution(oop, b)) <= 1e-6
+
+
+def test_cubic_interpolation_moves_a_nearly_invariant_subspace(tg):
+    """The reason for the cubic reading: on the Helmholtz operator -Lap u - 60^2 u (127^2,
+    coarse 63^2) the coarse GMRES-DR basis moved by cubic interpolation spans a subspace much
+    closer to invariant under the fine operator than the bilinear move of the same coarse
+    basis: ||A Y - Y (Y^T Y)^-1 Y^T A Y||_F / ||A Y||_F, computed here by the oracle's operator."""
+    N, mass = 127, -3600.0
+    oop = OOp(CD2D, N, (0.0,), mass=mass)
+    b = gi.rhs(oop.n, 45)
+    gaps = {}
+    for interp in ("linear", "cubic"):
+        top = tg.Operator("cd2d", N, (0.0,), mass=mass, interp=interp)
+        _, defl, _, _ = top.coarse_gmresdr(cu(b), 60, 30, rtolev=1e-8, rtol=1e-10, max_cycles=300, want_xc=False)
+        Y = host(defl.copy(0)).reshape(defl.kk, oop.n).T
+        AY = np.stack([oop.apply(Y[:, j]) for j in range(Y.shape[1])], axis=1)
+        C = np.linalg.lstsq(Y, AY, rcond=None)[0]
+        gaps[interp] = np.linalg.norm(AY - Y @ C) / np.linalg.norm(AY)
+    assert gaps["cubic"] < 0.5 * gaps["linear"], gaps

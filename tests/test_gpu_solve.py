@@ -87,6 +87,23 @@ def test_cfg0_cycle_schedule_ncyc(tg):
     assert st["cycles"] <= 20
 
 
+@pytest.mark.parametrize("N", [33, 9, 65])
+def test_float32_plane_stencil_bicgstab_parity(tg, N):
+    """The float32 3D BiCGStab runs its stencil products through the plane-marching kernels
+    (32 x 8 point columns, 32-plane chunks).  N = 33 and 65 leave partial tiles along every
+    axis, N = 9 a single partial tile; 12 products against the oracle's float64 BiCGStab
+    from x0 = 0 agree to float32 accuracy (the iterates differ by float32 rounding only)."""
+    beta = (2.0, 1.0, 0.5)
+    top, oop = tg.Operator("cd3d", N, beta), OOp(CD3D, N, beta)
+    b = gi.rhs(oop.n, 41)
+    ref = krylov.bicgstab_proj(oop.apply, b, np.zeros(oop.n), None, rtol=1e-14, ncyc=0, restart_mvps=12,
+                               max_mvps=12)
+    xt = cu(np.zeros(oop.n))
+    st, stats = top.solve(cu(b), xt, rtol=1e-14, ncyc=0, restart_mvps=12, max_mvps=12, precision="f32_ir")
+    assert stats[0]["mvps"] == ref.mvps == 12
+    assert rel(host(xt), ref.x) <= 1e-5
+
+
 def test_cfg0_two_grid_fp32_ir(tg):
     N = 127
     top, oop = tg.Operator("cd2d", N, (1.0,)), OOp(CD2D, N, (1.0,))
