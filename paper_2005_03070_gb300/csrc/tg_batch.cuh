@@ -672,12 +672,34 @@ __global__ void __launch_bounds__(kThreads) k_gb_gemv_n_norm(GdrBatchPtrs P, int
     float *w = S.V + (size_t)wcol * S.ldv;
     const int n = S.nc;
     float acc[1] = {0.f};
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
-        float a = 0.f;
-        for (int c = 0; c < ncol; ++c) a = fmaf(hs[c], V[(size_t)c * S.ldv + row], a);
-        const float wv = w[row] - a;
-        w[row] = wv;
-        acc[0] = fmaf(wv, wv, acc[0]);
+    // thread g takes rows 4g .. 4g + 3 as float4 (ldv a multiple of 128, V 16-byte aligned);
+    // rows at and beyond n (the padding) are computed but neither stored nor summed
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; 4 * g < n; g += gridDim.x * blockDim.x) {
+        const int r = 4 * g;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (int c = 0; c < ncol; ++c) {
+            const float4 v = ld4(V + (size_t)c * S.ldv, r);
+            const float hc = hs[c];
+            a0 = fmaf(hc, v.x, a0);
+            a1 = fmaf(hc, v.y, a1);
+            a2 = fmaf(hc, v.z, a2);
+            a3 = fmaf(hc, v.w, a3);
+        }
+        const float4 wo = ld4(w, r);
+        const float4 wn = make_float4(wo.x - a0, wo.y - a1, wo.z - a2, wo.w - a3);
+        if (r + 4 <= n) {
+            *reinterpret_cast<float4 *>(w + r) = wn;
+            acc[0] = fmaf(wn.x, wn.x, acc[0]);
+            acc[0] = fmaf(wn.y, wn.y, acc[0]);
+            acc[0] = fmaf(wn.z, wn.z, acc[0]);
+            acc[0] = fmaf(wn.w, wn.w, acc[0]);
+        } else {
+            const float e[4] = {wn.x, wn.y, wn.z, wn.w};
+            for (int i = 0; i < n - r; ++i) {
+                w[r + i] = e[i];
+                acc[0] = fmaf(e[i], e[i], acc[0]);
+            }
+        }
     }
     double *slice = P.part + (size_t)b * gridDim.x * P.partw;
     {
