@@ -204,7 +204,7 @@ enum Slot {
     S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC, S_XBAK,
     S_IG, S_IU, S_IP, S_IPR, S_IPRI, S_IT, S_IINFO,
     S_AE_S, S_AE_W, S_AE_H, S_AE_WW, S_AE_HA, S_AE_Y, S_AE_U, S_AE_P, S_AE_Z, S_AE_TH, S_AE_WR, S_AE_WI,
-    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM,
+    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM, S_PADX, S_PADR,
     S_COUNT
 };
 
@@ -981,34 +981,55 @@ struct CycleOut {
 };
 
 // One BiCGStab cycle on A e = r, updating x and r in place (device-resident scalars).
+// A float32 cycle on a 3D constant-coefficient grid runs in the padded layout of
+// k_bi_pad (rows of pitch P, a multiple of 4 above N, zero padding): x and r are copied in
+// at the start and back at the end, and every vector of the cycle has length P N^2.
+// padded > 0: x and r are already in that layout (the cycle proper).
 template <class T>
 static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r, int n, double target2, int cap,
-                      CycleOut *out, cudaStream_t s) {
+                      CycleOut *out, cudaStream_t s, int padded = 0) {
     using D = typename ST<T>::D;
+    if constexpr (std::is_same<T, float>::value) {
+        if (A.kind == DK_CD3D && !padded) {
+            const size_t np = (size_t)pad_pitch(A.N) * A.N * A.N;
+            TG_CHECK(wsx(op, S_PADX, np * 4));
+            TG_CHECK(wsx(op, S_PADR, np * 4));
+            float *xp = wsp<float>(op, S_PADX), *rp = wsp<float>(op, S_PADR);
+            const int gpk = grid_for((int64_t)np, 8), gn = grid_for(n, 8);
+            TG_PROF(P_CONVERT, 8.0 * n, 0, k_pad3d<<<gpk, kThreads, 0, s>>>(x, xp, A.N));
+            TG_PROF(P_CONVERT, 8.0 * n, 0, k_pad3d<<<gpk, kThreads, 0, s>>>(r, rp, A.N));
+            TG_LAUNCH_CHECK();
+            TG_CHECK(bicg_cycle<float>(op, A, A32, xp, rp, (int)np, target2, cap, out, s, n));
+            TG_PROF(P_CONVERT, 8.0 * n, 0, k_unpad3d<<<gn, kThreads, 0, s>>>(xp, x, A.N));
+            TG_PROF(P_CONVERT, 8.0 * n, 0, k_unpad3d<<<gn, kThreads, 0, s>>>(rp, r, A.N));
+            TG_LAUNCH_CHECK();
+            return TG_OK;
+        }
+    }
+    const int nb = padded ? padded : n;      // grid points (byte and flop accounting)
     BiVecs<T> w;
     TG_CHECK(bicg_vecs<T>(op, n, &w));
     const int g = grid_for(n, 8);
-    // float32 constant-coefficient 3D grids: the plane-marching stencil kernels, each block
-    // marching zlen planes; zlen is chosen so that one wave of resident blocks (8 per SM)
-    // covers the grid
-    const bool use_plane = std::is_same<T, float>::value && A.kind == DK_CD3D;
+    // the padded float32 3D stencil kernels, each block marching zlen planes; zlen is chosen
+    // so that one wave of resident blocks (4 per SM) covers the grid
+    const bool use_plane = std::is_same<T, float>::value && padded > 0;
     int zlen_v = 0, zlen_t = 0, gp_v = 0, gp_t = 0;
     if (use_plane) {
-        const int tiles = plane_tiles_xy(A.N);
+        const int tiles = pad_tiles(A.N);
         auto pick_z = [&](int per_sm, int *zl, int *blocks) {
             const int nz = std::max(1, std::min(A.N, num_sms() * per_sm / tiles));
             *zl = (A.N + nz - 1) / nz;
             *blocks = tiles * ((A.N + *zl - 1) / *zl);
         };
-        pick_z(8, &zlen_v, &gp_v);
-        pick_z(8, &zlen_t, &gp_t);
+        pick_z(4, &zlen_v, &gp_v);
+        pick_z(4, &zlen_t, &gp_t);
     }
     const int gp = std::max(gp_v, gp_t);
     TG_CHECK(red_ready(op, (size_t)(g > gp ? g : gp) * 4 * sizeof(D), s));
     D *part = wsp<D>(op, S_PART);
     unsigned *tk = wsp<unsigned>(op, S_TICKET);
     BiState<D> *st = reinterpret_cast<BiState<D> *>(wsp<char>(op, S_SMALL) + SmallArea::bistate);
-    TG_PROF(P_BI_INIT, 3.0 * n * sizeof(T), 2.0 * n, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
+    TG_PROF(P_BI_INIT, 3.0 * nb * sizeof(T), 2.0 * nb, k_bi_init<T><<<g, kThreads, 0, s>>>(r, w.rh, w.p, n, target2, cap, part, tk, st));
     TG_LAUNCH_CHECK();
     // float32 streaming updates with 16-byte aligned vectors: 4 points per thread
     bool use_v4 = false;
@@ -1028,27 +1049,27 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
         for (int c = 0; c < chunk; ++c) {
             if (use_plane) {
                 if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_plane<0><<<gp_v, 256, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st, zlen_v));
+                    TG_PROF(P_BI_V, (3 * es + xbs) * nb, (fl + 2 * cf) * nb, k_bi_pad<0><<<gp_v, 256, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st, zlen_v));
             } else {
-                TG_PROF(P_BI_V, (3 * es + xbs) * n, (fl + 2 * cf) * n, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
+                TG_PROF(P_BI_V, (3 * es + xbs) * nb, (fl + 2 * cf) * nb, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
             }
             if (use_v4) {
                 if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s_f4<<<g4, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
+                    TG_PROF(P_BI_S, 3 * es * nb, 4 * cf * nb, k_bi_s_f4<<<g4, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
             } else {
-                TG_PROF(P_BI_S, 3 * es * n, 4 * cf * n, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
+                TG_PROF(P_BI_S, 3 * es * nb, 4 * cf * nb, k_bi_s<T><<<g, kThreads, 0, s>>>(r, w.v, w.s, n, part, tk, st));
             }
             if (use_plane) {
                 if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_plane<1><<<gp_t, 256, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st, zlen_t));
+                    TG_PROF(P_BI_T, (3 * es + xbs) * nb, (fl + 8 * cf) * nb, k_bi_pad<1><<<gp_t, 256, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st, zlen_t));
             } else {
-                TG_PROF(P_BI_T, (3 * es + xbs) * n, (fl + 8 * cf) * n, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
+                TG_PROF(P_BI_T, (3 * es + xbs) * nb, (fl + 8 * cf) * nb, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
             }
             if (use_v4) {
                 if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x_f4<<<g4, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
+                    TG_PROF(P_BI_X, 8 * es * nb, 12 * cf * nb, k_bi_x_f4<<<g4, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
             } else {
-                TG_PROF(P_BI_X, 8 * es * n, 12 * cf * n, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
+                TG_PROF(P_BI_X, 8 * es * nb, 12 * cf * nb, k_bi_x<T><<<g, kThreads, 0, s>>>(x, r, w.p, w.s, w.t, w.v, n, part, tk, st));
             }
         }
         TG_LAUNCH_CHECK();

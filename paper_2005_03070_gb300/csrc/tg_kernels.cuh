@@ -990,90 +990,127 @@ __global__ void k_arnoldi_finish(const typename ST<T>::D *h1, const typename ST<
 
 
 
-// ----------------------------------------------------------------------------- float32 7-point stencil, plane marching
-// The constant-coefficient 3D stencil products of the float32 inner BiCGStab (v = A p with
-// <r_hat, v>; t = A s with <t,s>, <t,t>, <r_hat,s>, <r_hat,t>).  A block owns a 32 x 8 column
-// of points (warp w takes row y0 + w, lane l takes x0 + l) and marches through zlen
-// consecutive planes of it.  Each thread keeps its own values of p at planes k-1, k, k+1 (and
-// the next two planes, loaded ahead) in registers, so p and r_hat come from DRAM once per
-// point with the loads two planes ahead of their use; the x neighbours come from the
-// neighbouring lanes by shuffle (the block-edge lanes load one value), the y neighbours are
-// loads of the rows the neighbouring warps of the block fetched as their own (L1 hits inside
-// the block), issued one plane ahead.  No shared memory or barrier in the loop.  Summation
-// order per point is that of the one-point float32 stencil (centre, -x, +x, -y, +y, -z, +z);
-// terms outside the grid are exact zeros.
-constexpr int kPlX = 32, kPlY = 8;
+// ----------------------------------------------------------------------------- float32 3D stencil, padded rows
+// Inside a float32 BiCGStab cycle on a 3D constant-coefficient grid the cycle's vectors are
+// kept in a padded layout: element (x, y, z) at z P N + y P + x with the row pitch P a multiple
+// of 4 and greater than N, and x = N .. P-1 a zero column (the Dirichlet neighbour in x).  Rows
+// are then 16-byte aligned, so the stencil moves every operand as float4: a thread takes 4
+// consecutive points of a row, marches planes (its p at planes k-1..k+2 in registers, loaded
+// two planes ahead), takes its x neighbours from the neighbouring lanes' float4 (the block-edge
+// lanes load one value) and its y neighbours as float4 loads issued one plane ahead.  Outputs
+// at padding points are written as zeros, so every vector of the cycle keeps zero padding
+// and the cycle's dots need no mask.  Summation order per point is that of the one-point
+// float32 stencil (centre, -x, +x, -y, +y, -z, +z).
 
-// tiles in x and y of the plane-marching stencil for an N^3 grid
-__host__ __device__ __forceinline__ int plane_tiles_xy(int N) { return ((N + kPlX - 1) / kPlX) * ((N + kPlY - 1) / kPlY); }
+__host__ __device__ __forceinline__ int pad_pitch(int N) { return (N + 1 + 3) / 4 * 4; }
+__host__ __device__ __forceinline__ int pad_tiles(int N) {
+    const int G = pad_pitch(N) / 4;
+    return ((G + 31) / 32) * ((N + 7) / 8);
+}
+
+// in (N^3, x fastest) -> outp (padded, zero padding)
+__global__ void k_pad3d(const float *__restrict__ in, float *__restrict__ outp, int N) {
+    const unsigned P = (unsigned)pad_pitch(N), n = P * (unsigned)N * (unsigned)N;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned x = i % P, row = i / P;
+        outp[i] = x < (unsigned)N ? in[row * (unsigned)N + x] : 0.0f;
+    }
+}
+
+// inp (padded) -> out (N^3)
+__global__ void k_unpad3d(const float *__restrict__ inp, float *__restrict__ out, int N) {
+    const unsigned P = (unsigned)pad_pitch(N), n = (unsigned)N * (unsigned)N * (unsigned)N;
+    for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const unsigned x = j % (unsigned)N, row = j / (unsigned)N;
+        out[j] = inp[row * P + x];
+    }
+}
+
+__device__ __forceinline__ float4 ld4c(bool ok, const float *__restrict__ p, unsigned i) {
+    return ok ? *reinterpret_cast<const float4 *>(p + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float st7(const DevOp32 &o, float c, float w, float e, float s, float n, float d, float u) {
+    float v = o.c0 * c;
+    v = fmaf(o.cxm, w, v);
+    v = fmaf(o.cxp, e, v);
+    v = fmaf(o.cym, s, v);
+    v = fmaf(o.cyp, n, v);
+    v = fmaf(o.czm, d, v);
+    return fmaf(o.czp, u, v);
+}
 
 // MODE 0: out = A p, <r_hat, out> -> alpha;  MODE 1: out = A p (p = s), the four dots -> omega,
-// rho_next, beta (or the half-step exit), exactly as k_bi_v / k_bi_t.  Block b takes xy tile
-// b % tiles and planes (b / tiles) * zlen .. + zlen - 1.  Indices are 32-bit (n < 2^31).
+// rho_next, beta (or the half-step exit), as k_bi_v / k_bi_t.  Block b takes xy tile b % tiles
+// (32 float4 groups x 8 rows) and planes (b / tiles) * zlen .. + zlen - 1.
 template <int MODE>
-__global__ void __launch_bounds__(256, 8) k_bi_plane(DevOp op, DevOp32 o, const float *__restrict__ p,
-                                                  const float *__restrict__ rh, float *__restrict__ out,
-                                                  double *part, unsigned *ticket, BiState<double> *st, int zlen) {
+__global__ void __launch_bounds__(256, 4) k_bi_pad(DevOp op, DevOp32 o, const float *__restrict__ p,
+                                                   const float *__restrict__ rh, float *__restrict__ out,
+                                                   double *part, unsigned *ticket, BiState<double> *st, int zlen) {
     if (st->status != 0) return;
     if (MODE == 1 && st->half) return;
     constexpr int ND = MODE == 0 ? 1 : 4;
     __shared__ double red[(256 / 32) * ND];
     __shared__ double tot[ND];
     const int N = op.N;
-    const unsigned NN = (unsigned)N * (unsigned)N;
-    const int ntx = (N + kPlX - 1) / kPlX, tiles = plane_tiles_xy(N);
-    const int b = blockIdx.x;
-    const int xy = b % tiles;
-    const int x0 = (xy % ntx) * kPlX, y0 = (xy / ntx) * kPlY, z0 = (b / tiles) * zlen;
+    const int P = pad_pitch(N), G = P / 4;
+    const int ntx = (G + 31) / 32, tiles = pad_tiles(N);
+    const int b = blockIdx.x, xy = b % tiles;
+    const int g0 = (xy % ntx) * 32, y0 = (xy / ntx) * 8, z0 = (b / tiles) * zlen;
     const int z1 = min(z0 + zlen, N);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = x0 + lane, y = y0 + w;
-    const bool inside = x < N && y < N;
-    const bool hs = inside && y > 0, hn = inside && y < N - 1;
-    const bool hw = inside && lane == 0 && x > 0, he = inside && (lane == 31 || x == N - 1) && x < N - 1;
-    const unsigned col = inside ? (unsigned)y * (unsigned)N + (unsigned)x : 0u;   // offset within a plane
-    auto at = [&](int z) { return (unsigned)z * NN + col; };
-    // registers: planes k-1, k, k+1 of p; k+2 loaded ahead; r_hat of planes k, k+1; the y
-    // neighbours of plane k
-    float pm = (inside && z0 > 0) ? p[at(z0 - 1)] : 0.0f;
-    float pc = inside ? p[at(z0)] : 0.0f;
-    float pn = (inside && z0 + 1 < N) ? p[at(z0 + 1)] : 0.0f;
-    float pnn = (inside && z0 + 2 < N) ? p[at(z0 + 2)] : 0.0f;
-    float rc = inside ? rh[at(z0)] : 0.0f;
-    float rn = (inside && z0 + 1 < z1) ? rh[at(z0 + 1)] : 0.0f;
-    float ys = hs ? p[at(z0) - N] : 0.0f, yn = hn ? p[at(z0) + N] : 0.0f;
+    const int g = g0 + lane, y = y0 + w, x = 4 * g;
+    const bool act = g < G && y < N;
+    const bool hs = act && y > 0, hn = act && y < N - 1;
+    const bool hw = act && lane == 0 && x > 0, he = act && lane == 31 && g + 1 < G;
+    const unsigned PS = (unsigned)P * (unsigned)N;
+    const unsigned col = act ? (unsigned)y * P + x : 0u;
+    auto at = [&](int z) { return (unsigned)z * PS + col; };
+    float4 pm = ld4c(act && z0 > 0, p, at(z0 - 1));
+    float4 pc = ld4c(act, p, at(z0));
+    float4 pn = ld4c(act && z0 + 1 < N, p, at(z0 + 1));
+    float4 pnn = ld4c(act && z0 + 2 < N, p, at(z0 + 2));
+    float4 rc = ld4c(act, rh, at(z0));
+    float4 rn = ld4c(act && z0 + 1 < z1, rh, at(z0 + 1));
+    float4 ys = ld4c(hs, p, at(z0) - P), yn = ld4c(hn, p, at(z0) + P);
+    // which of the 4 points are grid points (x + i < N); the rest are padding
+    const bool in1 = x + 1 < N, in2 = x + 2 < N, in3 = x + 3 < N;
     float acc[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) acc[d] = 0.0f;
     for (int k = z0; k < z1; ++k) {
-        // loads for later planes first (independent of this plane's arithmetic)
-        const float pload = (inside && k + 3 < N) ? p[at(k + 3)] : 0.0f;
-        const float rload = (inside && k + 2 < z1) ? rh[at(k + 2)] : 0.0f;
+        const float4 pload = ld4c(act && k + 3 < N, p, at(k + 3));
+        const float4 rload = ld4c(act && k + 2 < z1, rh, at(k + 2));
         const bool nxt = k + 1 < z1;
-        const float ysn = (hs && nxt) ? p[at(k + 1) - N] : 0.0f;
-        const float ynn = (hn && nxt) ? p[at(k + 1) + N] : 0.0f;
-        // x neighbours: the neighbouring lanes' centre values (0 outside the grid)
-        float xw = __shfl_up_sync(0xffffffffu, pc, 1);
-        float xe = __shfl_down_sync(0xffffffffu, pc, 1);
+        const float4 ysn = ld4c(hs && nxt, p, at(k + 1) - P);
+        const float4 ynn = ld4c(hn && nxt, p, at(k + 1) + P);
+        float xw = __shfl_up_sync(0xffffffffu, pc.w, 1);
+        float xe = __shfl_down_sync(0xffffffffu, pc.x, 1);
         if (lane == 0) xw = hw ? p[at(k) - 1] : 0.0f;
-        if (he && lane == 31) xe = p[at(k) + 1];
-        if (x == N - 1) xe = 0.0f;
-        float v = o.c0 * pc;
-        v = fmaf(o.cxm, xw, v);
-        v = fmaf(o.cxp, xe, v);
-        v = fmaf(o.cym, ys, v);
-        v = fmaf(o.cyp, yn, v);
-        v = fmaf(o.czm, pm, v);
-        v = fmaf(o.czp, pn, v);
-        if (inside) {
-            out[at(k)] = v;
+        if (lane == 31) xe = he ? p[at(k) + 4] : 0.0f;
+        float4 v;
+        v.x = st7(o, pc.x, xw, pc.y, ys.x, yn.x, pm.x, pn.x);
+        v.y = in1 ? st7(o, pc.y, pc.x, pc.z, ys.y, yn.y, pm.y, pn.y) : 0.0f;
+        v.z = in2 ? st7(o, pc.z, pc.y, pc.w, ys.z, yn.z, pm.z, pn.z) : 0.0f;
+        v.w = in3 ? st7(o, pc.w, pc.z, xe, ys.w, yn.w, pm.w, pn.w) : 0.0f;
+        if (x >= N) v.x = 0.0f;
+        if (act) {
+            *reinterpret_cast<float4 *>(out + at(k)) = v;
             if (MODE == 0) {
-                acc[0] = fmaf(rc, v, acc[0]);
+                acc[0] = fmaf(rc.x, v.x, acc[0]);
+                acc[0] = fmaf(rc.y, v.y, acc[0]);
+                acc[0] = fmaf(rc.z, v.z, acc[0]);
+                acc[0] = fmaf(rc.w, v.w, acc[0]);
             } else {
-                acc[0] = fmaf(v, pc, acc[0]);
-                acc[ND > 1 ? 1 : 0] = fmaf(v, v, acc[ND > 1 ? 1 : 0]);
-                acc[ND > 2 ? 2 : 0] = fmaf(rc, pc, acc[ND > 2 ? 2 : 0]);
-                acc[ND > 3 ? 3 : 0] = fmaf(rc, v, acc[ND > 3 ? 3 : 0]);
+                const float vv[4] = {v.x, v.y, v.z, v.w}, cc[4] = {pc.x, pc.y, pc.z, pc.w};
+                const float rr[4] = {rc.x, rc.y, rc.z, rc.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    acc[0] = fmaf(vv[e], cc[e], acc[0]);
+                    acc[ND > 1 ? 1 : 0] = fmaf(vv[e], vv[e], acc[ND > 1 ? 1 : 0]);
+                    acc[ND > 2 ? 2 : 0] = fmaf(rr[e], cc[e], acc[ND > 2 ? 2 : 0]);
+                    acc[ND > 3 ? 3 : 0] = fmaf(rr[e], vv[e], acc[ND > 3 ? 3 : 0]);
+                }
             }
         }
         pm = pc; pc = pn; pn = pnn; pnn = pload;

@@ -309,8 +309,6 @@ __device__ void hessenberg(T *A, int m, T *Z, T *v) {
 // Schur vector rows.  Bulge entries that the next transform annihilates are stored as exact
 // zeros, so no clean-up pass is needed.
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kTwoBulgeMin = 12;    // real Schur: active windows of at least this many rows chase two bulges
-constexpr int kTwoBulgeLag = 4;     // steps between the two bulges (>= 4: disjoint rows and columns)
 
 // Complex Givens rotation G = [conj(a) conj(b); -b a] with G [x; y] = [r; 0], r = ||(x, y)||:
 // a = x / r, b = y / r.  Warp-wide call; lanes 0..3 hold x.re, x.im, y.re, y.im in v and
@@ -471,146 +469,6 @@ __device__ int real_schur(double *H, int m, double *Z) {
             if (tid == 0) hi_s = hi - 2;
             __syncthreads();
             its = 0;
-            continue;
-        }
-        // ---- two double-shift bulges per sweep on a window of at least kTwoBulgeMin rows:
-        // the shift pairs are the eigenvalues of the trailing 2x2 block (hi-1, hi) and of the
-        // 2x2 block above it (hi-3, hi-2); bulge 0 is introduced at l, bulge 1 kTwoBulgeLag
-        // steps later from the then-current top of the window.  A left update touches 3 rows
-        // and a right update 3 columns, and the bulges stay kTwoBulgeLag >= 4 apart, so in each
-        // time step both bulges' left updates (with their Schur-vector updates) run in one
-        // phase and their right updates in the next; warps 0 and 1 each finish their bulge's
-        // three rows and compute its next reflector, so the two reflector chains (the serial
-        // float64 part of a sweep) run side by side on two sub-partitions.
-        if (hi - l + 1 >= kTwoBulgeMin && (its + 1) % 10 != 0) {
-            ++its;
-            ++total;
-            if (total > 40 * m) {
-                if (tid == 0) status_s = 1;
-                __syncthreads();
-                break;
-            }
-            __shared__ double hb_s[2][3];      // tau, v1, v2 of each bulge's current reflector
-            __shared__ double s1_s, t1_s;      // shift pair of bulge 1
-            if (tid == 0) {
-                const double a = H[(hi - 1) + (size_t)(hi - 1) * m], b = H[(hi - 1) + (size_t)hi * m];
-                const double c = H[hi + (size_t)(hi - 1) * m], d = H[hi + (size_t)hi * m];
-                const double s = a + d, t = a * d - b * c;
-                const double a1 = H[(hi - 3) + (size_t)(hi - 3) * m], b1 = H[(hi - 3) + (size_t)(hi - 2) * m];
-                const double c1 = H[(hi - 2) + (size_t)(hi - 3) * m], d1 = H[(hi - 2) + (size_t)(hi - 2) * m];
-                s1_s = a1 + d1;
-                t1_s = a1 * d1 - b1 * c1;
-                const double h00 = H[l + (size_t)l * m], h01 = H[l + (size_t)(l + 1) * m];
-                const double h10 = H[(l + 1) + (size_t)l * m], h11 = H[(l + 1) + (size_t)(l + 1) * m];
-                x_s = h00 * h00 + h01 * h10 - s * h00 + t;
-                y_s = h10 * (h00 + h11 - s);
-                z_s = h10 * H[(l + 2) + (size_t)(l + 1) * m];
-            }
-            __syncthreads();
-            if (warp == 0) house3_warp(lane == 0 ? x_s : lane == 1 ? y_s : lane == 2 ? z_s : 0.0, hb_s[0]);
-            __syncthreads();
-            const int nsteps = (hi - l) + kTwoBulgeLag;
-            for (int ts = 0; ts < nsteps; ++ts) {
-                const int kb[2] = {l + ts, l + ts - kTwoBulgeLag};
-                const bool on[2] = {kb[0] <= hi - 1, ts >= kTwoBulgeLag && kb[1] <= hi - 1};
-                double tau[2], v1[2], v2[2];
-                int nrb[2], c0b[2], ncb[2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    nrb[q] = (kb[q] <= hi - 2) ? 3 : 2;
-                    tau[q] = hb_s[q][0];
-                    v1[q] = hb_s[q][1];
-                    v2[q] = nrb[q] == 3 ? hb_s[q][2] : 0.0;
-                    c0b[q] = kb[q] > l ? kb[q] - 1 : l;
-                    ncb[q] = on[q] ? m - c0b[q] : 0;
-                }
-                // phase 1: left updates (rows kb..kb+nr-1 over columns c0..m-1, the entries the
-                // reflector annihilates stored as exact zeros) and Schur-vector updates
-                // (Z <- Z P over columns kb..kb+nr-1, all m rows) of both bulges
-                const int nz0 = on[0] ? m : 0, nz1 = on[1] ? m : 0;
-                const int tot1 = ncb[0] + ncb[1] + nz0 + nz1;
-                for (int it = tid; it < tot1; it += nt) {
-                    int q, e;
-                    bool zrow;
-                    if (it < ncb[0]) { q = 0; e = it; zrow = false; }
-                    else if (it < ncb[0] + ncb[1]) { q = 1; e = it - ncb[0]; zrow = false; }
-                    else if (it < ncb[0] + ncb[1] + nz0) { q = on[0] ? 0 : 1; e = it - ncb[0] - ncb[1]; zrow = true; }
-                    else { q = 1; e = it - ncb[0] - ncb[1] - nz0; zrow = true; }
-                    const int k = kb[q], nr = nrb[q];
-                    if (!zrow) {
-                        const int c = c0b[q] + e;
-                        double *hc = H + (size_t)c * m + k;
-                        const double h0 = hc[0], h1 = hc[1];
-                        const double h2 = nr == 3 ? hc[2] : 0.0;
-                        const double sv = tau[q] * fma(v2[q], h2, fma(v1[q], h1, h0));
-                        const bool bulge = k > l && c == k - 1;
-                        hc[0] = h0 - sv;
-                        hc[1] = bulge ? 0.0 : fma(-sv, v1[q], h1);
-                        if (nr == 3) hc[2] = bulge ? 0.0 : fma(-sv, v2[q], h2);
-                    } else {
-                        double *zr = Z + e;
-                        const double h0 = zr[(size_t)k * m], h1 = zr[(size_t)(k + 1) * m];
-                        const double h2 = nr == 3 ? zr[(size_t)(k + 2) * m] : 0.0;
-                        const double sv = tau[q] * fma(v2[q], h2, fma(v1[q], h1, h0));
-                        zr[(size_t)k * m] = h0 - sv;
-                        zr[(size_t)(k + 1) * m] = fma(-sv, v1[q], h1);
-                        if (nr == 3) zr[(size_t)(k + 2) * m] = fma(-sv, v2[q], h2);
-                    }
-                }
-                __syncthreads();
-                // phase 2: right updates (columns kb..kb+nr-1 of rows 0..rmax).  Warp q (q = 0, 1)
-                // takes rows kb+1..rmax of bulge q (at most 3, one per lane), then computes the
-                // bulge's next reflector from column kb of those rows; warp 1 also introduces
-                // bulge 1 in the step before its first (from the current rows l..l+2).  Warps
-                // 2.. take rows 0..kb of both bulges.
-                if (warp < 2) {
-                    const int q = warp;
-                    if (on[q]) {
-                        const int k = kb[q], nr = nrb[q];
-                        const int rmax = (k + 3 < hi) ? k + 3 : hi;
-                        const int r = k + 1 + lane;
-                        double xv = 0.0;
-                        if (lane < 3 && r <= rmax) {
-                            double *hr = H + r;
-                            const double h0 = hr[(size_t)k * m], h1 = hr[(size_t)(k + 1) * m];
-                            const double h2 = nr == 3 ? hr[(size_t)(k + 2) * m] : 0.0;
-                            const double sv = tau[q] * fma(v2[q], h2, fma(v1[q], h1, h0));
-                            xv = h0 - sv;
-                            hr[(size_t)k * m] = xv;
-                            hr[(size_t)(k + 1) * m] = fma(-sv, v1[q], h1);
-                            if (nr == 3) hr[(size_t)(k + 2) * m] = fma(-sv, v2[q], h2);
-                        }
-                        __syncwarp();
-                        if (k < hi - 1) house3_warp(xv, hb_s[q]);     // z = 0 when k + 3 > hi
-                    } else if (q == 1 && ts == kTwoBulgeLag - 1) {
-                        double v = 0.0;
-                        if (lane < 3) {
-                            const double s = s1_s, t = t1_s;
-                            const double h00 = H[l + (size_t)l * m], h01 = H[l + (size_t)(l + 1) * m];
-                            const double h10 = H[(l + 1) + (size_t)l * m], h11 = H[(l + 1) + (size_t)(l + 1) * m];
-                            v = lane == 0 ? h00 * h00 + h01 * h10 - s * h00 + t
-                              : lane == 1 ? h10 * (h00 + h11 - s)
-                                          : h10 * H[(l + 2) + (size_t)(l + 1) * m];
-                        }
-                        house3_warp(v, hb_s[1]);
-                    }
-                } else {
-                    const int nh0 = on[0] ? kb[0] + 1 : 0, nh1 = on[1] ? kb[1] + 1 : 0;
-                    for (int t2 = tid - 64; t2 < nh0 + nh1; t2 += nt - 64) {
-                        const int q = t2 < nh0 ? 0 : 1;
-                        const int row = t2 < nh0 ? t2 : t2 - nh0;
-                        const int k = kb[q], nr = nrb[q];
-                        double *hr = H + row;
-                        const double h0 = hr[(size_t)k * m], h1 = hr[(size_t)(k + 1) * m];
-                        const double h2 = nr == 3 ? hr[(size_t)(k + 2) * m] : 0.0;
-                        const double sv = tau[q] * fma(v2[q], h2, fma(v1[q], h1, h0));
-                        hr[(size_t)k * m] = h0 - sv;
-                        hr[(size_t)(k + 1) * m] = fma(-sv, v1[q], h1);
-                        if (nr == 3) hr[(size_t)(k + 2) * m] = fma(-sv, v2[q], h2);
-                    }
-                }
-                __syncthreads();
-            }
             continue;
         }
         // ---- double-shift sweep on rows/cols l..hi
