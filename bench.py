@@ -44,6 +44,10 @@ WORKLOADS = {
     # 32^4 U(1) lattice, complex128, mass tuned to lambda_min = 1e-3, coarse 16^4 Galerkin, k = 40
     "u1_32": dict(kind="u1_4d", N=32, m=80, k=40, nev=40, rtolev=1e-2, rtol_c=1e-8, max_cycles=300,
                   method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20, restart_mvps=0, m3=20),
+    # the same with the moved vectors improved on the fine lattice (10 Arnoldi-E(80, 40) cycles)
+    "u1_32_improved": dict(kind="u1_4d", N=32, m=80, k=40, nev=40, rtolev=1e-2, rtol_c=1e-8, max_cycles=300,
+                           method="bicgstab", proj="minres", precision="f64", rtol=1e-8, ncyc=20, restart_mvps=0,
+                           m3=20, improve=dict(m=80, cycles=10, nstart=10, rtolev=1e-3)),
     # 128 independent 2D problems, N_i odd ~ U{255..1023}, beta_i ~ U(0.5, 4), 8 right-hand
     # sides each sharing one 20-vector basis; float32 inner BiCGStab, float64 refinement
     # coarse phase GMRES-DR(60,20), at most 100 cycles: the whole-step optimum of a sweep over
@@ -269,8 +273,12 @@ def run_tg(args, wl, rank, world):
                                             rtol=wl["rtol_c"], max_cycles=wl["max_cycles"], proj=wl["proj"],
                                             precision=precision)
         x = op.prolong(xc)
+        if wl.get("improve"):
+            # the paper's optional phase 2: Arnoldi-E cycles on the moved vectors (fine grid)
+            im = wl["improve"]
+            defl.improve(m=im["m"], cycles=im["cycles"], nstart=im["nstart"], nev=wl["nev"], rtolev=im["rtolev"])
         if mid is not None:
-            mid.record(torch.cuda.current_stream())     # end of the setup (coarse phase, A Y, factor)
+            mid.record(torch.cuda.current_stream())     # end of the setup (coarse phase, A Y, factor[, improve])
         status, st = op.solve(bvec, x, defl, method=wl["method"], precision=precision, rtol=wl["rtol"],
                               ncyc=wl["ncyc"], restart_mvps=wl["restart_mvps"], m3=wl["m3"])
         return x, status, st[0], cst
