@@ -28,7 +28,6 @@ namespace {
 
 constexpr double kEps = DBL_EPSILON;
 
-__device__ __forceinline__ double sq(double a) { return a * a; }
 
 // ----------------------------------------------------------------------------- generic helpers
 template <class T> struct Cx;

@@ -89,10 +89,12 @@ def test_cfg0_cycle_schedule_ncyc(tg):
 
 @pytest.mark.parametrize("N", [33, 9, 65])
 def test_float32_plane_stencil_bicgstab_parity(tg, N):
-    """The float32 3D BiCGStab runs its stencil products through the plane-marching kernels
-    (32 x 8 point columns, 32-plane chunks).  N = 33 and 65 leave partial tiles along every
-    axis, N = 9 a single partial tile; 12 products against the oracle's float64 BiCGStab
-    from x0 = 0 agree to float32 accuracy (the iterates differ by float32 rounding only)."""
+    """The float32 3D BiCGStab cycle runs in the padded layout (row pitch the multiple of 4
+    above N, zero padding column) with the float4 plane-marching stencil (32 float4 groups x
+    8 rows per block).  N = 33, 9 and 65 (pitch 36, 12, 68) leave partial groups and tiles
+    along every axis; 12 products against the oracle's float64 BiCGStab from x0 = 0 agree to
+    float32 accuracy (the iterates differ by float32 rounding only), which also checks the
+    copies into and out of the padded layout."""
     beta = (2.0, 1.0, 0.5)
     top, oop = tg.Operator("cd3d", N, beta), OOp(CD3D, N, beta)
     b = gi.rhs(oop.n, 41)
