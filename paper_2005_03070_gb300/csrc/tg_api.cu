@@ -204,7 +204,7 @@ enum Slot {
     S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC, S_XBAK,
     S_IG, S_IU, S_IP, S_IPR, S_IPRI, S_IT, S_IINFO,
     S_AE_S, S_AE_W, S_AE_H, S_AE_WW, S_AE_HA, S_AE_Y, S_AE_U, S_AE_P, S_AE_Z, S_AE_TH, S_AE_WR, S_AE_WI,
-    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM, S_PADX, S_PADR,
+    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM, S_PADX, S_PADR, S_AE_HR, S_AE_WWR,
     S_COUNT
 };
 
@@ -481,33 +481,36 @@ static int gemv_t(tg_op *op, const T *V, size_t ldv, int ncol, const T *w, int n
 // computed, the lower one mirrored)
 template <class T, int EPT>
 static int gram_ept(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int sym, typename ST<T>::D *G,
-                    cudaStream_t s) {
+                    cudaStream_t s, int kb) {
     using D = typename ST<T>::D;
-    const int nent = sym ? k * (k + 1) / 2 : k * k;
+    const int nent = sym ? k * (k + 1) / 2 : k * kb;
     const int gy = (nent + kThreads * EPT - 1) / (kThreads * EPT);
     const int gx = std::max(1, tiles_grid(n, 4) / gy);
     TG_CHECK(red_ready(op, (size_t)gx * nent * sizeof(D) + (size_t)nent * sizeof(D), s));
     D *part = wsp<D>(op, S_PART);
     D *packed = part + (size_t)gx * nent;
-    const size_t smem = (size_t)(A == B ? 1 : 2) * 33 * k * sizeof(T);
+    const size_t smem = (size_t)(A == B ? k : k + kb) * 33 * sizeof(T);
     TG_CHECK(set_smem<T>((const void *)k_gram_packed<T, EPT>, smem));
-    TG_PROF(P_GRAM, (A == B ? 1.0 : 2.0) * k * n * sizeof(T), 2.0 * nent * n * (sizeof(T) == 16 ? 4 : 1),
-            k_gram_packed<T, EPT><<<dim3(gx, gy), kThreads, smem, s>>>(A, B, ld, k, n, sym, nent, part));
+    TG_PROF(P_GRAM, (A == B ? 1.0 * k : 1.0 * (k + kb)) * n * sizeof(T), 2.0 * nent * n * (sizeof(T) == 16 ? 4 : 1),
+            k_gram_packed<T, EPT><<<dim3(gx, gy), kThreads, smem, s>>>(A, B, ld, k, n, sym, nent, part, kb));
     TG_LAUNCH_CHECK();
     TG_PROF(P_SUM_PART, (double)gx * nent * sizeof(D), (double)gx * nent,
             k_sum_part<D><<<(nent + 7) / 8, 256, 0, s>>>(part, gx, nent, packed, 0));
-    TG_PROF(P_SMALL, 0, 0, k_gram_unpack<D><<<(nent + 255) / 256, 256, 0, s>>>(packed, k, sym, G));
+    TG_PROF(P_SMALL, 0, 0, k_gram_unpack<D><<<(nent + 255) / 256, 256, 0, s>>>(packed, k, sym, G, kb));
     TG_LAUNCH_CHECK();
     return TG_OK;
 }
+
+// G = A^H B: A has k columns, B has kb columns (kb < 0: kb = k); sym requires B = A.
 template <class T>
 static int gram(tg_op *op, const T *A, const T *B, size_t ld, int k, int n, int sym, typename ST<T>::D *G,
-                cudaStream_t s) {
-    const int nent = sym ? k * (k + 1) / 2 : k * k;
-    if (nent <= kThreads) return gram_ept<T, 1>(op, A, B, ld, k, n, sym, G, s);
-    if (nent <= 2 * kThreads) return gram_ept<T, 2>(op, A, B, ld, k, n, sym, G, s);
-    if (nent <= 4 * kThreads) return gram_ept<T, 4>(op, A, B, ld, k, n, sym, G, s);
-    return gram_ept<T, 8>(op, A, B, ld, k, n, sym, G, s);
+                cudaStream_t s, int kb = -1) {
+    if (kb < 0) kb = k;
+    const int nent = sym ? k * (k + 1) / 2 : k * kb;
+    if (nent <= kThreads) return gram_ept<T, 1>(op, A, B, ld, k, n, sym, G, s, kb);
+    if (nent <= 2 * kThreads) return gram_ept<T, 2>(op, A, B, ld, k, n, sym, G, s, kb);
+    if (nent <= 4 * kThreads) return gram_ept<T, 4>(op, A, B, ld, k, n, sym, G, s, kb);
+    return gram_ept<T, 8>(op, A, B, ld, k, n, sym, G, s, kb);
 }
 
 // CholQR2: A (n x k) = Q R.  Writes Q (n x k), R and Rinv (k x k, device D).
@@ -2011,9 +2014,42 @@ static int cgs2_column(tg_op *op, T *V, size_t ldv, int n, int j, double drop_re
 // Rayleigh-Ritz on span(S) (cols orthonormal columns, leading dimension ld) with W = A S:
 // H = S^H W, WW = W^H W, the small dense kernel in Rayleigh-Ritz mode (ordered Ritz pairs,
 // k kept, k + 1 if a pair would split); then Y = S P_k and u = S z (Ritz vector start_q).
+// Rayleigh-Ritz matrices of an Arnoldi-E cycle whose first p + 1 basis columns K are an
+// Arnoldi basis (A K[:, :p] = K Ha, Ha (p+1) x p upper Hessenberg, ld p+1) and whose other
+// columns are orthogonal to K: with W_R = A S[:, p:] (q = cols - p columns), HR = S^H W_R
+// (cols x q) and WWR = W_R^H W_R (q x q), the cycle's matrices are
+//   H  = S^H A S:       columns j < p are [Ha[:, j]; 0], columns p.. are HR;
+//   WW = (A S)^H (A S): [[Ha^H Ha, Ha^H HR[:p+1, :]], [HR[:p+1, :]^H Ha, WWR]],
+// so A is applied, and the long Gram products run, on the q columns of W_R only.
+template <class T>
+__global__ void k_ae_assemble(const T *__restrict__ Ha, int p, const T *__restrict__ HR,
+                              const T *__restrict__ WWR, int cols, T *__restrict__ H, T *__restrict__ WW) {
+    const int q = cols - p, ldh = p + 1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cols * cols; e += gridDim.x * blockDim.x) {
+        const int i = e % cols, j = e / cols;
+        T h = ST<T>::zero();
+        if (j >= p) h = HR[i + (size_t)(j - p) * cols];
+        else if (i <= j + 1) h = Ha[i + (size_t)j * ldh];
+        H[e] = h;
+        T w = ST<T>::zero();
+        if (i < p && j < p) {
+            const int lmax = (i < j ? i : j) + 1;          // Ha[l, c] = 0 for l > c + 1
+            for (int l = 0; l <= lmax; ++l) w = w + dconj(Ha[l + (size_t)i * ldh]) * Ha[l + (size_t)j * ldh];
+        } else if (i < p) {
+            for (int l = 0; l <= i + 1; ++l) w = w + dconj(Ha[l + (size_t)i * ldh]) * HR[l + (size_t)(j - p) * cols];
+        } else if (j < p) {
+            for (int l = 0; l <= j + 1; ++l) w = w + dconj(HR[l + (size_t)(i - p) * cols]) * Ha[l + (size_t)j * ldh];
+        } else {
+            w = WWR[(i - p) + (size_t)(j - p) * q];
+        }
+        WW[e] = w;
+    }
+}
+
 template <class T>
 static int rayleigh_ritz(tg_op *op, const T *S, const T *W, size_t ld, int n, int cols, int k, int nev,
-                         double rtolev, int start_q, T *Y, T *u, GdrInfo *info_h, cudaStream_t s) {
+                         double rtolev, int start_q, T *Y, T *u, GdrInfo *info_h, cudaStream_t s,
+                         const T *Ha = nullptr, int p = 0) {
     using D = typename ST<T>::D;
     const int m = cols;
     TG_CHECK(wsx(op, S_AE_H, (size_t)m * m * sizeof(T)));
@@ -2031,8 +2067,20 @@ static int rayleigh_ritz(tg_op *op, const T *S, const T *W, size_t ld, int n, in
     TG_CHECK(wsx(op, S_AE_INFO, sizeof(GdrInfo)));
     TG_CHECK(wsx(op, S_AE_DUM, (size_t)(m + 2) * (m + 2) * sizeof(T)));
     T *H = wsp<T>(op, S_AE_H), *WW = wsp<T>(op, S_AE_WW);
-    TG_CHECK(gram<T>(op, S, W, ld, m, n, 0, reinterpret_cast<D *>(H), s));
-    TG_CHECK(gram<T>(op, W, W, ld, m, n, 1, reinterpret_cast<D *>(WW), s));
+    if (p > 0) {
+        const int q = m - p;
+        TG_CHECK(wsx(op, S_AE_HR, (size_t)m * q * sizeof(T)));
+        TG_CHECK(wsx(op, S_AE_WWR, (size_t)q * q * sizeof(T)));
+        T *HR = wsp<T>(op, S_AE_HR), *WWR = wsp<T>(op, S_AE_WWR);
+        const T *WR = W + (size_t)p * ld;
+        TG_CHECK(gram<T>(op, S, WR, ld, m, n, 0, reinterpret_cast<D *>(HR), s, q));
+        TG_CHECK(gram<T>(op, WR, WR, ld, q, n, 1, reinterpret_cast<D *>(WWR), s));
+        TG_PROF(P_SMALL, 0, 0, k_ae_assemble<T><<<(m * m + 255) / 256, 256, 0, s>>>(Ha, p, HR, WWR, m, H, WW));
+        TG_LAUNCH_CHECK();
+    } else {
+        TG_CHECK(gram<T>(op, S, W, ld, m, n, 0, reinterpret_cast<D *>(H), s));
+        TG_CHECK(gram<T>(op, W, W, ld, m, n, 1, reinterpret_cast<D *>(WW), s));
+    }
     GdrArgs<T> a;
     T *dum = wsp<T>(op, S_AE_DUM);
     a.H = H; a.ldh = m; a.c = dum; a.m = m; a.k = k; a.nev = nev; a.rtolev = rtolev;
@@ -2106,9 +2154,11 @@ static int improve_impl(tg_op *op, tg_defl *d, int m, int cycles, int nstart, in
             TG_CHECK(cgs2_column<T>(op, S, ld, n, cols, 1e-10, &kept, s));
             if (kept) ++cols;
         }
-        for (int c = 0; c < cols; ++c) TG_CHECK(launch_apply<T>(A, A32, S + (size_t)c * ld, W + (size_t)c * ld, s));
-        mvps += cols;
-        TG_CHECK(rayleigh_ritz<T>(op, S, W, ld, n, cols, k, nev, rtolev, (cyc + 1) % nstart, Y, u, &info, s));
+        // A S[:, :p] = S[:, :p+1] Ha is known from the Arnoldi step: only the last Krylov column
+        // and the appended vectors are multiplied
+        for (int c = p; c < cols; ++c) TG_CHECK(launch_apply<T>(A, A32, S + (size_t)c * ld, W + (size_t)c * ld, s));
+        mvps += cols - p;
+        TG_CHECK(rayleigh_ritz<T>(op, S, W, ld, n, cols, k, nev, rtolev, (cyc + 1) % nstart, Y, u, &info, s, Ha, p));
         kk = info.kk;
         done = cyc + 1;
         if (rtolev > 0 && nev > 0 && info.nconv >= nev) break;

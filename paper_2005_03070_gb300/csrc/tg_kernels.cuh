@@ -874,7 +874,8 @@ __global__ void __launch_bounds__(kThreads) k_tsm(const T *__restrict__ In, size
 
 // Partial Gram products G = A^H B over 32-row tiles, on a packed list of output entries:
 // sym = 1 takes the upper triangle i <= j column by column (entry e = j (j + 1) / 2 + i; the
-// lower triangle is its conjugate), sym = 0 all k^2 entries (e = i + j k).  Block (x, y)
+// lower triangle is its conjugate), sym = 0 all k x kb entries (e = i + j k; B has kb columns,
+// kb = k for a square Gram).  Block (x, y)
 // takes row tiles x, x + gridDim.x, ... and entries y * kThreads * EPT + threadIdx.x +
 // q * kThreads, q < EPT, and writes part[x * nent + e].  Tiles are staged with a row stride of
 // 33 elements, so the lanes of a warp (consecutive i) read distinct shared-memory banks; each
@@ -882,7 +883,7 @@ __global__ void __launch_bounds__(kThreads) k_tsm(const T *__restrict__ In, size
 template <class T, int EPT>
 __global__ void __launch_bounds__(kThreads) k_gram_packed(const T *__restrict__ A, const T *__restrict__ B,
                                                            size_t ld, int k, int n, int sym, int nent,
-                                                           typename ST<T>::D *part) {
+                                                           typename ST<T>::D *part, int kb) {
     using D = typename ST<T>::D;
     constexpr int kS = 33;                   // staged row stride (elements)
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -916,8 +917,13 @@ __global__ void __launch_bounds__(kThreads) k_gram_packed(const T *__restrict__ 
             const int r = e & 31, c = e >> 5;
             const int row = row0 + r;
             ta[c * kS + r] = row < n ? A[(size_t)c * ld + row] : ST<T>::zero();
-            if (!same) tb[c * kS + r] = row < n ? B[(size_t)c * ld + row] : ST<T>::zero();
         }
+        if (!same)
+            for (int e = threadIdx.x; e < 32 * kb; e += blockDim.x) {
+                const int r = e & 31, c = e >> 5;
+                const int row = row0 + r;
+                tb[c * kS + r] = row < n ? B[(size_t)c * ld + row] : ST<T>::zero();
+            }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
@@ -937,12 +943,12 @@ __global__ void __launch_bounds__(kThreads) k_gram_packed(const T *__restrict__ 
     }
 }
 
-// G (k x k, column-major) from the packed entries; sym: the lower triangle is the conjugate.
+// G (k x kb, column-major) from the packed entries; sym (kb = k): the lower triangle is the conjugate.
 __device__ __forceinline__ double dconj(double a) { return a; }
 __device__ __forceinline__ cplx dconj(cplx a) { return conj(a); }
 template <class D>
-__global__ void k_gram_unpack(const D *__restrict__ packed, int k, int sym, D *G) {
-    const int nent = sym ? k * (k + 1) / 2 : k * k;
+__global__ void k_gram_unpack(const D *__restrict__ packed, int k, int sym, D *G, int kb) {
+    const int nent = sym ? k * (k + 1) / 2 : k * kb;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += gridDim.x * blockDim.x) {
         int i, j;
         if (sym) {
