@@ -856,7 +856,8 @@ def run_paper(args, name, rank, world):
             Y = op_of(Nl).prolong(Y)
             x0 = op_of(Nl).prolong(x0)
         fine = op_of(N)
-        dfl, t_f = sync_time(lambda: fine.defl_from_basis(Y, kk, proj=cfg["proj"]))
+        # float32 copies too: the float32 + refinement IDR below uses them
+        dfl, t_f = sync_time(lambda: fine.defl_from_basis(Y, kk, proj=cfg["proj"], precision="f32_ir"))
         return x0, dfl, {"coarse_N": coarse_N, "cycles": cst["cycles"], "coarse_mvps": cst["coarse_mvps"],
                          "eig_converged": cst["eig_converged"], "kk": kk, "coarse_seconds": round(t_c, 3),
                          "AY_and_factor_seconds": round(t_f, 3)}
@@ -881,6 +882,10 @@ def run_paper(args, name, rank, world):
     for ncyc in cfg["idr_ncyc"]:
         record("idr_proj", ncyc, lambda x: fine.solve_idr(b, x, P, dfl, rtol=cfg["rtol"], ncyc=ncyc,
                                                           max_mvps=200000))
+    out["idr_proj_f32_ir"] = {}
+    for ncyc in cfg["idr_ncyc"]:
+        record("idr_proj_f32_ir", ncyc, lambda x: fine.solve_idr(b, x, P, dfl, rtol=cfg["rtol"], ncyc=ncyc,
+                                                                 max_mvps=200000, precision="f32_ir"))
     # without deflation: restarted BiCGStab with one cycle (non-restarted) from x0 = 0
     xz = torch.zeros_like(b)
     (status, st), t = sync_time(lambda: fine.solve(b, xz, None, rtol=cfg["rtol"], ncyc=1, restart_mvps=0,

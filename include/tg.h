@@ -227,8 +227,13 @@ int tg_solve_proj(tg_op *op, const tg_defl *defl, int method, int precision,
  *       independent (random normal is the usual choice); the library orthonormalises them
  *       by CholQR2 (the QR factor with a positive-diagonal R) and uses the same space in
  *       every cycle.  TG_BAD_ARG when they are numerically dependent.
- * precision must be TG_F64 (float64 / complex128).  Other arguments, stats and the return
- * value as for tg_solve_proj.  Synchronises `stream`.                                   */
+ * precision TG_F64 (float64 / complex128), or TG_F32_IR for the real operators: each
+ * cycle solves the correction equation in float32 IDR(s) (the orthonormalised shadow space
+ * rounded once to float32, a float32 projection with the handle's float32 copies, which
+ * must then exist) with float64 refinement of x and of the true residual; a correction
+ * that does not lower the float64 residual is undone and float64 IDR(s)-Proj cycles finish
+ * (stats.fp64_cycles).  b and x are float64 in both forms.  Other arguments, stats and the
+ * return value as for tg_solve_proj.  Synchronises `stream`.                             */
 int tg_solve_idr(tg_op *op, const tg_defl *defl, int precision, const void *b, void *x, int nrhs,
                  double rtol, int ncyc, int restart_mvps, int s, const void *P, double kappa,
                  int64_t max_mvps, tg_stats *stats, void *stream);

@@ -204,7 +204,7 @@ enum Slot {
     S_CQ_G, S_CQ_R1, S_CQ_R1I, S_CQ_R2, S_CQ_R2I, S_GAL_RY, S_GAL_RYI, S_GAL_W, S_GYC, S_XBAK,
     S_IG, S_IU, S_IP, S_IPR, S_IPRI, S_IT, S_IINFO,
     S_AE_S, S_AE_W, S_AE_H, S_AE_WW, S_AE_HA, S_AE_Y, S_AE_U, S_AE_P, S_AE_Z, S_AE_TH, S_AE_WR, S_AE_WI,
-    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM, S_PADX, S_PADR, S_AE_HR, S_AE_WWR,
+    S_AE_ORD, S_AE_ERES, S_AE_WORK, S_AE_YW, S_AE_GW, S_AE_INFO, S_AE_DUM, S_PADX, S_PADR, S_AE_HR, S_AE_WWR, S_IP32,
     S_COUNT
 };
 
@@ -1314,8 +1314,8 @@ struct IdrCfg {
 // One IDR(s) cycle on A e = r (updating x and r); device-resident scalars, status read
 // once per batch of rounds.
 template <class T>
-static int idr_cycle(tg_op *op, const DevOp &A, T *x, T *r, int n, const T *P, int sd, double kappa, double target2,
-                     int cap, CycleOut *out, cudaStream_t s) {
+static int idr_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r, int n, const T *P, int sd,
+                     double kappa, double target2, int cap, CycleOut *out, cudaStream_t s) {
     using D = typename ST<T>::D;
     const size_t ld = (size_t)n;
     TG_CHECK(wsx(op, S_IG, (size_t)n * sd * sizeof(T)));
@@ -1343,12 +1343,12 @@ static int idr_cycle(tg_op *op, const DevOp &A, T *x, T *r, int n, const T *P, i
                 TG_PROF(P_IDR_UPD, (2.0 + (first ? 0.0 : 2.0 * (sd - k))) * n * es, 4.0 * (sd - k) * n * cf,
                         k_idr_u<T><<<g, kThreads, 0, s>>>(r, G, U, ld, n, k, first, st));
                 TG_PROF(P_IDR_MV, (2.0 + sd) * n * es + xb * n, (fl + 2.0 * sd * cf) * n,
-                        k_idr_g<T><<<g, kThreads, 0, s>>>(A, U, G, P, ld, k, part, tk, st));
+                        k_idr_g<T><<<g, kThreads, 0, s>>>(A, A32, U, G, P, ld, k, part, tk, st));
                 TG_PROF(P_IDR_UPD, (2.0 * k + 8.0) * n * es, (4.0 * k + 6.0) * n * cf,
                         k_idr_upd<T><<<g, kThreads, 0, s>>>(G, U, ld, r, x, n, k, part, tk, st));
             }
             TG_PROF(P_IDR_MV, 2.0 * n * es + xb * n, (fl + 6.0 * cf) * n,
-                    k_idr_t<T><<<g, kThreads, 0, s>>>(A, r, t, part, tk, st));
+                    k_idr_t<T><<<g, kThreads, 0, s>>>(A, A32, r, t, part, tk, st));
             TG_PROF(P_IDR_UPD, (5.0 + sd) * n * es, (4.0 + 2.0 * (sd + 1)) * n * cf,
                     k_idr_xr<T><<<g, kThreads, 0, s>>>(x, r, t, P, ld, n, part, tk, st));
         }
@@ -1420,7 +1420,8 @@ static int solve_idr64(tg_op *op, const tg_defl *df, const T *b, T *x, const Sol
         if (cfg.restart_mvps > 0 && cap64 > cfg.restart_mvps) cap64 = cfg.restart_mvps;
         if (cap64 > INT_MAX / 2) cap64 = INT_MAX / 2;
         CycleOut co;
-        TG_CHECK(idr_cycle<T>(op, A, x, r, n, P, sv, ic.kappa, (rt * nr) * (rt * nr), (int)cap64, &co, s));
+        TG_CHECK(idr_cycle<T>(op, A, pick32(op, TG_FINE, 0), x, r, n, P, sv, ic.kappa, (rt * nr) * (rt * nr),
+                              (int)cap64, &co, s));
         mvps += co.mvps;
         if (co.status == 4) { status = TG_NAN; break; }
         TG_CHECK(true_residual<T>(op, A, b, x, r, &nr, &nb, s));
@@ -1435,6 +1436,113 @@ static int solve_idr64(tg_op *op, const tg_defl *df, const T *b, T *x, const Sol
         st->relres = nb > 0 ? nr / nb : 0.0;
         st->status = status;
         st->vops = mvps * (4 * sv + 8) / (sv + 1);
+    }
+    return status;
+}
+
+// IDR(ncyc)-Proj(k) in the float32 + refinement form (real operators): each cycle solves the
+// correction equation A e = r / ||r|| by float32 IDR(s) (float32 shadow space: the float64
+// orthonormalised one rounded once), after a float32 projection; x += ||r|| e in float64 and
+// the true residual is recomputed in float64.  A correction that does not lower the float64
+// residual is undone and float64 IDR(s)-Proj cycles finish the solve, as in solve_bicg_ir.
+static int solve_idr_ir(tg_op *op, const tg_defl *df, const double *b, double *x, const SolveCfg &cfg,
+                        const IdrCfg &ic, tg_stats *st, cudaStream_t s) {
+    const DevOp &A = pick(op, TG_FINE, 0);
+    const DevOp32 &A32 = pick32(op, TG_FINE, 0);
+    const int n = op->n, sv = ic.s;
+    TG_CHECK(wsx(op, S_IP, (size_t)n * sv * 8));
+    TG_CHECK(wsx(op, S_IPR, (size_t)sv * sv * 8));
+    TG_CHECK(wsx(op, S_IPRI, (size_t)sv * sv * 8));
+    TG_CHECK(wsx(op, S_IINFO, 64));
+    TG_CHECK(wsx(op, S_IP32, (size_t)n * sv * 4));
+    TG_CHECK_CUDA(cudaMemsetAsync(op->ws[S_IINFO].p, 0, 64, s));
+    double *P = wsp<double>(op, S_IP);
+    float *P32 = wsp<float>(op, S_IP32);
+    TG_CHECK(cholqr2<double>(op, static_cast<const double *>(ic.P_in), sv, n, P, wsp<double>(op, S_IPR),
+                             wsp<double>(op, S_IPRI), wsp<int>(op, S_IINFO), s));
+    {
+        int info[2] = {0, 0};
+        TG_CHECK(readback(op, wsp<int>(op, S_IINFO), 2 * sizeof(int), s));
+        memcpy(info, op->pin.p, sizeof(info));
+        if (info[0] || info[1]) {
+            set_error("the shadow columns are linearly dependent (Cholesky of P^H P failed)");
+            return TG_BAD_ARG;
+        }
+    }
+    TG_PROF(P_CONVERT, 12.0 * n * sv, 0, launch_d2f(grid_for((int64_t)n * sv, 8), s, P, P32, (size_t)n * sv));
+    TG_LAUNCH_CHECK();
+    TG_CHECK(wsx(op, S_R64, (size_t)n * 8));
+    TG_CHECK(wsx(op, S_R32, (size_t)n * 4));
+    TG_CHECK(wsx(op, S_E32, (size_t)n * 4));
+    TG_CHECK(wsx(op, S_XBAK, (size_t)n * 8));
+    double *xbak = wsp<double>(op, S_XBAK), *r = wsp<double>(op, S_R64);
+    float *r32 = wsp<float>(op, S_R32), *e32 = wsp<float>(op, S_E32);
+    const int g = grid_for(n, 8);
+    double nr, nb;
+    TG_CHECK(true_residual<double>(op, A, b, x, r, &nr, &nb, s));
+    int64_t mvps = 0;
+    int cyc = 0, fp64_cycles = 0;
+    int status = TG_NOT_CONVERGED;
+    if (!std::isfinite(nr)) status = TG_NAN;
+    else if (nb == 0.0 || nr <= cfg.rtol * nb) status = TG_OK;
+    while (status == TG_NOT_CONVERGED) {
+        ++cyc;
+        const bool sched = cfg.ncyc && cyc <= cfg.ncyc;
+        TG_PROF(P_CONVERT, 12.0 * n, n, launch_d2f_scaled(g, s, r, r32, n, 1.0 / nr));
+        TG_CHECK_CUDA(cudaMemsetAsync(e32, 0, (size_t)n * 4, s));
+        const double scale = nr;
+        double nrel = 1.0;
+        if (df && df->kk > 0) {
+            TG_CHECK(project_impl<float>(op, df, df->W32.as<float>(), df->B1_32.as<float>(), df->B2_32.as<float>(), e32,
+                                         r32, n, s));
+            double rr;
+            TG_CHECK(dot_host<float>(op, r32, nullptr, n, &rr, nullptr, s));
+            nrel = sqrt(rr);
+        }
+        const double nrp = nrel * scale;
+        double rt = sched ? cycle_tol(cfg.rtol, nb, nrp, cyc, cfg.ncyc) : cfg.rtol * nb / nrp;
+        if (rt < 1e-6) rt = 1e-6;   // a float32 cycle cannot resolve more; refinement continues
+        hist_push(st, nrp / nb, rt, mvps);
+        int64_t cap64 = cfg.max_mvps - mvps;
+        const int64_t cyc_cap = cfg.restart_mvps > 0 ? cfg.restart_mvps : kIrCycleCap;
+        if (cap64 > cyc_cap) cap64 = cyc_cap;
+        if (cap64 > INT_MAX / 2) cap64 = INT_MAX / 2;
+        CycleOut co;
+        TG_CHECK(idr_cycle<float>(op, A, A32, e32, r32, n, P32, sv, ic.kappa, (rt * nrel) * (rt * nrel), (int)cap64,
+                                  &co, s));
+        mvps += co.mvps;
+        TG_CHECK_CUDA(cudaMemcpyAsync(xbak, x, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        const double nr_before = nr;
+        TG_PROF(P_CONVERT, 20.0 * n, 2.0 * n, launch_add_f2d_scaled(g, s, x, e32, n, scale));
+        TG_LAUNCH_CHECK();
+        TG_CHECK(true_residual<double>(op, A, b, x, r, &nr, &nb, s));
+        if (std::isfinite(nr) && nr <= cfg.rtol * nb) { status = TG_OK; break; }
+        if (!std::isfinite(nr) || nr >= nr_before || co.status == 4) {
+            TG_CHECK_CUDA(cudaMemcpyAsync(x, xbak, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+            SolveCfg c64 = cfg;
+            c64.max_mvps = std::max<int64_t>(1, cfg.max_mvps - mvps);
+            c64.ncyc = 0;
+            if (c64.restart_mvps <= 0) c64.restart_mvps = 1000;
+            tg_stats s64{};
+            s64.history = nullptr;
+            const int rc64 = solve_idr64<double>(op, df, b, x, c64, ic, &s64, s);
+            mvps += s64.mvps;
+            cyc += s64.cycles;
+            fp64_cycles = s64.cycles;
+            nr = s64.relres * nb;
+            status = rc64;
+            break;
+        }
+        if (mvps >= cfg.max_mvps) break;
+        if (co.mvps == 0) { status = TG_BREAKDOWN; break; }
+    }
+    if (st) {
+        st->mvps = mvps;
+        st->cycles = cyc;
+        st->relres = nb > 0 ? nr / nb : 0.0;
+        st->status = status;
+        st->vops = mvps * (4 * sv + 8) / (sv + 1);
+        st->fp64_cycles = fp64_cycles;
     }
     return status;
 }
@@ -1640,7 +1748,10 @@ extern "C" int tg_solve_idr(tg_op *op, const tg_defl *defl, int precision, const
                             int64_t max_mvps, tg_stats *stats, void *stream) {
     TG_ARG(op && b && x && P, "NULL argument");
     TG_ARG(nrhs >= 1, "nrhs must be >= 1");
-    TG_ARG(precision == TG_F64, "IDR(s)-Proj runs in float64 / complex128");
+    TG_ARG(precision == TG_F64 || precision == TG_F32_IR, "bad precision");
+    TG_ARG(!(op->cplx_ && precision == TG_F32_IR), "the lattice path is complex128 only");
+    TG_ARG(!defl || precision == TG_F64 || defl->precision == TG_F32_IR,
+           "the deflation handle was built without float32 copies (precision TG_F64)");
     TG_ARG(s >= 1 && s <= kIdrMaxS, "s must be in 1..%d (got %d)", kIdrMaxS, s);
     TG_ARG(s < op->n, "s must be smaller than the problem size");
     TG_ARG(rtol > 0 && rtol < 1, "rtol must be in (0, 1)");
@@ -1663,7 +1774,8 @@ extern "C" int tg_solve_idr(tg_op *op, const tg_defl *defl, int precision, const
         const char *bc = (const char *)b + (size_t)c * op->n * es;
         char *xc = (char *)x + (size_t)c * op->n * es;
         const int rc = op->cplx_ ? solve_idr64<cplx>(op, defl, (const cplx *)bc, (cplx *)xc, cfg, ic, sp, st)
-                                 : solve_idr64<double>(op, defl, (const double *)bc, (double *)xc, cfg, ic, sp, st);
+                       : precision == TG_F32_IR ? solve_idr_ir(op, defl, (const double *)bc, (double *)xc, cfg, ic, sp, st)
+                                                : solve_idr64<double>(op, defl, (const double *)bc, (double *)xc, cfg, ic, sp, st);
         if (rc != TG_OK && worst == TG_OK) worst = rc;
         if (rc == TG_CUDA_ERROR || rc == TG_OOM || rc == TG_BAD_ARG) return rc;
     }

@@ -1,4 +1,5 @@
-// IDR(s) cycle kernels (float64 / complex128): the biorthogonal IDR(s) of van Gijzen and
+// IDR(s) cycle kernels (float64 / complex128, and float32 for the float32 + refinement form,
+// whose scalars stay float64): the biorthogonal IDR(s) of van Gijzen and
 // Sonneveld, the paper's other fine-grid solver (Section 4.1, IDR(ncyc)-Proj(k)).
 //
 // One round of s + 1 operator products, with every scalar of the recurrence kept on the
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_idr_u(const T *__restrict__ r, con
 
 // G_k = A U_k; d = P^H G_k; last block: alpha, M[k:, k], beta, f.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_idr_g(DevOp op, const T *__restrict__ U, T *__restrict__ G,
+__global__ void __launch_bounds__(kThreads) k_idr_g(DevOp op, DevOp32 o32, const T *__restrict__ U, T *__restrict__ G,
                                                      const T *__restrict__ P, size_t ld, int k,
                                                      typename ST<T>::D *part, unsigned *ticket,
                                                      IdrState<typename ST<T>::D> *st) {
@@ -143,7 +144,6 @@ __global__ void __launch_bounds__(kThreads) k_idr_g(DevOp op, const T *__restric
     __shared__ D tot[kIdrMaxS];
     const int s = st->s;
     const int n = op.n;
-    const DevOp32 o32{};
     const T *Uk = U + (size_t)k * ld;
     T *Gk = G + (size_t)k * ld;
     T acc[kIdrMaxS];
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_idr_upd(T *__restrict__ G, T *__re
 
 // t = A r; <t, r>, <t, t>, <r, r>; last block: omega with the angle safeguard.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_idr_t(DevOp op, const T *__restrict__ r, T *__restrict__ t,
+__global__ void __launch_bounds__(kThreads) k_idr_t(DevOp op, DevOp32 o32, const T *__restrict__ r, T *__restrict__ t,
                                                      typename ST<T>::D *part, unsigned *ticket,
                                                      IdrState<typename ST<T>::D> *st) {
     using D = typename ST<T>::D;
@@ -241,7 +241,6 @@ __global__ void __launch_bounds__(kThreads) k_idr_t(DevOp op, const T *__restric
     __shared__ D red[(kThreads / 32) * 3];
     __shared__ D tot[3];
     const int n = op.n;
-    const DevOp32 o32{};
     T acc[3] = {ST<T>::zero(), ST<T>::zero(), ST<T>::zero()};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const T ti = Apply<T>::at(op, o32, i, [&](int j) { return r[j]; });

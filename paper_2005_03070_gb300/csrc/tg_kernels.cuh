@@ -37,6 +37,7 @@ __host__ __device__ __forceinline__ double dreal(cplx a) { return a.re; }
 __host__ __device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
 __host__ __device__ __forceinline__ cplx ddiv(cplx a, cplx b) { return cdiv(a, b); }
 __host__ __device__ __forceinline__ double dmul(double a, double b) { return a * b; }
+__host__ __device__ __forceinline__ float dmul(float a, float b) { return a * b; }
 __host__ __device__ __forceinline__ cplx dmul(cplx a, cplx b) { return a * b; }
 __host__ __device__ __forceinline__ double dsub(double a, double b) { return a - b; }
 __host__ __device__ __forceinline__ cplx dsub(cplx a, cplx b) { return a - b; }

@@ -245,9 +245,10 @@ class Operator:
         return status, out
 
     def solve_idr(self, b, x, P, defl=None, rtol=1e-8, ncyc=20, restart_mvps=0, kappa=0.7, max_mvps=10 ** 7,
-                  nrhs=1, history=0, stream=None):
+                  nrhs=1, history=0, precision="f64", stream=None):
         """tg_solve_idr: IDR(s)-Proj(k) with s = P's column count; P is an (s, n) tensor whose
-        rows are the shadow columns (the library orthonormalises them)."""
+        rows are the shadow columns (the library orthonormalises them); precision "f64" or
+        "f32_ir" (float32 cycles with float64 refinement, real operators)."""
         s = P.shape[0]
         stats = (TgStats * nrhs)()
         bufs = []
@@ -257,7 +258,7 @@ class Operator:
                 bufs.append(buf)
                 st.history = C.cast(buf, C.POINTER(C.c_double))
                 st.history_cap = history
-        status = _lib.tg_solve_idr(self._h, defl.handle if defl is not None else None, TG_F64, _ptr(b), _ptr(x),
+        status = _lib.tg_solve_idr(self._h, defl.handle if defl is not None else None, PREC[precision], _ptr(b), _ptr(x),
                                    nrhs, rtol, ncyc, restart_mvps, s, _ptr(P.contiguous()), kappa, max_mvps, stats,
                                    _stream(stream))
         if status in (TG_BAD_ARG, TG_OOM, TG_CUDA_ERROR):

@@ -92,6 +92,33 @@ def test_example1_two_grid(tg, method):
     assert rel(x, xs) <= 1e-6
 
 
+@pytest.mark.parametrize("case", ["exp2d", "helmholtz"])
+def test_idr_float32_refinement_two_grid(tg, case):
+    """IDR(4)-Proj in the float32 + refinement form: float32 IDR cycles on the correction
+    equation (float32 shadow space and projection) with float64 refinement, on Example 1's
+    operator (127^2) and on the indefinite Helmholtz case (63^2, -Lap u - 30^2 u, cubic
+    prolongation).  The solution reaches rtol = 1e-10 (recomputed by the oracle's operator)
+    and the direct solution to 1e-6."""
+    if case == "exp2d":
+        top, oop = _pairs(tg, 127)["exp2d"]
+        m, k, ncyc = 40, 20, 20
+    else:
+        top = tg.Operator("cd2d", 63, (0.0,), mass=-900.0, interp="cubic")
+        oop = OOp(CD2D, 63, (0.0,), mass=-900.0)
+        m, k, ncyc = 40, 20, 10
+    b = gi.rhs(oop.n, 46)
+    xs = twogrid.exact_solution(oop, b)
+    bt = cu(b)
+    xc, defl, _, _ = top.coarse_gmresdr(bt, m, k, rtolev=1e-3, rtol=1e-8, max_cycles=300, precision="f32_ir")
+    x = top.prolong(xc)
+    P = cu(gi.random_dense((4, top.n), 42))
+    status, st = top.solve_idr(bt, x, P, defl, rtol=1e-10, ncyc=ncyc, precision="f32_ir")
+    assert status == tg.TG_OK, st
+    xh = host(x)
+    assert np.linalg.norm(b - oop.apply(xh)) / np.linalg.norm(b) <= 1e-10
+    assert rel(xh, xs) <= 1e-6
+
+
 @pytest.mark.parametrize("interp", ["linear", "cubic"])
 @pytest.mark.parametrize("method", ["gmres", "idr"])
 def test_helmholtz_two_grid(tg, method, interp):
