@@ -1014,7 +1014,7 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
     TG_CHECK(bicg_vecs<T>(op, n, &w));
     const int g = grid_for(n, 8);
     // the padded float32 3D stencil kernels, each block marching zlen planes; zlen is chosen
-    // so that one wave of resident blocks (4 per SM) covers the grid
+    // so that one wave of resident blocks (two blocks of 32 x kPadRows threads per SM) covers the grid
     const bool use_plane = std::is_same<T, float>::value && padded > 0;
     int zlen_v = 0, zlen_t = 0, gp_v = 0, gp_t = 0;
     if (use_plane) {
@@ -1024,8 +1024,8 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
             *zl = (A.N + nz - 1) / nz;
             *blocks = tiles * ((A.N + *zl - 1) / *zl);
         };
-        pick_z(4, &zlen_v, &gp_v);
-        pick_z(4, &zlen_t, &gp_t);
+        pick_z(2, &zlen_v, &gp_v);
+        pick_z(2, &zlen_t, &gp_t);
     }
     const int gp = std::max(gp_v, gp_t);
     TG_CHECK(red_ready(op, (size_t)(g > gp ? g : gp) * 4 * sizeof(D), s));
@@ -1052,7 +1052,7 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
         for (int c = 0; c < chunk; ++c) {
             if (use_plane) {
                 if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_V, (3 * es + xbs) * nb, (fl + 2 * cf) * nb, k_bi_pad<0><<<gp_v, 256, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st, zlen_v));
+                    TG_PROF(P_BI_V, (3 * es + xbs) * nb, (fl + 2 * cf) * nb, k_bi_pad<0><<<gp_v, 32 * kPadRows, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st, zlen_v));
             } else {
                 TG_PROF(P_BI_V, (3 * es + xbs) * nb, (fl + 2 * cf) * nb, k_bi_v<T><<<g, kThreads, 0, s>>>(A, A32, w.p, w.rh, w.v, part, tk, st));
             }
@@ -1064,7 +1064,7 @@ static int bicg_cycle(tg_op *op, const DevOp &A, const DevOp32 &A32, T *x, T *r,
             }
             if (use_plane) {
                 if constexpr (std::is_same<T, float>::value)
-                    TG_PROF(P_BI_T, (3 * es + xbs) * nb, (fl + 8 * cf) * nb, k_bi_pad<1><<<gp_t, 256, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st, zlen_t));
+                    TG_PROF(P_BI_T, (3 * es + xbs) * nb, (fl + 8 * cf) * nb, k_bi_pad<1><<<gp_t, 32 * kPadRows, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st, zlen_t));
             } else {
                 TG_PROF(P_BI_T, (3 * es + xbs) * nb, (fl + 8 * cf) * nb, k_bi_t<T><<<g, kThreads, 0, s>>>(A, A32, w.s, w.rh, w.t, part, tk, st));
             }

@@ -1002,17 +1002,22 @@ __global__ void k_arnoldi_finish(const typename ST<T>::D *h1, const typename ST<
 // kept in a padded layout: element (x, y, z) at z P N + y P + x with the row pitch P a multiple
 // of 4 and greater than N, and x = N .. P-1 a zero column (the Dirichlet neighbour in x).  Rows
 // are then 16-byte aligned, so the stencil moves every operand as float4: a thread takes 4
-// consecutive points of a row, marches planes (its p at planes k-1..k+2 in registers, loaded
-// two planes ahead), takes its x neighbours from the neighbouring lanes' float4 (the block-edge
-// lanes load one value) and its y neighbours as float4 loads issued one plane ahead.  Outputs
-// at padding points are written as zeros, so every vector of the cycle keeps zero padding
-// and the cycle's dots need no mask.  Summation order per point is that of the one-point
-// float32 stencil (centre, -x, +x, -y, +y, -z, +z).
+// consecutive points of a row and marches planes.  Its p at planes k-1..k+2 sit in a ring of
+// four float4 registers, r_hat and the y neighbours (float4 loads of the rows above and below)
+// in rings of two; after the compute of plane k the dead slots are refilled with p(k+3),
+// r_hat(k+2) and the y neighbours at k+2.  The loop is unrolled by the ring length, so no
+// register is copied and no load is waited on before the plane that needs it (a rotating copy
+// would wait for a load issued in the same plane).  The x neighbours come from the
+// neighbouring lanes' float4 (the block-edge lanes load one value).  Outputs at padding points
+// are written as zeros, so every vector of the cycle keeps zero padding and the cycle's dots
+// need no mask.  Summation order per point is that of the one-point float32 stencil (centre,
+// -x, +x, -y, +y, -z, +z).
 
 __host__ __device__ __forceinline__ int pad_pitch(int N) { return (N + 1 + 3) / 4 * 4; }
+constexpr int kPadRows = 16;     // rows per xy tile: a block of 32 x kPadRows threads
 __host__ __device__ __forceinline__ int pad_tiles(int N) {
     const int G = pad_pitch(N) / 4;
-    return ((G + 31) / 32) * ((N + 7) / 8);
+    return ((G + 31) / 32) * ((N + kPadRows - 1) / kPadRows);
 }
 
 // in (N^3, x fastest) -> outp (padded, zero padding)
@@ -1049,21 +1054,23 @@ __device__ __forceinline__ float st7(const DevOp32 &o, float c, float w, float e
 
 // MODE 0: out = A p, <r_hat, out> -> alpha;  MODE 1: out = A p (p = s), the four dots -> omega,
 // rho_next, beta (or the half-step exit), as k_bi_v / k_bi_t.  Block b takes xy tile b % tiles
-// (32 float4 groups x 8 rows) and planes (b / tiles) * zlen .. + zlen - 1.
+// (32 float4 groups x kPadRows rows) and planes (b / tiles) * zlen .. + zlen - 1.
 template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_bi_pad(DevOp op, DevOp32 o, const float *__restrict__ p,
-                                                   const float *__restrict__ rh, float *__restrict__ out,
-                                                   double *part, unsigned *ticket, BiState<double> *st, int zlen) {
+__global__ void __launch_bounds__(32 * kPadRows, 2) k_bi_pad(DevOp op, DevOp32 o, const float *__restrict__ p,
+                                                             const float *__restrict__ rh, float *__restrict__ out,
+                                                             double *part, unsigned *ticket, BiState<double> *st,
+                                                             int zlen) {
     if (st->status != 0) return;
     if (MODE == 1 && st->half) return;
     constexpr int ND = MODE == 0 ? 1 : 4;
-    __shared__ double red[(256 / 32) * ND];
+    constexpr int RP = 4, RR = 2;     // ring lengths: p planes, r_hat / y-neighbour planes
+    __shared__ double red[kPadRows * ND];
     __shared__ double tot[ND];
     const int N = op.N;
     const int P = pad_pitch(N), G = P / 4;
     const int ntx = (G + 31) / 32, tiles = pad_tiles(N);
     const int b = blockIdx.x, xy = b % tiles;
-    const int g0 = (xy % ntx) * 32, y0 = (xy / ntx) * 8, z0 = (b / tiles) * zlen;
+    const int g0 = (xy % ntx) * 32, y0 = (xy / ntx) * kPadRows, z0 = (b / tiles) * zlen;
     const int z1 = min(z0 + zlen, N);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = g0 + lane, y = y0 + w, x = 4 * g;
@@ -1073,56 +1080,68 @@ __global__ void __launch_bounds__(256, 4) k_bi_pad(DevOp op, DevOp32 o, const fl
     const unsigned PS = (unsigned)P * (unsigned)N;
     const unsigned col = act ? (unsigned)y * P + x : 0u;
     auto at = [&](int z) { return (unsigned)z * PS + col; };
-    float4 pm = ld4c(act && z0 > 0, p, at(z0 - 1));
-    float4 pc = ld4c(act, p, at(z0));
-    float4 pn = ld4c(act && z0 + 1 < N, p, at(z0 + 1));
-    float4 pnn = ld4c(act && z0 + 2 < N, p, at(z0 + 2));
-    float4 rc = ld4c(act, rh, at(z0));
-    float4 rn = ld4c(act && z0 + 1 < z1, rh, at(z0 + 1));
-    float4 ys = ld4c(hs, p, at(z0) - P), yn = ld4c(hn, p, at(z0) + P);
+    // slots: p at plane z in (z - z0 + 1) % RP; r_hat and the y neighbours at plane z in (z - z0) % RR
+    float4 q[RP], r[RR], ys[RR], yn[RR];
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+        const int z = z0 - 1 + i;
+        q[i] = ld4c(act && z >= 0 && z < N, p, at(z));
+    }
+#pragma unroll
+    for (int i = 0; i < RR; ++i) {
+        const int z = z0 + i;
+        r[i] = ld4c(act && z < z1, rh, at(z));
+        ys[i] = ld4c(hs && z < z1, p, at(z) - P);
+        yn[i] = ld4c(hn && z < z1, p, at(z) + P);
+    }
     // which of the 4 points are grid points (x + i < N); the rest are padding
     const bool in1 = x + 1 < N, in2 = x + 2 < N, in3 = x + 3 < N;
+    const int zp = min(N, z1 + 1);     // p is needed up to plane z1
     float acc[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) acc[d] = 0.0f;
-    for (int k = z0; k < z1; ++k) {
-        const float4 pload = ld4c(act && k + 3 < N, p, at(k + 3));
-        const float4 rload = ld4c(act && k + 2 < z1, rh, at(k + 2));
-        const bool nxt = k + 1 < z1;
-        const float4 ysn = ld4c(hs && nxt, p, at(k + 1) - P);
-        const float4 ynn = ld4c(hn && nxt, p, at(k + 1) + P);
-        float xw = __shfl_up_sync(0xffffffffu, pc.w, 1);
-        float xe = __shfl_down_sync(0xffffffffu, pc.x, 1);
-        if (lane == 0) xw = hw ? p[at(k) - 1] : 0.0f;
-        if (lane == 31) xe = he ? p[at(k) + 4] : 0.0f;
-        float4 v;
-        v.x = st7(o, pc.x, xw, pc.y, ys.x, yn.x, pm.x, pn.x);
-        v.y = in1 ? st7(o, pc.y, pc.x, pc.z, ys.y, yn.y, pm.y, pn.y) : 0.0f;
-        v.z = in2 ? st7(o, pc.z, pc.y, pc.w, ys.z, yn.z, pm.z, pn.z) : 0.0f;
-        v.w = in3 ? st7(o, pc.w, pc.z, xe, ys.w, yn.w, pm.w, pn.w) : 0.0f;
-        if (x >= N) v.x = 0.0f;
-        if (act) {
-            *reinterpret_cast<float4 *>(out + at(k)) = v;
-            if (MODE == 0) {
-                acc[0] = fmaf(rc.x, v.x, acc[0]);
-                acc[0] = fmaf(rc.y, v.y, acc[0]);
-                acc[0] = fmaf(rc.z, v.z, acc[0]);
-                acc[0] = fmaf(rc.w, v.w, acc[0]);
-            } else {
-                const float vv[4] = {v.x, v.y, v.z, v.w}, cc[4] = {pc.x, pc.y, pc.z, pc.w};
-                const float rr[4] = {rc.x, rc.y, rc.z, rc.w};
+    for (int kb = z0; kb < z1; kb += RP) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    acc[0] = fmaf(vv[e], cc[e], acc[0]);
-                    acc[ND > 1 ? 1 : 0] = fmaf(vv[e], vv[e], acc[ND > 1 ? 1 : 0]);
-                    acc[ND > 2 ? 2 : 0] = fmaf(rr[e], cc[e], acc[ND > 2 ? 2 : 0]);
-                    acc[ND > 3 ? 3 : 0] = fmaf(rr[e], vv[e], acc[ND > 3 ? 3 : 0]);
+        for (int j = 0; j < RP; ++j) {
+            const int k = kb + j;
+            if (k >= z1) break;
+            const float4 pm = q[j], pc = q[(j + 1) % RP], pn = q[(j + 2) % RP];
+            const float4 rc = r[j % RR], ysc = ys[j % RR], ync = yn[j % RR];
+            float xw = __shfl_up_sync(0xffffffffu, pc.w, 1);
+            float xe = __shfl_down_sync(0xffffffffu, pc.x, 1);
+            if (lane == 0) xw = hw ? p[at(k) - 1] : 0.0f;
+            if (lane == 31) xe = he ? p[at(k) + 4] : 0.0f;
+            float4 v;
+            v.x = st7(o, pc.x, xw, pc.y, ysc.x, ync.x, pm.x, pn.x);
+            v.y = in1 ? st7(o, pc.y, pc.x, pc.z, ysc.y, ync.y, pm.y, pn.y) : 0.0f;
+            v.z = in2 ? st7(o, pc.z, pc.y, pc.w, ysc.z, ync.z, pm.z, pn.z) : 0.0f;
+            v.w = in3 ? st7(o, pc.w, pc.z, xe, ysc.w, ync.w, pm.w, pn.w) : 0.0f;
+            if (x >= N) v.x = 0.0f;
+            if (act) {
+                *reinterpret_cast<float4 *>(out + at(k)) = v;
+                if (MODE == 0) {
+                    acc[0] = fmaf(rc.x, v.x, acc[0]);
+                    acc[0] = fmaf(rc.y, v.y, acc[0]);
+                    acc[0] = fmaf(rc.z, v.z, acc[0]);
+                    acc[0] = fmaf(rc.w, v.w, acc[0]);
+                } else {
+                    const float vv[4] = {v.x, v.y, v.z, v.w}, cc[4] = {pc.x, pc.y, pc.z, pc.w};
+                    const float rr[4] = {rc.x, rc.y, rc.z, rc.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        acc[0] = fmaf(vv[e], cc[e], acc[0]);
+                        acc[ND > 1 ? 1 : 0] = fmaf(vv[e], vv[e], acc[ND > 1 ? 1 : 0]);
+                        acc[ND > 2 ? 2 : 0] = fmaf(rr[e], cc[e], acc[ND > 2 ? 2 : 0]);
+                        acc[ND > 3 ? 3 : 0] = fmaf(rr[e], vv[e], acc[ND > 3 ? 3 : 0]);
+                    }
                 }
             }
+            // refill the slots this plane freed
+            q[j] = ld4c(act && k + RP - 1 < zp, p, at(k + RP - 1));
+            r[j % RR] = ld4c(act && k + RR < z1, rh, at(k + RR));
+            ys[j % RR] = ld4c(hs && k + RR < z1, p, at(k + RR) - P);
+            yn[j % RR] = ld4c(hn && k + RR < z1, p, at(k + RR) + P);
         }
-        pm = pc; pc = pn; pn = pnn; pnn = pload;
-        rc = rn; rn = rload;
-        ys = ysn; yn = ynn;
     }
     block_reduce_store<float, double, ND>(acc, part, red);
     if (last_block(ticket)) {
