@@ -87,12 +87,13 @@ def test_cfg0_cycle_schedule_ncyc(tg):
     assert st["cycles"] <= 20
 
 
-@pytest.mark.parametrize("N", [33, 9, 65])
+@pytest.mark.parametrize("N", [33, 9, 65, 151])
 def test_float32_plane_stencil_bicgstab_parity(tg, N):
     """The float32 3D BiCGStab cycle runs in the padded layout (row pitch the multiple of 4
     above N, zero padding column) with the float4 plane-marching stencil (32 float4 groups x
-    8 rows per block).  N = 33, 9 and 65 (pitch 36, 12, 68) leave partial groups and tiles
-    along every axis; 12 products against the oracle's float64 BiCGStab from x0 = 0 agree to
+    16 rows per block, register rings of 4 and 2 planes).  N = 33, 9, 65 and 151 (pitch 36, 12,
+    68, 152) leave partial groups and tiles along every axis; their runs of 1, 2 and 11 planes
+    per block end inside and after the ring's unrolled period of 4; 12 products against the oracle's float64 BiCGStab from x0 = 0 agree to
     float32 accuracy (the iterates differ by float32 rounding only), which also checks the
     copies into and out of the padded layout."""
     beta = (2.0, 1.0, 0.5)
