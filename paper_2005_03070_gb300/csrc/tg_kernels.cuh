@@ -1008,7 +1008,9 @@ __global__ void k_arnoldi_finish(const typename ST<T>::D *h1, const typename ST<
 // r_hat(k+2) and the y neighbours at k+2.  The loop is unrolled by the ring length, so no
 // register is copied and no load is waited on before the plane that needs it (a rotating copy
 // would wait for a load issued in the same plane).  The x neighbours come from the
-// neighbouring lanes' float4 (the block-edge lanes load one value).  Outputs at padding points
+// neighbouring lanes' float4; the block-edge lanes take theirs (one value in the neighbouring
+// tile) from another ring of two, also loaded two planes ahead: loaded at the plane that uses
+// it, that one value held every warp for a full memory latency.  Outputs at padding points
 // are written as zeros, so every vector of the cycle keeps zero padding and the cycle's dots
 // need no mask.  Summation order per point is that of the one-point float32 stencil (centre,
 // -x, +x, -y, +y, -z, +z).
@@ -1080,8 +1082,10 @@ __global__ void __launch_bounds__(32 * kPadRows, 2) k_bi_pad(DevOp op, DevOp32 o
     const unsigned PS = (unsigned)P * (unsigned)N;
     const unsigned col = act ? (unsigned)y * P + x : 0u;
     auto at = [&](int z) { return (unsigned)z * PS + col; };
-    // slots: p at plane z in (z - z0 + 1) % RP; r_hat and the y neighbours at plane z in (z - z0) % RR
+    // slots: p at plane z in (z - z0 + 1) % RP; r_hat, the y neighbours and the x-edge values
+    // (lane 0: x - 1, lane 31: x + 4, both in the neighbouring tiles) at plane z in (z - z0) % RR
     float4 q[RP], r[RR], ys[RR], yn[RR];
+    float xwr[RR], xer[RR];
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
         const int z = z0 - 1 + i;
@@ -1093,6 +1097,8 @@ __global__ void __launch_bounds__(32 * kPadRows, 2) k_bi_pad(DevOp op, DevOp32 o
         r[i] = ld4c(act && z < z1, rh, at(z));
         ys[i] = ld4c(hs && z < z1, p, at(z) - P);
         yn[i] = ld4c(hn && z < z1, p, at(z) + P);
+        xwr[i] = hw && z < z1 ? p[at(z) - 1] : 0.0f;
+        xer[i] = he && z < z1 ? p[at(z) + 4] : 0.0f;
     }
     // which of the 4 points are grid points (x + i < N); the rest are padding
     const bool in1 = x + 1 < N, in2 = x + 2 < N, in3 = x + 3 < N;
@@ -1109,8 +1115,8 @@ __global__ void __launch_bounds__(32 * kPadRows, 2) k_bi_pad(DevOp op, DevOp32 o
             const float4 rc = r[j % RR], ysc = ys[j % RR], ync = yn[j % RR];
             float xw = __shfl_up_sync(0xffffffffu, pc.w, 1);
             float xe = __shfl_down_sync(0xffffffffu, pc.x, 1);
-            if (lane == 0) xw = hw ? p[at(k) - 1] : 0.0f;
-            if (lane == 31) xe = he ? p[at(k) + 4] : 0.0f;
+            if (lane == 0) xw = xwr[j % RR];
+            if (lane == 31) xe = xer[j % RR];
             float4 v;
             v.x = st7(o, pc.x, xw, pc.y, ysc.x, ync.x, pm.x, pn.x);
             v.y = in1 ? st7(o, pc.y, pc.x, pc.z, ysc.y, ync.y, pm.y, pn.y) : 0.0f;
@@ -1141,6 +1147,8 @@ __global__ void __launch_bounds__(32 * kPadRows, 2) k_bi_pad(DevOp op, DevOp32 o
             r[j % RR] = ld4c(act && k + RR < z1, rh, at(k + RR));
             ys[j % RR] = ld4c(hs && k + RR < z1, p, at(k + RR) - P);
             yn[j % RR] = ld4c(hn && k + RR < z1, p, at(k + RR) + P);
+            xwr[j % RR] = hw && k + RR < z1 ? p[at(k + RR) - 1] : 0.0f;
+            xer[j % RR] = he && k + RR < z1 ? p[at(k + RR) + 4] : 0.0f;
         }
     }
     block_reduce_store<float, double, ND>(acc, part, red);
