@@ -149,14 +149,14 @@ __global__ void __launch_bounds__(kThreads) k_mrb_bi_v(const float *__restrict__
     for (int q = 0; q < R; ++q) acc[0][q] = 0.f;
     const int n = op.n;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        // every column's A p is stored: a column that has left the cycle never reads its v, s
+        // or t again (its x and r are frozen; the next cycle starts from p = r), so its
+        // values need not be preserved, and the old values are not read
         VecR<R> y = applyR<R>(op, o32, j, p);
-        VecR<R> old = ldR<R>(v, j);
         VecR<R> h = ldR<R>(rh, j);
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            if (!on[q]) y.v[q] = old.v[q];
-            else acc[0][q] = fmaf(h.v[q], y.v[q], acc[0][q]);
-        }
+        for (int q = 0; q < R; ++q)
+            if (on[q]) acc[0][q] = fmaf(h.v[q], y.v[q], acc[0][q]);
         stR<R>(v, j, y);
     }
     double *slice = seg_part<R>(P);
@@ -199,13 +199,11 @@ __global__ void __launch_bounds__(kThreads) k_mrb_bi_s(const float *__restrict__
 #pragma unroll
     for (int q = 0; q < R; ++q) acc[0][q] = 0.f;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        VecR<R> a = ldR<R>(r, j), bb = ldR<R>(v, j), o = ldR<R>(s, j);
+        VecR<R> a = ldR<R>(r, j), bb = ldR<R>(v, j), o;
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            if (on[q]) {
-                o.v[q] = fmaf(ma[q], bb.v[q], a.v[q]);
-                acc[0][q] = fmaf(o.v[q], o.v[q], acc[0][q]);
-            }
+            o.v[q] = fmaf(ma[q], bb.v[q], a.v[q]);     // stored for every column, as in k_mrb_bi_v
+            if (on[q]) acc[0][q] = fmaf(o.v[q], o.v[q], acc[0][q]);
         }
         stR<R>(s, j, o);
     }
@@ -251,10 +249,10 @@ __global__ void __launch_bounds__(kThreads) k_mrb_bi_t(const float *__restrict__
     const int n = op.n;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         VecR<R> y = applyR<R>(op, o32, j, s);
-        VecR<R> old = ldR<R>(t, j), sv = ldR<R>(s, j), h = ldR<R>(rh, j);
+        VecR<R> sv = ldR<R>(s, j), h = ldR<R>(rh, j);     // t stored for every column, as in k_mrb_bi_v
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            if (!on[q]) { y.v[q] = old.v[q]; continue; }
+            if (!on[q]) continue;
             acc[0][q] = fmaf(y.v[q], sv.v[q], acc[0][q]);
             acc[1][q] = fmaf(y.v[q], y.v[q], acc[1][q]);
             acc[2][q] = fmaf(h.v[q], sv.v[q], acc[2][q]);
@@ -309,12 +307,23 @@ __global__ void __launch_bounds__(kThreads) k_mrb_bi_x(float *__restrict__ x, fl
         om[q] = (float)c.omega;
         be[q] = (float)c.beta;
     }
+    // with every column on a full step the new r is s - omega t throughout, and the old r
+    // (read only to keep the other columns' r) is not loaded
+    bool full = true;
+#pragma unroll
+    for (int q = 0; q < R; ++q) full = full && mode[q] == 1;
     float acc[1][R];
 #pragma unroll
     for (int q = 0; q < R; ++q) acc[0][q] = 0.f;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        VecR<R> xv = ldR<R>(x, j), rv = ldR<R>(r, j), pv = ldR<R>(p, j), sv = ldR<R>(s, j), tv = ldR<R>(t, j),
-                vv = ldR<R>(v, j);
+        VecR<R> xv = ldR<R>(x, j), pv = ldR<R>(p, j), sv = ldR<R>(s, j), tv = ldR<R>(t, j), vv = ldR<R>(v, j);
+        VecR<R> rv;
+        if (full) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) rv.v[q] = 0.0f;
+        } else {
+            rv = ldR<R>(r, j);
+        }
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             if (mode[q] == 1) {
