@@ -3058,6 +3058,14 @@ static int batch_setup_all(tg_batch *b, const double *R0, int m, int k, int nev,
     }
     GdrBatchPtrs P{C.seg.as<GdrSeg>(), C.part.as<double>(), kGbPartW, C.ticket.as<unsigned>()};
     const dim3 grid(kGbBlocks, count);
+    // V^H w through the pipelined kernel when its shared memory can be granted
+    static_assert(kGbPartW <= kGbPipeCols + 1, "the pipelined batched V^H w covers every column count");
+    bool gb_pipe = smem_attr_once((const void *)k_gb_gemv_t_pipe, (int)kGbPipeSmem) == cudaSuccess;
+    if (!gb_pipe) (void)cudaGetLastError();
+    auto gemv_t_all = [&](int j, int ncol_step, int reorth, int which) {
+        if (gb_pipe) k_gb_gemv_t_pipe<<<grid, kThreads, kGbPipeSmem, s>>>(P, j, ncol_step, reorth, which);
+        else k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, j, ncol_step, reorth, which);
+    };
     int any = count;
     int cyc = 0;
     while (any) {
@@ -3077,9 +3085,9 @@ static int batch_setup_all(tg_batch *b, const double *R0, int m, int k, int nev,
         // Arnoldi from each instance's j0 to m
         for (int j = jmin; j < m; ++j) {
             TG_PROF(P_APPLY, 0, 0, k_gb_apply<<<grid, kThreads, 0, s>>>(P, j));
-            TG_PROF(P_GEMV_T, 0, 0, k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, j, j + 2, 0, 0));
+            TG_PROF(P_GEMV_T, 0, 0, gemv_t_all(j, j + 2, 0, 0));
             TG_PROF(P_GEMV_N, 0, 0, k_gb_gemv_n_norm<<<grid, kThreads, 0, s>>>(P, j, j + 1, 0, 0));
-            TG_PROF(P_GEMV_T, 0, 0, k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, j, j + 1, 0, 1));
+            TG_PROF(P_GEMV_T, 0, 0, gemv_t_all(j, j + 1, 0, 1));
             TG_PROF(P_GEMV_N, 0, 0, k_gb_gemv_n_norm<<<grid, kThreads, 0, s>>>(P, j, j + 1, 0, 1));
             TG_PROF(P_SMALL, 0, 0, k_gb_finish<<<(count + 127) / 128, 128, 0, s>>>(P, count, j, ldh, 0));
             TG_PROF(P_SCALE, 0, 0, k_gb_scale<<<grid, kThreads, 0, s>>>(P, j, 0));
@@ -3157,7 +3165,7 @@ static int batch_setup_all(tg_batch *b, const double *R0, int m, int k, int nev,
             seg[i].j0 = seg[i].kk;
         }
         TG_CHECK_CUDA(cudaMemcpyAsync(C.seg.p, seg.data(), seg.size() * sizeof(GdrSeg), cudaMemcpyHostToDevice, s));
-        TG_PROF(P_REORTH, 0, 0, k_gb_gemv_t<<<grid, kThreads, 0, s>>>(P, 0, 0, 1, 0));
+        TG_PROF(P_REORTH, 0, 0, gemv_t_all(0, 0, 1, 0));
         TG_PROF(P_REORTH, 0, 0, k_gb_gemv_n_norm<<<grid, kThreads, 0, s>>>(P, 0, 0, 1, 0));
         TG_PROF(P_SMALL, 0, 0, k_gb_finish<<<(count + 127) / 128, 128, 0, s>>>(P, count, 0, ldh, 1));
         TG_PROF(P_SCALE, 0, 0, k_gb_scale<<<grid, kThreads, 0, s>>>(P, 0, 1));

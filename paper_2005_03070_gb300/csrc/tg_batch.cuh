@@ -661,6 +661,96 @@ __global__ void __launch_bounds__(kThreads) k_gb_gemv_t(GdrBatchPtrs P, int j, i
     }
 }
 
+// The same product with the rows staged through shared memory by a 3-deep cp.async chunk
+// pipeline (as k_gemv_t_pipe): block (x, i) takes instance i's 128-row chunks x, x + gx, ...,
+// each copied as (ncol + 1) columns x 512 bytes (w is the extra column) while the block
+// works on the previous chunk.  The basis columns start 16-byte aligned and ldv is a multiple
+// of 128 rows, so every chunk lies inside the allocation (rows at or beyond nc are masked).
+// ncol <= kGbPipeCols; dynamic shared memory 3 x (kGbPipeCols + 1) x 512 bytes.
+constexpr int kGbPipeCols = 64;
+constexpr size_t kGbPipeSmem = (size_t)3 * (kGbPipeCols + 1) * 128 * sizeof(float);
+__global__ void __launch_bounds__(kThreads, 2) k_gb_gemv_t_pipe(GdrBatchPtrs P, int j, int ncol_step, int reorth,
+                                                              int which) {
+    constexpr int R = 128, PE = 4, U = R / 32, kStages = 3, kMaxPerWarp = kGbPipeCols / 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *buf = reinterpret_cast<float *>(smem_raw);
+    const int b = blockIdx.y;
+    const GdrSeg &S = P.seg[b];
+    const bool on = reorth ? (S.active != 0) : gdr_takes(S, j);
+    if (!on) return;
+    const int ncol = reorth ? S.kk : ncol_step;
+    const int wcol = reorth ? S.kk : j + 1;
+    const float *V = S.V;
+    const float *w = S.V + (size_t)wcol * S.ldv;
+    const int n = S.nc;
+    const int cols = ncol + 1;
+    const size_t stage = (size_t)cols * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nchunks = (n + R - 1) / R, G = gridDim.x;
+    const int mine = (int)blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / G + 1 : 0;
+    auto issue = [&](int it) {
+        if (it < mine) {
+            const size_t row0 = ((size_t)blockIdx.x + (size_t)it * G) * R;
+            float *dst = buf + (size_t)(it % kStages) * stage;
+            for (int e = threadIdx.x; e < cols * (R / PE); e += blockDim.x) {
+                const int c = e / (R / PE), rp = e % (R / PE);
+                const float *src = (c < ncol ? V + (size_t)c * S.ldv : w) + row0 + PE * rp;
+                cp_async16(dst + (size_t)c * R + PE * rp, src);
+            }
+        }
+        cp_async_commit();
+    };
+    float acc[kMaxPerWarp];
+#pragma unroll
+    for (int q = 0; q < kMaxPerWarp; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int st = 0; st < kStages - 1; ++st) issue(st);
+    for (int it = 0; it < mine; ++it) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        issue(it + kStages - 1);          // the buffer of chunk it - 1, which every thread has read
+        const float *sb = buf + (size_t)(it % kStages) * stage;
+        const int row0 = ((int)blockIdx.x + it * G) * R;
+        float wv[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ok[u] = row0 + lane + 32 * u < n;
+            wv[u] = ok[u] ? sb[(size_t)ncol * R + lane + 32 * u] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kMaxPerWarp; ++q) {
+            const int c = warp + 8 * q;
+            if (c < ncol) {
+                const float *sc = sb + (size_t)c * R;
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[q] = fmaf(ok[u] ? sc[lane + 32 * u] : 0.f, wv[u], acc[q]);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    double *slice = P.part + (size_t)b * gridDim.x * P.partw;
+#pragma unroll
+    for (int q = 0; q < kMaxPerWarp; ++q) {
+        const int c = warp + 8 * q;
+        if (c < ncol) {
+            const float sum = warp_sum(acc[q]);
+            if (lane == 0) slice[(size_t)blockIdx.x * P.partw + c] = (double)sum;
+        }
+    }
+    if (last_block(P.ticket + b)) {
+        double *h = which ? S.h2 : S.h1;
+        for (int c = warp; c < ncol; c += (int)(blockDim.x >> 5)) {
+            double sum = 0.0;
+            for (int bb = lane; bb < (int)gridDim.x; bb += 32) sum += __ldcg(slice + (size_t)bb * P.partw + c);
+            sum = warp_sum(sum);
+            if (lane == 0) h[c] = sum;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) P.ticket[b] = 0u;
+    }
+}
+
 // w -= V[:, 0..ncol-1] h (float32, coefficients rounded once per block), then ||w||^2 into
 // nrm[0] (per instance, deterministic).
 __global__ void __launch_bounds__(kThreads) k_gb_gemv_n_norm(GdrBatchPtrs P, int j, int ncol_step, int reorth,
